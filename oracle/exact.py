@@ -1,0 +1,69 @@
+"""Closed-form eigenbasis solutions on constant-coefficient grids (oracle).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+For a = 1 on a uniform Dirichlet grid the matrix Atilde is a Kronecker sum of
+1D matrices h^{-2} tridiag(-1,2,-1), whose eigenpairs are
+(4 h^{-2} sin^2(i pi h / 2), sin(i j pi h)) (Sec. 5.1, with the 1D scaling undone);
+the orthonormal eigenvector matrix is the type-I discrete sine transform.
+Every function of A is then W phi(D) W^T f (eq. (exacalg), Sec. 1.1):
+  * exact solution          u   = A^{-alpha} f                    (phi = lambda^-alpha)
+  * exact BURA value        u_r = sum_j c_j (A - d_j I)^{-1} f    (phi = sum c_j/(lambda-d_j),
+                                                                    eq. (Rgeneral), Sec. 2.2)
+A = Atilde / Lambda with Lambda = max absolute row sum of Atilde (eq. (algebraic)).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft as sfft
+
+__all__ = ["gershgorin", "eigenvalues", "apply_function", "fractional", "bura_value", "bura_components"]
+
+
+def gershgorin(shape):
+    """max_i sum_j |Atilde_ij| for a = 1: each axis adds 2/h^2 plus 1/h^2 per interior neighbour."""
+    lam = 0.0
+    for n in shape:
+        h2 = (1.0 / (n + 1)) ** 2
+        lam += (2.0 + min(n - 1, 2)) / h2
+    return lam
+
+
+def eigenvalues(shape):
+    """Eigenvalues of the scaled A on the grid, as an array of the grid's shape."""
+    shape = tuple(int(n) for n in shape)
+    lam = np.zeros(shape)
+    d = len(shape)
+    for axis, n in enumerate(shape):
+        h = 1.0 / (n + 1)
+        i = np.arange(1, n + 1)
+        mu = 4.0 / h ** 2 * np.sin(i * np.pi * h / 2) ** 2
+        s = [1] * d
+        s[axis] = n
+        lam = lam + mu.reshape(s)
+    return lam / gershgorin(shape)
+
+
+def apply_function(shape, f, phi):
+    """W phi(Lambda) W^T f with W the orthonormal DST-I on every axis."""
+    shape = tuple(int(n) for n in shape)
+    F = sfft.dstn(np.asarray(f, dtype=np.float64).reshape(shape), type=1, norm="ortho")
+    F *= phi(eigenvalues(shape))
+    return sfft.idstn(F, type=1, norm="ortho").ravel()
+
+
+def fractional(shape, f, alpha):
+    """Exact u = A^{-alpha} f."""
+    return apply_function(shape, f, lambda lam: lam ** (-float(alpha)))
+
+
+def bura_value(shape, f, c, d):
+    """Exact u_r = sum_j c_j (A - d_j I)^{-1} f (every shifted system solved exactly)."""
+    c = [float(v) for v in c]
+    d = [float(v) for v in d]
+    return apply_function(shape, f, lambda lam: sum(cj / (lam - dj) for cj, dj in zip(c, d)))
+
+
+def bura_components(shape, f, d):
+    """The k+1 exact solutions v_j = (A - d_j I)^{-1} f, shape (k+1, N)."""
+    return np.stack([apply_function(shape, f, lambda lam, dj=float(dj): 1.0 / (lam - dj)) for dj in d])

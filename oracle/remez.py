@@ -1,0 +1,361 @@
+"""1-BURA of t^(1-alpha) on [0,1] by the modified Remez algorithm (oracle).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+What is computed
+----------------
+For 0 < alpha < 1 and k >= 1 the best uniform rational approximation
+r = P_k/Q_k in R(k,k) of t^(1-alpha) on [0,1] (Definition 2.1 "def-BURA",
+Sec. 2.1, with beta = 1, m = k), its error E_alpha(k,k;1), its 2k+2 extreme
+points, and the partial-fraction coefficients of t^{-1} r(t) (eq. (simplified),
+Sec. 2.2):
+
+    t^{-1} r(t) = sum_{j=0}^k c_j / (t - d_j),   d_0 = 0 > d_1 > ... > d_k.
+
+How (Algorithm 1, Sec. 3.2, taken step by step)
+------------------------------------------------
+* Work in the Chebyshev representation of eq. (eq1bua): s = 2t - 1 and
+  f(s) = ((1+s)/2)^(1-alpha), r(s) = sum pbar_j T_j(s) / (1 + sum_{j>=1} qbar_j T_j(s)).
+* Step 3 (update the rational approximation): on the current points s_i solve
+  f(s_i) - r(s_i) = (-1)^i E (i = 1..l, l = 2k+2) by the inner iteration of
+  Step 3(ii): with E^{(v-1)} fixed the system is linear in (pbar, qbar, E^{(v)});
+  the iteration on E is accelerated with Aitken-Steffensen over three successive
+  values (remark (3) after Algorithm 1).
+* Step 1 (update the equioscillation set): for every point s_i take the nearest
+  zeros of f - r on each side (Step 1(i)), the maximiser of |f - r| between them
+  (Step 1(ii)), then the global maximiser with the sign-preserving insertion
+  rule of Step 1(iii)-(iv).
+* Step 2 (convergence): stop when max_i eta_i - min_i eta_i < delta.
+* Output: E = |E_n| and the points; poles are the roots of Q mapped back with
+  t = (1+s)/2, and c_0 = P(0)/Q(0), c_j = P(d_j) / (d_j Q'(d_j)) (eq. (simplified);
+  c_0 = E by eq. (c0,beta), Sec. 4.1).
+
+Readings where the paper leaves a choice (each also listed in the design doc)
+-----------------------------------------------------------------------
+* Arithmetic: mpmath at ``dps`` decimal digits (default 60).  Table (tabLastS)
+  shows that quad precision stops converging at k = 7..11; the extreme points
+  cluster at 0 (eta_2 ~ 1e-25 for alpha = 0.9, k = 9), so far more digits are used.
+* Initialisation (the paper uses uniformly sampled points and a least-squares
+  r_0, without detail): continuation.  At alpha = 1/2 the k = 1 problem starts
+  from the points {0, 0.01, 0.3, 1} and the points for k+1 are those for k with
+  two points added below eta_2 by geometric extrapolation of the three smallest
+  nonzero points.  Any other alpha starts from the converged points of the same k
+  at alpha -/+ 0.05 (towards 1/2).  r_0 is the exact solution of Step 3 on these
+  points; it must alternate with E > 0 there, as the Initialization step requires,
+  otherwise the run stops with an error.
+* Stopping: delta = 1e-13 E; a run that does not reach it within N = 80
+  iterations raises (the extreme points are located to about 1e-15 in log t, so
+  the spread floors near 1e-14 E).
+* Step 1 search: the paper refines on shrinking local meshes (remark (2)); here
+  zeros are bracketed by bisection in log t and maxima found by golden-section
+  search in log t after a coarse scan.
+* Sign convention: i = 1 is s = -1 (t = 0), so f(0) - r(0) = -E and r(0) = +E,
+  matching Lemma 2.2 ("BURA_caracter") item 3 and eq. (c0,beta).
+* Normalisation of the monomial form: q_k = 1, as in Tables ta:coeff1-3.
+"""
+from __future__ import annotations
+
+import functools
+
+import mpmath as mp
+
+__all__ = ["bura", "remez_bura", "partial_fractions", "error_at", "BuraResult"]
+
+
+def _cheb(s, n):
+    """T_0(s) .. T_n(s) by the three-term recurrence of eq. (eq1bua)."""
+    T = [mp.mpf(1), s]
+    for _ in range(2, n + 1):
+        T.append(2 * s * T[-1] - T[-2])
+    return T[: n + 1]
+
+
+class _Problem:
+    def __init__(self, alpha, k):
+        self.g = 1 - mp.mpf(alpha)  # exponent beta - alpha with beta = 1
+        self.k = k
+
+    def f(self, t):
+        return mp.mpf(0) if t <= 0 else t ** self.g
+
+    def r(self, pbar, qbar, t):
+        T = _cheb(2 * t - 1, self.k)
+        return mp.fsum(a * b for a, b in zip(pbar, T)) / mp.fsum(a * b for a, b in zip(qbar, T))
+
+    def e(self, pbar, qbar, t):
+        """f - r at t (the error whose extrema are equalised)."""
+        return self.f(t) - self.r(pbar, qbar, t)
+
+
+def _step3_linear(P, pts, E_prev):
+    """One linear solve of Step 3(ii) with E^{(v-1)} = E_prev fixed."""
+    k = P.k
+    l = 2 * k + 2
+    M = mp.matrix(l, l)
+    rhs = mp.matrix(l, 1)
+    for i in range(l):
+        sgn = -1 if i % 2 == 0 else 1  # (-1)^i with the paper's i = 1..l
+        T = _cheb(2 * pts[i] - 1, k)
+        fi = P.f(pts[i])
+        for j in range(k + 1):
+            M[i, j] = T[j]
+        for j in range(1, k + 1):
+            M[i, k + j] = -(fi - sgn * E_prev) * T[j]
+        M[i, l - 1] = sgn
+        rhs[i] = fi
+    x = mp.lu_solve(M, rhs)
+    pbar = [x[j] for j in range(k + 1)]
+    qbar = [mp.mpf(1)] + [x[k + j] for j in range(1, k + 1)]
+    return pbar, qbar, x[l - 1]
+
+
+def _step3(P, pts, E0, V=60):
+    """Step 3: the fixed point E = phi(E) of the inner iteration of Step 3(ii), where phi(E) is
+    the E^{(v)} returned by the linear solve with E^{(v-1)} = E.  Aitken-Steffensen over three
+    successive values (remark (3) after Algorithm 1); when that does not settle the residual
+    g(E) = phi(E) - E within V steps, a secant iteration on g takes over."""
+    E = E0
+    eps = mp.mpf(10) ** (-(mp.mp.dps - 20))
+
+    def phi(x):
+        return _step3_linear(P, pts, x)[2]
+
+    for _ in range(V):
+        E1 = phi(E)
+        E2 = phi(E1)
+        den = E2 - 2 * E1 + E
+        En = E2 if den == 0 else E - (E1 - E) ** 2 / den
+        done = abs(En - E) <= eps * abs(En)
+        E = En
+        if done:
+            break
+    g = phi(E) - E
+    if abs(g) > eps * max(abs(E), mp.mpf(10) ** -30):
+        a, ga = E, g
+        b = E * (1 + mp.mpf(10) ** -6) if E != 0 else mp.mpf(10) ** -8
+        gb = phi(b) - b
+        for _ in range(4 * V):
+            if gb == ga:
+                break
+            c = b - gb * (b - a) / (gb - ga)
+            a, ga = b, gb
+            b = c
+            gb = phi(b) - b
+            if abs(gb) <= eps * abs(b):
+                break
+        E = b
+    return _step3_linear(P, pts, E)
+
+
+def _zero_between(P, pbar, qbar, a, b):
+    """A zero of f - r in (a, b) where the error changes sign (bisection in log t)."""
+    ea = P.e(pbar, qbar, a)
+    tiny = mp.mpf(10) ** (-(mp.mp.dps - 5))
+    for _ in range(500):
+        if a > 0:
+            m = mp.sqrt(a * b)
+        else:
+            m = b / 1000 if b > tiny else b / 2
+        em = P.e(pbar, qbar, m)
+        if (em > 0) == (ea > 0):
+            a, ea = m, em
+        else:
+            b = m
+        if a > 0 and b / a - 1 < mp.mpf(10) ** -20:
+            break
+    return (a + b) / 2
+
+
+def _golden_max(P, pbar, qbar, a, b):
+    la, lb = mp.log(a), mp.log(b)
+    gr = (mp.sqrt(5) - 1) / 2
+    x1, x2 = lb - gr * (lb - la), la + gr * (lb - la)
+    f1 = abs(P.e(pbar, qbar, mp.exp(x1)))
+    f2 = abs(P.e(pbar, qbar, mp.exp(x2)))
+    while lb - la > mp.mpf(10) ** -15:
+        if f1 > f2:
+            lb, x2, f2 = x2, x1, f1
+            x1 = lb - gr * (lb - la)
+            f1 = abs(P.e(pbar, qbar, mp.exp(x1)))
+        else:
+            la, x1, f1 = x1, x2, f2
+            x2 = la + gr * (lb - la)
+            f2 = abs(P.e(pbar, qbar, mp.exp(x2)))
+    return mp.exp((la + lb) / 2)
+
+
+def _argmax_between(P, pbar, qbar, a, b, nscan=12):
+    """Step 1(ii): argmax of |f - r| on [a, b] (a may be 0, b may be 1)."""
+    lo = b * mp.mpf(10) ** (-(mp.mp.dps - 15)) if a == 0 else a
+    cands = ([mp.mpf(0)] if a == 0 else []) + [lo * (b / lo) ** (mp.mpf(i) / nscan) for i in range(nscan + 1)]
+    vals = [abs(P.e(pbar, qbar, t)) for t in cands]
+    i = max(range(len(cands)), key=vals.__getitem__)
+    t = cands[i]
+    if t == 0 or t == 1:
+        return t
+    left = cands[i - 1] if i > 0 and cands[i - 1] > 0 else t / 10
+    right = cands[i + 1] if i + 1 < len(cands) else b
+    return _golden_max(P, pbar, qbar, max(left, lo), min(right, b))
+
+
+def _global_argmax(P, pbar, qbar, pts, nscan=400):
+    """Step 1(iii): global maximiser of |f - r| on [0,1] (scan + refine)."""
+    lo_exp = mp.mp.dps - 15
+    grid = sorted(set([mp.mpf(0), mp.mpf(1)] + list(pts)
+                      + [mp.mpf(10) ** (-lo_exp + lo_exp * mp.mpf(i) / nscan) for i in range(nscan)]
+                      + [mp.mpf(i) / 64 for i in range(1, 64)]))
+    vals = [abs(P.e(pbar, qbar, t)) for t in grid]
+    i = max(range(len(grid)), key=vals.__getitem__)
+    t = grid[i]
+    if t in pts or t == 0 or t == 1:
+        return t
+    # a maximiser that does not beat the current points beyond rounding is "already in the set"
+    if vals[i] <= max(abs(P.e(pbar, qbar, s)) for s in pts) * (1 + mp.mpf(10) ** (-(mp.mp.dps // 2))):
+        return pts[0]
+    return _golden_max(P, pbar, qbar, grid[i - 1], grid[i + 1])
+
+
+def remez_bura(alpha, k, pts0, dps=60, N=80, delta_rel=mp.mpf(10) ** -13):
+    """Algorithm 1 for beta = 1, m = k, from the initial points ``pts0`` (in t).
+
+    Returns (pbar, qbar, E, pts): Chebyshev coefficients of P and Q in s = 2t-1
+    (qbar_0 = 1), the signed level E (> 0 at convergence) and the 2k+2 points in t.
+    """
+    with mp.workdps(dps):
+        P = _Problem(alpha, k)
+        l = 2 * k + 2
+        pts = [mp.mpf(t) for t in pts0]
+        if len(pts) != l:
+            raise ValueError("need 2k+2 initial points")
+        # Initialization: r_0 solves Step 3 on s^(0); it must alternate there with E > 0.
+        pbar, qbar, E = _step3(P, pts, mp.mpf(0))
+        if not E > 0:
+            raise RuntimeError("inadmissible initial points for alpha=%s k=%d" % (alpha, k))
+        converged = False
+        for _n in range(1, N + 1):
+            # Step 1 (i)-(ii): zeros around each point, then the maximiser between them.
+            zeros = [_zero_between(P, pbar, qbar, pts[i], pts[i + 1]) for i in range(l - 1)]
+            bnd = [mp.mpf(0)] + zeros + [mp.mpf(1)]
+            new = [_argmax_between(P, pbar, qbar, bnd[i], bnd[i + 1]) for i in range(l)]
+            # Step 1 (iii)-(iv): global maximiser, inserted keeping the sign pattern.
+            ts = _global_argmax(P, pbar, qbar, new)
+            if ts not in new:
+                j = max(i for i in range(l) if new[i] < ts) if ts > new[0] else 0
+                if j + 1 < l and mp.sign(P.e(pbar, qbar, ts)) != mp.sign(P.e(pbar, qbar, new[j])):
+                    new[j + 1] = ts
+                else:
+                    new[j] = ts
+            eta = [abs(P.e(pbar, qbar, t)) for t in new]
+            pts = new
+            # Step 2: convergence check.
+            if max(eta) - min(eta) < delta_rel * abs(E):
+                converged = True
+                break
+            # Step 3: new rational approximation on the updated points.
+            pbar, qbar, E = _step3(P, pts, E)
+            if not E > 0:
+                raise RuntimeError("Remez lost the alternation for alpha=%s k=%d" % (alpha, k))
+        if not converged:
+            raise RuntimeError("Remez did not converge for alpha=%s k=%d" % (alpha, k))
+        return pbar, qbar, E, pts
+
+
+def _cheb_to_monomial(cb):
+    """Coefficients (ascending powers of t) of sum_j cb_j T_j(2t-1)."""
+    n = len(cb) - 1
+    Tm = [[mp.mpf(1)], [mp.mpf(-1), mp.mpf(2)]]
+    for j in range(2, n + 1):
+        a, b = Tm[-1], Tm[-2]
+        nxt = [mp.mpf(0)] * (j + 1)
+        for i, v in enumerate(a):  # 2(2t-1) * T_{j-1}
+            nxt[i] -= 2 * v
+            nxt[i + 1] += 4 * v
+        for i, v in enumerate(b):
+            nxt[i] -= v
+        Tm.append(nxt)
+    out = [mp.mpf(0)] * (n + 1)
+    for j, c in enumerate(cb):
+        for i, v in enumerate(Tm[j]):
+            out[i] += c * v
+    return out
+
+
+def _polyval(c, t):
+    return mp.fsum(ci * t ** i for i, ci in enumerate(c))
+
+
+def partial_fractions(pbar, qbar):
+    """Monomial p, q (q_k = 1), poles d_0 = 0 > d_1 > ... > d_k, zeros zeta and c_j.
+
+    eq. (simplified): t^{-1} P(t)/Q(t) = sum_j c_j / (t - d_j) with d_0 = 0;
+    c_0 = P(0)/Q(0) and c_j = P(d_j) / (d_j Q'(d_j)) for the simple poles d_j.
+    """
+    p = _cheb_to_monomial(pbar)
+    q = _cheb_to_monomial(qbar)
+    lead = q[-1]
+    p = [v / lead for v in p]
+    q = [v / lead for v in q]
+    k = len(q) - 1
+    extra = mp.mp.dps
+    poles = mp.polyroots(list(reversed(q)), maxsteps=400, extraprec=4 * extra)
+    zeros = mp.polyroots(list(reversed(p)), maxsteps=400, extraprec=4 * extra)
+    poles = sorted((mp.re(z) for z in poles), reverse=True)
+    zeros = sorted((mp.re(z) for z in zeros), reverse=True)
+    dq = [i * q[i] for i in range(1, k + 1)]
+    c = [_polyval(p, 0) / _polyval(q, 0)]
+    for d in poles:
+        c.append(_polyval(p, d) / (d * _polyval(dq, d)))
+    return p, q, [mp.mpf(0)] + poles, c, zeros
+
+
+class BuraResult:
+    """alpha, k, E, eta (extreme points), p, q (monomial, q_k = 1), d, c, zeta."""
+
+    def __init__(self, alpha, k, E, eta, p, q, d, c, zeta, pbar, qbar):
+        self.alpha, self.k, self.E, self.eta = alpha, k, E, eta
+        self.p, self.q, self.d, self.c, self.zeta = p, q, d, c, zeta
+        self.pbar, self.qbar = pbar, qbar
+
+    def r(self, t):
+        """r(t) = P(t)/Q(t) (multi-precision)."""
+        t = mp.mpf(t)
+        return _polyval(self.p, t) / _polyval(self.q, t)
+
+    def floats(self):
+        return {"alpha": float(self.alpha), "k": self.k, "E": float(self.E),
+                "c": [float(v) for v in self.c], "d": [float(v) for v in self.d]}
+
+
+def _extend_points(pts):
+    """Continuation k -> k+1: two extra points below eta_2 (geometric extrapolation)."""
+    r1 = pts[2] / pts[1]
+    r2 = pts[3] / pts[2]
+    n1 = pts[1] / (r1 * r1 / r2)
+    n0 = n1 / (r1 ** 3 / r2 ** 2)
+    return [mp.mpf(0), n0, n1] + list(pts[1:])
+
+
+@functools.lru_cache(maxsize=None)
+def bura(alpha, k, dps=60):
+    """1-BURA data for (alpha, k), by continuation (see the module notes)."""
+    alpha = round(float(alpha), 6)
+    if not (0 < alpha < 1) or k < 1:
+        raise ValueError("need 0 < alpha < 1 and k >= 1")
+    with mp.workdps(dps):
+        if alpha == 0.5:
+            if k == 1:
+                pts = [mp.mpf(0), mp.mpf("0.01"), mp.mpf("0.3"), mp.mpf(1)]
+            else:
+                pts = _extend_points(bura(0.5, k - 1, dps).eta)
+        else:
+            nxt = 0.5 if abs(alpha - 0.5) <= 0.05 + 1e-12 else round(alpha - (0.05 if alpha > 0.5 else -0.05), 6)
+            pts = list(bura(nxt, k, dps).eta)
+        pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=dps)
+        p, q, d, c, zeta = partial_fractions(pbar, qbar)
+        return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
+
+
+def error_at(res, t):
+    """t^(1-alpha) - r(t) for a BuraResult (multi-precision)."""
+    t = mp.mpf(t)
+    return (t ** (1 - mp.mpf(res.alpha)) if t > 0 else mp.mpf(0)) - res.r(t)
