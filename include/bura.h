@@ -1,0 +1,167 @@
+/*
+ * bura.h — C ABI of the GB300 BURA fractional solver.
+ *
+ * Solves  A^alpha u = f  (0 < alpha < 1) for the scaled SPD finite-difference
+ * matrix A = Atilde / Lambda of -div(a grad u) on a uniform 2D/3D interior grid
+ * of the unit square/cube with homogeneous Dirichlet data (eq. (algebraic),
+ * Sec. 1.2; Lambda = max absolute row sum of Atilde, so spec(A) lies in (0,1]).
+ *
+ * Method (beta = 1): the best uniform rational approximation r of t^(1-alpha)
+ * on [0,1] (Definition def-BURA, Sec. 2.1) is written as
+ *     t^{-1} r(t) = sum_{j=0}^k c_j / (t - d_j),  d_0 = 0 > d_1 > ... > d_k,  c_j > 0
+ * (eq. (simplified), Sec. 2.2) and
+ *     u = sum_{j=0}^k c_j (A - d_j I)^{-1} f            (eq. (Rgeneral), Sec. 2.2).
+ * All k+1 shifted SPD systems are solved together by one multi-shift conjugate
+ * gradient method preconditioned by geometric multigrid, in CUDA kernels on the
+ * current device; the weighted sum is formed in FP64 on the device.
+ *
+ * Conventions for every entry point
+ *  - Return value: BURA_OK (0) or a negative bura_status; nothing aborts and no
+ *    exception crosses the ABI.  bura_strerror() describes a code.
+ *  - Grid vectors (f, u) have N = nx*ny*nz entries in lexicographic order, x fastest.
+ *  - A "device" pointer is CUDA global memory of the current device; a "host"
+ *    pointer is ordinary (ideally page-locked) host memory.
+ *  - A plan is used by one host thread and one stream at a time.
+ *  - There is no CPU fallback: without a usable CUDA device every solve fails
+ *    with BURA_ECUDA.
+ */
+#ifndef BURA_H
+#define BURA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BURA_MAX_K 12 /* largest supported BURA degree k (k+1 shifted systems) */
+
+typedef enum {
+    BURA_OK = 0,
+    BURA_EINVAL = -1,   /* bad argument: alpha not in (0,1), k out of range, bad grid, null pointer */
+    BURA_ENOMEM = -2,   /* device or host allocation failed */
+    BURA_EREMEZ = -3,   /* the rational approximation did not converge for (alpha, k) */
+    BURA_ENOTSPD = -4,  /* CG breakdown: p^T (A - d I) p <= 0 or non-finite values */
+    BURA_ENOCONV = -5,  /* tolerance not met within the iteration caps; u holds the last iterate */
+    BURA_ETIMEOUT = -6, /* a bounded device-side wait ran out */
+    BURA_ECUDA = -7,    /* a CUDA runtime call failed (no device, launch error, ...) */
+    BURA_ERANGE = -8    /* a size is above a documented maximum */
+} bura_status;
+
+typedef enum { BURA_COEF_CONSTANT = 0, BURA_COEF_FACES = 1 } bura_coef_kind;
+
+typedef enum {
+    BURA_PREC_FP64 = 0,  /* every inner iteration in FP64 */
+    BURA_PREC_MIXED = 1  /* FP32 multigrid-PCG inner solves inside FP64 iterative refinement */
+} bura_precision;
+
+/* Interior grid.  dim = 2 uses n[0] = nx, n[1] = ny (n[2] ignored); dim = 3 uses all three.
+ * Mesh sizes are h_x = 1/(nx+1) etc.  Multigrid coarsens while every n is odd and >= 3
+ * (n -> (n-1)/2), so sizes 2^m - 1 give the deepest hierarchy. */
+typedef struct {
+    int dim;
+    int n[3];
+    int coef_kind; /* bura_coef_kind */
+} bura_grid;
+
+/* Solver options; bura_default_options() fills the defaults. */
+typedef struct {
+    int precision;        /* bura_precision; default BURA_PREC_MIXED */
+    int smoother_degree;  /* Chebyshev degree of each pre/post smoothing; default 2 */
+    double smoother_ratio;/* Chebyshev interval [lmax/ratio, lmax] of D^{-1}(A - d I); default 8 */
+    int max_iters;        /* cap on PCG iterations per (inner) solve; default 200 */
+    int max_outer;        /* cap on FP64 refinement steps (mixed precision); default 12 */
+    double inner_rtol;    /* relative residual reduction of one FP32 inner solve; default 1e-5 */
+    int coarse_degree;    /* Chebyshev degree on the coarsest level when it has > 1 point; 0 = auto */
+    int reserved[8];
+} bura_options;
+
+/* Statistics of the last bura_solve*/
+typedef struct {
+    double Lambda;                   /* Gershgorin scale of Atilde */
+    double E;                        /* BURA error E_alpha(k,k;1) of the rational approximation */
+    int k;                           /* degree; k+1 systems */
+    int levels;                      /* multigrid levels */
+    int iters;                       /* PCG iterations in total (sum over refinement steps) */
+    int outer;                       /* FP64 refinement steps (mixed precision), 1 for FP64 */
+    int shift_iters[BURA_MAX_K + 1]; /* iterations each system stayed active */
+    double rel_res[BURA_MAX_K + 1];  /* final ||f - (A - d_j I) v_j|| / ||f|| per system */
+    double err_bound;                /* sum_j c_j ||r_j|| / ((lambda_lo - d_j) ||f||): bound on ||u - u_r|| / ||f|| */
+    double lambda_lo;                /* lower bound on lambda_min(A) used by the stopping test */
+} bura_stats;
+
+typedef struct bura_plan bura_plan;
+
+/* Fill *opt with the defaults listed in bura_options. */
+void bura_default_options(bura_options* opt);
+
+/*
+ * Best uniform rational approximation of t^(1-alpha) on [0,1] in R(k,k), host only
+ * (Sec. 3; the library's own Remez solver, see the implementation notes).
+ *   c[0..k], d[0..k]: caller-owned host arrays of k+1 doubles; d[0] = 0 > d[1] > ... > d[k].
+ *   E: the equioscillation level (may be NULL).
+ * Errors: BURA_EINVAL (alpha not in (0,1), k not in [1, BURA_MAX_K], null c/d),
+ *         BURA_EREMEZ (no convergence).
+ */
+int bura_rational(double alpha, int k, double* c, double* d, double* E);
+
+/*
+ * Build a plan for one grid, one operator, one (alpha, k): computes Lambda, the BURA
+ * coefficients, the multigrid hierarchy and all device workspaces (cudaMalloc on the
+ * current device; the plan owns them until bura_destroy).
+ *   faces: NULL for BURA_COEF_CONSTANT; otherwise `dim` HOST arrays of doubles
+ *          faces[0] = a on x-faces, shape (nz, ny, nx+1) [2D: (ny, nx+1)],
+ *          faces[1] = a on y-faces, shape (nz, ny+1, nx) [2D: (ny+1, nx)],
+ *          faces[2] = a on z-faces, shape (nz+1, ny, nx) (3D only),
+ *          C order, x fastest; faces[0][.., i] is a between interior nodes i-1 and i
+ *          (i = 0 and i = nx are the faces to the boundary).  All values must be > 0.
+ *          The arrays are copied; the caller keeps ownership.
+ *   opt: NULL for the defaults.
+ * Errors: BURA_EINVAL, BURA_ERANGE (N * (k+1) above 2^31), BURA_EREMEZ, BURA_ENOMEM, BURA_ECUDA.
+ */
+int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, int k,
+               const bura_options* opt, bura_plan** out);
+
+/*
+ * u = sum_j c_j (A - d_j I)^{-1} f, stream-ordered on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  f and u are DEVICE arrays of N doubles owned by the caller (they
+ * may alias each other).  The call returns once the solve has converged; u is complete when
+ * `stream` reaches this point.
+ *   tol: target bound on ||u - u_r|| / ||f||, u_r the exact value of eq. (Rgeneral).  Each system
+ *        j stops when c_j ||f - (A - d_j I) v_j|| / (lambda_lo - d_j) <= tol ||f|| / (k+1).
+ * Errors: BURA_EINVAL, BURA_ENOTSPD, BURA_ENOCONV (u still written), BURA_ECUDA.
+ */
+int bura_solve(bura_plan* plan, const double* f, double* u, double tol, void* stream);
+
+/*
+ * Same as bura_solve with HOST arrays f and u (N doubles each): copies f to the device,
+ * solves and copies u back on `stream`; returns after u is in host memory.
+ */
+int bura_solve_host(bura_plan* plan, const double* f, double* u, double tol, void* stream);
+
+/*
+ * The k+1 solutions v_j = (A - d_j I)^{-1} f themselves, written to the DEVICE array V of
+ * (k+1)*N doubles, system-major (V[j*N + i]), with the stopping rule of bura_solve.
+ */
+int bura_solve_systems(bura_plan* plan, const double* f, double* V, double tol, void* stream);
+
+/*
+ * y_j = (A - d_j I) x_j for the plan's shifts (the multi-shift operator of the solve, FP64):
+ * x and y are DEVICE arrays of (k+1)*N doubles, system-major.  For testing the operator.
+ */
+int bura_apply_shifted(bura_plan* plan, const double* x, double* y, void* stream);
+
+/* c[0..k], d[0..k] (host arrays of k+1 doubles) and E of the plan's rational approximation. */
+int bura_get_rational(const bura_plan* plan, double* c, double* d, double* E);
+
+/* Statistics of the last solve (host struct). */
+int bura_get_stats(const bura_plan* plan, bura_stats* stats);
+
+/* Frees every device and host resource of the plan (NULL is accepted). */
+int bura_destroy(bura_plan* plan);
+
+/* Static description of a status code. */
+const char* bura_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BURA_H */

@@ -32,9 +32,10 @@ How (Algorithm 1, Sec. 3.2, taken step by step)
 
 Readings where the paper leaves a choice (each also listed in the design doc)
 -----------------------------------------------------------------------
-* Arithmetic: mpmath at ``dps`` decimal digits (default 60).  Table (tabLastS)
-  shows that quad precision stops converging at k = 7..11; the extreme points
-  cluster at 0 (eta_2 ~ 1e-25 for alpha = 0.9, k = 9), so far more digits are used.
+* Arithmetic: mpmath with max(60, 40 + 4 |log10 eta_2|) decimal digits.  Table
+  (tabLastS) shows that quad precision stops converging at k = 7..11; the extreme
+  points cluster at 0 (eta_2 ~ 1e-25 for alpha = 0.9, k = 9) and the Step 3 matrix
+  loses about 4 digits per decade of eta_2, so far more digits are used.
 * Initialisation (the paper uses uniformly sampled points and a least-squares
   r_0, without detail): continuation.  At alpha = 1/2 the k = 1 problem starts
   from the points {0, 0.01, 0.3, 1} and the points for k+1 are those for k with
@@ -350,9 +351,14 @@ def bura(alpha, k, dps=60):
         else:
             nxt = 0.5 if abs(alpha - 0.5) <= 0.05 + 1e-12 else round(alpha - (0.05 if alpha > 0.5 else -0.05), 6)
             pts = list(bura(nxt, k, dps).eta)
-        pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=dps)
-        p, q, d, c, zeta = partial_fractions(pbar, qbar)
-        return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
+        # The Step 3 matrix loses about 4 digits per decade that eta_2 sits below 1 (its rows at
+        # the clustered points near s = -1 become nearly equal), so the working precision grows
+        # with -log10(eta_2) of the starting points.
+        work = max(dps, int(mp.ceil(40 + 4 * (-mp.log10(pts[1])))))
+        with mp.workdps(work):
+            pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=work)
+            p, q, d, c, zeta = partial_fractions(pbar, qbar)
+            return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
 
 
 def error_at(res, t):

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of the C ABI in include/bura.h (argument marshalling only).
+
+Every function has the name of its C entry point.  Device buffers are passed as
+torch CUDA tensors (their data_ptr()), host buffers as numpy arrays, and streams as
+torch.cuda.Stream objects or raw cudaStream_t integers.  Nothing here computes: the
+solver runs in libbura.so, and importing this module fails loudly if the library is
+missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbura.so")
+
+BURA_MAX_K = 12
+BURA_OK, BURA_EINVAL, BURA_ENOMEM, BURA_EREMEZ = 0, -1, -2, -3
+BURA_ENOTSPD, BURA_ENOCONV, BURA_ETIMEOUT, BURA_ECUDA, BURA_ERANGE = -4, -5, -6, -7, -8
+BURA_COEF_CONSTANT, BURA_COEF_FACES = 0, 1
+BURA_PREC_FP64, BURA_PREC_MIXED = 0, 1
+
+
+class bura_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("coef_kind", C.c_int)]
+
+
+class bura_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("smoother_degree", C.c_int), ("smoother_ratio", C.c_double),
+                ("max_iters", C.c_int), ("max_outer", C.c_int), ("inner_rtol", C.c_double),
+                ("coarse_degree", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class bura_stats(C.Structure):
+    _fields_ = [("Lambda", C.c_double), ("E", C.c_double), ("k", C.c_int), ("levels", C.c_int),
+                ("iters", C.c_int), ("outer", C.c_int), ("shift_iters", C.c_int * (BURA_MAX_K + 1)),
+                ("rel_res", C.c_double * (BURA_MAX_K + 1)), ("err_bound", C.c_double),
+                ("lambda_lo", C.c_double)]
+
+    def to_dict(self):
+        k = self.k
+        return {"Lambda": self.Lambda, "E": self.E, "k": k, "levels": self.levels, "iters": self.iters,
+                "outer": self.outer, "shift_iters": list(self.shift_iters)[: k + 1],
+                "rel_res": list(self.rel_res)[: k + 1], "err_bound": self.err_bound, "lambda_lo": self.lambda_lo}
+
+
+class BuraError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, _lib().bura_strerror(code).decode(), code))
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libbura.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        D = C.c_double
+        I = C.c_int
+        dp = C.POINTER(C.c_double)
+        L.bura_default_options.argtypes = [C.POINTER(bura_options)]
+        L.bura_default_options.restype = None
+        L.bura_rational.argtypes = [D, I, dp, dp, dp]
+        L.bura_setup.argtypes = [C.POINTER(bura_grid), C.POINTER(dp), D, I, C.POINTER(bura_options),
+                                 C.POINTER(P)]
+        L.bura_solve.argtypes = [P, P, P, D, P]
+        L.bura_solve_host.argtypes = [P, dp, dp, D, P]
+        L.bura_solve_systems.argtypes = [P, P, P, D, P]
+        L.bura_apply_shifted.argtypes = [P, P, P, P]
+        L.bura_get_rational.argtypes = [P, dp, dp, dp]
+        L.bura_get_stats.argtypes = [P, C.POINTER(bura_stats)]
+        L.bura_destroy.argtypes = [P]
+        L.bura_strerror.argtypes = [I]
+        L.bura_strerror.restype = C.c_char_p
+        for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
+                     "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy"):
+            getattr(L, name).restype = I
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, where, allow=()):
+    if rc != BURA_OK and rc not in allow:
+        raise BuraError(rc, where)
+    return rc
+
+
+def _dptr(t):
+    """Device pointer of a contiguous float64 torch CUDA tensor."""
+    if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float64"):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _hptr(a):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError("expected a C-contiguous float64 numpy array")
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def bura_default_options():
+    o = bura_options()
+    _lib().bura_default_options(C.byref(o))
+    return o
+
+
+def bura_strerror(code):
+    return _lib().bura_strerror(int(code)).decode()
+
+
+def bura_rational(alpha, k):
+    """(c, d, E) of the library's BURA of t^(1-alpha), k+1 coefficients each."""
+    c = np.zeros(k + 1)
+    d = np.zeros(k + 1)
+    E = C.c_double()
+    _check(_lib().bura_rational(float(alpha), int(k), _hptr(c), _hptr(d), C.byref(E)), "bura_rational")
+    return c, d, E.value
+
+
+def bura_setup(shape, alpha, k, faces=None, options=None):
+    """Plan for an interior grid ``shape`` = (nx, ny) or (nx, ny, nz).
+
+    faces: None (a = 1) or a tuple of float64 arrays (ax, ay[, az]) with the shapes of
+    include/bura.h (numpy C order (nz, ny, nx+1) etc.).  Returns an opaque plan handle.
+    """
+    g = bura_grid()
+    g.dim = len(shape)
+    for i, n in enumerate(shape[:3]):
+        g.n[i] = int(n)
+    g.coef_kind = BURA_COEF_CONSTANT if faces is None else BURA_COEF_FACES
+    keep = []
+    fptr = None
+    if faces is not None:
+        arr = (C.POINTER(C.c_double) * len(faces))()
+        for i, a in enumerate(faces):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            arr[i] = _hptr(a)
+        fptr = C.cast(arr, C.POINTER(C.POINTER(C.c_double)))
+    opt = options if options is not None else bura_default_options()
+    plan = C.c_void_p()
+    _check(_lib().bura_setup(C.byref(g), fptr, float(alpha), int(k), C.byref(opt), C.byref(plan)), "bura_setup")
+    return plan
+
+
+def bura_solve(plan, f, u, tol, stream=None):
+    """u = sum_j c_j (A - d_j I)^{-1} f on the device (torch float64 CUDA tensors); returns the status."""
+    return _check(_lib().bura_solve(plan, _dptr(f), _dptr(u), float(tol), _stream(stream)), "bura_solve",
+                  allow=(BURA_ENOCONV,))
+
+
+def bura_solve_host(plan, f, u, tol, stream=None):
+    """Same with host numpy arrays (copies inside the call)."""
+    return _check(_lib().bura_solve_host(plan, _hptr(f), _hptr(u), float(tol), _stream(stream)),
+                  "bura_solve_host", allow=(BURA_ENOCONV,))
+
+
+def bura_solve_systems(plan, f, V, tol, stream=None):
+    """The k+1 solutions (A - d_j I)^{-1} f into the (k+1, N) float64 CUDA tensor V."""
+    return _check(_lib().bura_solve_systems(plan, _dptr(f), _dptr(V), float(tol), _stream(stream)),
+                  "bura_solve_systems", allow=(BURA_ENOCONV,))
+
+
+def bura_apply_shifted(plan, x, y, stream=None):
+    """y_j = (A - d_j I) x_j for (k+1, N) float64 CUDA tensors."""
+    return _check(_lib().bura_apply_shifted(plan, _dptr(x), _dptr(y), _stream(stream)), "bura_apply_shifted")
+
+
+def bura_get_rational(plan, k):
+    c = np.zeros(k + 1)
+    d = np.zeros(k + 1)
+    E = C.c_double()
+    _check(_lib().bura_get_rational(plan, _hptr(c), _hptr(d), C.byref(E)), "bura_get_rational")
+    return c, d, E.value
+
+
+def bura_get_stats(plan):
+    st = bura_stats()
+    _check(_lib().bura_get_stats(plan, C.byref(st)), "bura_get_stats")
+    return st.to_dict()
+
+
+def bura_destroy(plan):
+    return _check(_lib().bura_destroy(plan), "bura_destroy")
+
+
+EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
+            "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
+            "bura_strerror"]

@@ -1,0 +1,108 @@
+// Device kernels of the multi-shift multigrid-preconditioned CG (all k+1 shifted systems at once).
+//
+// Data layout ("interleaved k-vector"): a multi-shift vector holds, for every grid point P
+// (lexicographic, x fastest), Kp consecutive values, one per shifted system (Kp = k+1 rounded up
+// to a multiple of W = 16 bytes / sizeof(T)).  A thread owns one 16-byte chunk (W systems) of one
+// point, so every load/store is a 128-bit vector access, a warp covers contiguous memory, and each
+// stencil neighbour / face coefficient is fetched once for all systems of the point.
+// Threads of a block form a (C = Kp/W) x PPB grid: threadIdx.x = chunk, threadIdx.y = point.
+//
+// Reductions (per system dot products) are deterministic: per-thread partials, a fixed-order
+// block reduction in shared memory, per-block partials in global scratch and a fixed-order
+// reduction by the last block to finish (threadfence + atomic ticket), which also applies the
+// CG scalar updates for every system.  Accumulation is FP64 from the block level up; a thread's
+// own partial is FP32 for FP32 data (at most a few tens of products) and FP64 for FP64 data.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bura {
+
+constexpr int KMAXP = 16;  // largest padded number of systems per point
+
+template <class T> struct VecT;
+template <> struct VecT<double> { static constexpr int W = 2; using V = double2; using Acc = double; };
+template <> struct VecT<float> { static constexpr int W = 4; using V = float4; using Acc = float; };
+
+// Geometry and operator of one multigrid level (passed by value).
+struct Lev {
+    int nx, ny, nz;     // interior sizes (nz = 1 in 2D)
+    long long N;        // nx*ny*nz
+    long long plane;    // nx*ny
+    double wx, wy, wz;  // constant-coefficient weights 1/(h^2 Lambda) per axis (wz = 0 in 2D)
+    const void* fx;     // variable coefficients: face weights a/(h^2 Lambda), element type T
+    const void* fy;
+    const void* fz;
+};
+
+// Per-system CG state shared by the kernels (device memory).
+struct Scal {
+    double rz[KMAXP];     // r^T z of the current iteration
+    double pq[KMAXP];     // p^T (A - dI) p
+    double alpha[KMAXP];
+    double beta[KMAXP];
+    double rr[KMAXP];     // ||r||^2
+    double thr[KMAXP];    // stop when rr <= thr
+    double dsh[KMAXP];    // shifts d_j
+    int active[KMAXP];
+    int iters[KMAXP];
+    int nactive;
+    int breakdown;
+    unsigned int ticket;  // last-block ticket, reset by the last block
+    int pad;
+};
+
+// Chebyshev step coefficients of one level: d_m = c1 d_{m-1} + c2 Dinv res (c2 includes 1/(diag - d)
+// for constant coefficients, where Dinv is a per-system scalar).
+struct ChebStep {
+    const double* c1;  // [Kp]
+    const double* c2;  // [Kp]
+};
+
+enum ReduceOp { RED_NONE = 0, RED_ALPHA = 1, RED_CONV = 2, RED_BETA = 3, RED_STORE = 4 };
+
+struct Red {
+    double* partial;   // [gridDim.x * Kp] scratch
+    Scal* scal;
+    double* out;       // RED_STORE destination [Kp]
+    int op;
+};
+
+struct Launch {
+    int Kp, C, PPB, blocks;
+};
+
+// ------------------------------------------------------------------ host launchers
+template <class T>
+struct Ops {
+    static void broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s);
+    static void spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, const T* pold, T* pnew, T* q,
+                       const Red& red, cudaStream_t s);
+    static void cg_update(const Launch& g, long long N, T* x, T* r, const T* p, const T* q, const Red& red,
+                          cudaStream_t s);
+    static void cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStep cs,
+                          const double* dsh, cudaStream_t s);
+    static void cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,
+                          T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s);
+    static void restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x,
+                             const T* b, T* bc, const double* dsh, cudaStream_t s);
+    static void prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x,
+                            cudaStream_t s);
+    static void apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const double* dsh,
+                              cudaStream_t s);
+    static void dot(const Launch& g, long long N, const T* a, const T* b, const Red& red, cudaStream_t s);
+};
+
+// FP64 refinement and output kernels.
+void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
+                       double* r, const Red& red, cudaStream_t s);
+void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K, const double* r64,
+                        const double* scale, float* r32, float* x32, float* p32, cudaStream_t s);
+void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
+                      const double* scale, cudaStream_t s);
+void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s);
+void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s);
+void launch_scatter_systems(long long N, int Kp, int K, const double* X, double* x, cudaStream_t s);
+void launch_gather_systems_f(long long N, int Kp, int K, const float* v, double* V, cudaStream_t s);
+
+}  // namespace bura

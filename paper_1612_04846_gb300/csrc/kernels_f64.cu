@@ -1,0 +1,156 @@
+// FP64 instantiation of the multi-shift MG-PCG kernels, plus the FP64 refinement, cast and output
+// kernels shared by both precision paths.
+#include <cstddef>
+
+#include "kernels_impl.cuh"
+
+namespace bura {
+template struct Ops<double>;
+
+// r = f - (A - d_j I) v (FP64 true residual of every system) and ||r_j||^2 -> red.out.
+template <int DIM, bool VAR>
+__global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const double* __restrict__ v,
+                             double* __restrict__ r, const double* __restrict__ dsh, Red red) {
+    constexpr int W = 2;
+    const int off = threadIdx.x * W;
+    double d[W];
+    for (int q = 0; q < W; ++q) d[q] = dsh[off + q];
+    LoadPlain<double> ld{v};
+    Accum<double> acc;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < L.N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= L.N) continue;
+        double vc[W], Av[W], diag;
+        stencil<double, DIM, VAR>(L, Kp, P, off, ld, vc, Av, diag);
+        const double fv = __ldg(f + P);
+        double rv[W];
+        for (int q = 0; q < W; ++q) rv[q] = fv - fma(-d[q], vc[q], Av[q]);
+        vst(r + (size_t)P * Kp + off, rv);
+        acc.add(rv, rv);
+    }
+    reduce_finish<double>(acc, red, Kp);
+}
+
+void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
+                       double* r, const Red& red, cudaStream_t s) {
+    const size_t sh = (size_t)g.C * g.PPB * 2 * sizeof(double);
+    // the shifts live in the device Scal record (address arithmetic only, no host dereference)
+    const double* dsh = reinterpret_cast<const double*>(reinterpret_cast<const char*>(red.scal) + offsetof(Scal, dsh));
+    if (dim == 2 && !var) k_residual64<2, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else if (dim == 2) k_residual64<2, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else if (!var) k_residual64<3, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else k_residual64<3, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+}
+
+// r32 = r64 * invscale_j (systems j < K with invscale > 0, else 0); x32 = 0; p32 = 0.  FP32 layout.
+__global__ void k_cast_scaled(int N, int Kp64, int Kp32, int K, const double* __restrict__ r64,
+                              const double* __restrict__ invscale, float* __restrict__ r32, float* __restrict__ x32,
+                              float* __restrict__ p32) {
+    const int off = threadIdx.x * 4;
+    double is[4];
+    for (int q = 0; q < 4; ++q) is[q] = (off + q < K) ? invscale[off + q] : 0.0;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= N) continue;
+        float rv[4], zv[4];
+        for (int q = 0; q < 4; ++q) {
+            rv[q] = (off + q < K) ? (float)(r64[(size_t)P * Kp64 + off + q] * is[q]) : 0.f;
+            zv[q] = 0.f;
+        }
+        const size_t base = (size_t)P * Kp32 + off;
+        vst(r32 + base, rv);
+        vst(x32 + base, zv);
+        vst(p32 + base, zv);
+    }
+}
+
+void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K, const double* r64,
+                        const double* invscale, float* r32, float* x32, float* p32, cudaStream_t s) {
+    k_cast_scaled<<<g32.blocks, dim3(g32.C, g32.PPB), 0, s>>>((int)N, g64.Kp, g32.Kp, K, r64, invscale, r32, x32, p32);
+}
+
+// v += scale_j * e (FP32 correction promoted to FP64); one thread per (point, pair of systems).
+__global__ void k_correct64(int N, int Kp64, int Kp32, int K, double* __restrict__ v, const float* __restrict__ e,
+                            const double* __restrict__ scale) {
+    const int off = threadIdx.x * 2;
+    double sc[2];
+    for (int q = 0; q < 2; ++q) sc[q] = (off + q < K) ? scale[off + q] : 0.0;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= N) continue;
+        const size_t b64 = (size_t)P * Kp64 + off;
+        const float2 ev = *reinterpret_cast<const float2*>(e + (size_t)P * Kp32 + off);
+        double2 vv = *reinterpret_cast<double2*>(v + b64);
+        vv.x = fma(sc[0], (double)ev.x, vv.x);
+        vv.y = fma(sc[1], (double)ev.y, vv.y);
+        *reinterpret_cast<double2*>(v + b64) = vv;
+    }
+}
+
+void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
+                      const double* scale, cudaStream_t s) {
+    k_correct64<<<g64.blocks, dim3(g64.C, g64.PPB), 0, s>>>((int)N, g64.Kp, g32.Kp, K, v, e, scale);
+}
+
+// u = sum_j c_j v_j (FP64, fixed order j = 0..K-1); one thread per point.
+__global__ void k_weighted_sum(int N, int Kp, int K, const double* __restrict__ v, const double* __restrict__ c,
+                               double* __restrict__ u) {
+    __shared__ double cs[KMAXP];
+    if (threadIdx.x < KMAXP) cs[threadIdx.x] = threadIdx.x < K ? c[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int P = blockIdx.x * blockDim.x + threadIdx.x; P < N; P += gridDim.x * blockDim.x) {
+        const double2* vp = reinterpret_cast<const double2*>(v + (size_t)P * Kp);
+        double s = 0.0;
+        for (int q = 0; q < Kp / 2; ++q) {
+            const double2 a = vp[q];
+            s = fma(cs[2 * q], a.x, s);
+            s = fma(cs[2 * q + 1], a.y, s);
+        }
+        u[P] = s;
+    }
+}
+
+static int grid1(long long N, int bs) {
+    long long b = (N + bs - 1) / bs;
+    return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s) {
+    k_weighted_sum<<<grid1(N, 256), 256, 0, s>>>((int)N, Kp, K, v, c, u);
+}
+
+__global__ void k_gather(int N, int Kp, int K, const double* __restrict__ v, double* __restrict__ V) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)N * K;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / N), P = (int)(t - (long long)j * N);
+        V[t] = v[(size_t)P * Kp + j];
+    }
+}
+
+__global__ void k_gather_f(int N, int Kp, int K, const float* __restrict__ v, double* __restrict__ V) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)N * K;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t / N), P = (int)(t - (long long)j * N);
+        V[t] = (double)v[(size_t)P * Kp + j];
+    }
+}
+
+__global__ void k_scatter(int N, int Kp, int K, const double* __restrict__ X, double* __restrict__ x) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)N * Kp;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int P = (int)(t / Kp), j = (int)(t - (long long)P * Kp);
+        x[t] = j < K ? X[(size_t)j * N + P] : 0.0;
+    }
+}
+
+void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s) {
+    k_gather<<<grid1(N * K, 256), 256, 0, s>>>((int)N, Kp, K, v, V);
+}
+void launch_gather_systems_f(long long N, int Kp, int K, const float* v, double* V, cudaStream_t s) {
+    k_gather_f<<<grid1(N * K, 256), 256, 0, s>>>((int)N, Kp, K, v, V);
+}
+void launch_scatter_systems(long long N, int Kp, int K, const double* X, double* x, cudaStream_t s) {
+    k_scatter<<<grid1(N * Kp, 256), 256, 0, s>>>((int)N, Kp, K, X, x);
+}
+
+}  // namespace bura

@@ -1,0 +1,794 @@
+// Host side of the C ABI: plan setup (scaling, multigrid hierarchy, Chebyshev smoother tables,
+// device workspaces) and the solve drivers (FP64 multi-shift PCG, and FP32 PCG inside FP64
+// iterative refinement), followed by the FP64 weighted sum u = sum_j c_j v_j (eq. (Rgeneral)).
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bura.h"
+#include "kernels.cuh"
+
+using namespace bura;
+
+namespace {
+
+struct HostLevel {
+    int n[3];            // nx, ny, nz (nz = 1 in 2D)
+    long long N;
+    double h[3];         // mesh sizes (h[2] unused in 2D)
+    double w[3];         // constant weights 1/(h^2 Lambda)
+    std::vector<double> a[3];  // unscaled face coefficients (variable coefficients only)
+    double amax;         // max diagonal of the scaled level operator
+    double lmin;         // lower bound on lambda_min of the scaled level operator
+};
+
+template <class T>
+struct Work {
+    int Kp = 0, W = 0, C = 0;
+    std::vector<Launch> g;
+    std::vector<Lev> L;
+    T *x = nullptr, *r = nullptr, *pa = nullptr, *pb = nullptr, *q = nullptr;
+    std::vector<T*> b, xa, xb, dd;
+    std::vector<std::vector<double*>> c1, c2;  // [level][step]
+    std::vector<int> deg;
+    double* dsh = nullptr;
+    Scal* scal = nullptr;
+    bool ready = false;
+};
+
+int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct bura_plan {
+    int dev = 0, nsm = 152;
+    int dim = 2;
+    bool var = false;
+    int k = 0, K = 0;
+    double alpha = 0, E = 0, Lambda = 0, lambda_lo = 0;
+    std::vector<double> c, d;
+    bura_options opt{};
+    std::vector<HostLevel> hl;
+    Work<double> w64;
+    Work<float> w32;
+    double* v64 = nullptr;   // FP64 solutions (refinement accumulator), Kp64 layout
+    double* r64 = nullptr;   // FP64 residuals, Kp64 layout
+    double* cdev = nullptr;  // c_j, Kp64 entries
+    double* partial = nullptr;
+    double* red_out = nullptr;  // [KMAXP]
+    double* scale = nullptr;    // [KMAXP] refinement scales
+    double* invscale = nullptr;
+    Scal* scal_outer = nullptr;
+    Scal* hscal = nullptr;      // pinned host mirror
+    double* hbuf = nullptr;     // pinned host scratch [4*KMAXP]
+    double* fdev = nullptr;     // host-solve staging
+    double* udev = nullptr;
+    std::vector<void*> allocs;
+    bura_stats st{};
+};
+
+namespace {
+
+cudaError_t g_last = cudaSuccess;
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) {                  \
+            g_last = e_;                          \
+            return BURA_ECUDA;                    \
+        }                                         \
+    } while (0)
+#define CKL() CK(cudaGetLastError())
+
+template <class P>
+int dalloc(bura_plan* p, P** ptr, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        g_last = e;
+        return e == cudaErrorMemoryAllocation ? BURA_ENOMEM : BURA_ECUDA;
+    }
+    p->allocs.push_back(q);
+    *ptr = reinterpret_cast<P*>(q);
+    return BURA_OK;
+}
+#define CA(expr)                      \
+    do {                              \
+        int rc_ = (expr);             \
+        if (rc_ != BURA_OK) return rc_; \
+    } while (0)
+
+Launch make_launch(int Kp, int W, long long N, int nsm) {
+    Launch g;
+    g.Kp = Kp;
+    g.C = Kp / W;
+    g.PPB = g.C <= 4 ? 64 : 32;
+    long long tiles = (N + g.PPB - 1) / g.PPB;
+    long long cap = (long long)nsm * 8;
+    g.blocks = (int)std::max(1LL, std::min(tiles, cap));
+    return g;
+}
+
+double harm(double a, double b) { return 2.0 / (1.0 / a + 1.0 / b); }
+
+// Coarse face coefficients: harmonic mean of the two fine faces in series on the line through
+// the coarse node (coarse node I sits on fine node 2I+1).
+void coarsen_faces(const HostLevel& f, HostLevel& c, int dim) {
+    const int fx = f.n[0], fy = f.n[1];
+    const int cx = c.n[0], cy = c.n[1], cz = c.n[2];
+    auto fidx = [&](int axis, int l, int j, int i) -> size_t {  // face arrays of the fine level
+        if (axis == 0) return ((size_t)l * fy + j) * (fx + 1) + i;
+        if (axis == 1) return ((size_t)l * (fy + 1) + j) * fx + i;
+        return ((size_t)l * fy + j) * fx + i;
+    };
+    c.a[0].assign((size_t)cz * cy * (cx + 1), 0.0);
+    c.a[1].assign((size_t)cz * (cy + 1) * cx, 0.0);
+    if (dim == 3) c.a[2].assign((size_t)(cz + 1) * cy * cx, 0.0);
+    for (int L = 0; L < cz; ++L) {
+        const int l = dim == 3 ? 2 * L + 1 : 0;
+        for (int J = 0; J < cy; ++J)
+            for (int I = 0; I <= cx; ++I)
+                c.a[0][((size_t)L * cy + J) * (cx + 1) + I] =
+                    harm(f.a[0][fidx(0, l, 2 * J + 1, 2 * I)], f.a[0][fidx(0, l, 2 * J + 1, 2 * I + 1)]);
+        for (int J = 0; J <= cy; ++J)
+            for (int I = 0; I < cx; ++I)
+                c.a[1][((size_t)L * (cy + 1) + J) * cx + I] =
+                    harm(f.a[1][fidx(1, l, 2 * J, 2 * I + 1)], f.a[1][fidx(1, l, 2 * J + 1, 2 * I + 1)]);
+    }
+    if (dim == 3)
+        for (int L = 0; L <= cz; ++L)
+            for (int J = 0; J < cy; ++J)
+                for (int I = 0; I < cx; ++I)
+                    c.a[2][((size_t)L * cy + J) * cx + I] =
+                        harm(f.a[2][fidx(2, 2 * L, 2 * J + 1, 2 * I + 1)], f.a[2][fidx(2, 2 * L + 1, 2 * J + 1, 2 * I + 1)]);
+}
+
+// Max diagonal of the scaled operator and min face value of a level (variable coefficients).
+void level_bounds(HostLevel& h, int dim, bool var, double Lambda) {
+    const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
+    double lc = 0.0;  // lambda_min of the constant-coefficient scaled operator on this level
+    for (int a = 0; a < dim; ++a) {
+        const double s = std::sin(M_PI * h.h[a] / 2.0);
+        lc += 4.0 * h.w[a] * s * s;
+    }
+    if (!var) {
+        h.amax = 2.0 * (h.w[0] + h.w[1] + (dim == 3 ? h.w[2] : 0.0));
+        h.lmin = lc;
+        return;
+    }
+    (void)Lambda;
+    double amax = 0.0, amin = 1e300;
+    for (int a = 0; a < dim; ++a)
+        for (double v : h.a[a]) amin = std::min(amin, v);
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double dg = (h.a[0][((size_t)l * ny + j) * (nx + 1) + i] + h.a[0][((size_t)l * ny + j) * (nx + 1) + i + 1]) * h.w[0];
+                dg += (h.a[1][((size_t)l * (ny + 1) + j) * nx + i] + h.a[1][((size_t)l * (ny + 1) + j + 1) * nx + i]) * h.w[1];
+                if (dim == 3)
+                    dg += (h.a[2][((size_t)l * ny + j) * nx + i] + h.a[2][((size_t)(l + 1) * ny + j) * nx + i]) * h.w[2];
+                amax = std::max(amax, dg);
+            }
+    h.amax = amax;
+    h.lmin = amin * lc;
+}
+
+// Gershgorin bound max_P sum_Q |Atilde_PQ| of the unscaled fine operator.
+double gershgorin(const HostLevel& h, int dim, bool var) {
+    const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
+    if (!var) {
+        double s = 0.0;
+        for (int a = 0; a < dim; ++a) s += (2.0 + std::min(h.n[a] - 1, 2)) / (h.h[a] * h.h[a]);
+        return s;
+    }
+    const double ix = 1.0 / (h.h[0] * h.h[0]), iy = 1.0 / (h.h[1] * h.h[1]), iz = dim == 3 ? 1.0 / (h.h[2] * h.h[2]) : 0.0;
+    double best = 0.0;
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double xm = h.a[0][((size_t)l * ny + j) * (nx + 1) + i] * ix;
+                const double xp = h.a[0][((size_t)l * ny + j) * (nx + 1) + i + 1] * ix;
+                const double ym = h.a[1][((size_t)l * (ny + 1) + j) * nx + i] * iy;
+                const double yp = h.a[1][((size_t)l * (ny + 1) + j + 1) * nx + i] * iy;
+                double zm = 0, zp = 0;
+                if (dim == 3) {
+                    zm = h.a[2][((size_t)l * ny + j) * nx + i] * iz;
+                    zp = h.a[2][((size_t)(l + 1) * ny + j) * nx + i] * iz;
+                }
+                double s = xm + xp + ym + yp + zm + zp;  // diagonal
+                if (i > 0) s += xm;
+                if (i < nx - 1) s += xp;
+                if (j > 0) s += ym;
+                if (j < ny - 1) s += yp;
+                if (dim == 3) {
+                    if (l > 0) s += zm;
+                    if (l < nz - 1) s += zp;
+                }
+                best = std::max(best, s);
+            }
+    return best;
+}
+
+// Chebyshev step coefficients for one level and every system: eigenvalue interval [lo_s, hi_s] of
+// Dinv (A - d_s I); c1/c2 per step as in the three-term Chebyshev semi-iteration.
+void cheb_tables(const HostLevel& h, bool var, const std::vector<double>& d, int K, int Kp, int deg, double ratio,
+                 bool coarse_solve, std::vector<std::vector<double>>& C1, std::vector<std::vector<double>>& C2) {
+    C1.assign(deg, std::vector<double>(Kp, 0.0));
+    C2.assign(deg, std::vector<double>(Kp, 0.0));
+    for (int s = 0; s < K; ++s) {
+        const double mds = -d[s];  // >= 0
+        const double hi = 1.0 + h.amax / (h.amax + mds);
+        double lo;
+        if (coarse_solve) lo = (h.lmin + mds) / (h.amax + mds);
+        else lo = std::max(hi / ratio, mds / (h.amax + mds));
+        lo = std::min(lo, hi * (1.0 - 1e-12));
+        const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+        const double sigma = theta / delta;
+        const double dinv = var ? 1.0 : 1.0 / (h.amax + mds);  // constant diagonal: amax == diag
+        double rho = 1.0 / sigma;
+        for (int m = 0; m < deg; ++m) {
+            if (m == 0) {
+                C1[m][s] = 0.0;
+                C2[m][s] = dinv / theta;
+            } else {
+                const double rn = 1.0 / (2.0 * sigma - rho);
+                C1[m][s] = rn * rho;
+                C2[m][s] = dinv * 2.0 * rn / delta;
+                rho = rn;
+            }
+        }
+    }
+}
+
+int coarse_degree_auto(const HostLevel& h, double d0) {
+    if (h.N == 1) return 1;
+    const double mds = -d0;
+    const double hi = 1.0 + h.amax / (h.amax + mds);
+    const double lo = (h.lmin + mds) / (h.amax + mds);
+    const double sigma = (hi + lo) / (hi - lo);
+    int m = (int)std::ceil(std::acosh(20.0) / std::acosh(sigma));
+    return std::max(2, std::min(m, 400));
+}
+
+template <class T>
+int build_work(bura_plan* p, Work<T>& w) {
+    const int nlev = (int)p->hl.size();
+    w.W = VecT<T>::W;
+    w.Kp = ceil_to(p->K, w.W);
+    w.C = w.Kp / w.W;
+    w.g.resize(nlev);
+    w.L.resize(nlev);
+    w.b.assign(nlev, nullptr);
+    w.xa.assign(nlev, nullptr);
+    w.xb.assign(nlev, nullptr);
+    w.dd.assign(nlev, nullptr);
+    w.c1.resize(nlev);
+    w.c2.resize(nlev);
+    w.deg.resize(nlev);
+    for (int l = 0; l < nlev; ++l) {
+        const HostLevel& h = p->hl[l];
+        w.g[l] = make_launch(w.Kp, w.W, h.N, p->nsm);
+        Lev& L = w.L[l];
+        L.nx = h.n[0];
+        L.ny = h.n[1];
+        L.nz = h.n[2];
+        L.N = h.N;
+        L.plane = (long long)h.n[0] * h.n[1];
+        L.wx = h.w[0];
+        L.wy = h.w[1];
+        L.wz = p->dim == 3 ? h.w[2] : 0.0;
+        L.fx = L.fy = L.fz = nullptr;
+        if (p->var) {
+            for (int a = 0; a < p->dim; ++a) {
+                std::vector<T> sc(h.a[a].size());
+                for (size_t i = 0; i < sc.size(); ++i) sc[i] = (T)(h.a[a][i] * h.w[a]);
+                T* dptr = nullptr;
+                CA(dalloc(p, &dptr, sc.size() * sizeof(T)));
+                CK(cudaMemcpy(dptr, sc.data(), sc.size() * sizeof(T), cudaMemcpyHostToDevice));
+                if (a == 0) L.fx = dptr;
+                else if (a == 1) L.fy = dptr;
+                else L.fz = dptr;
+            }
+        }
+        const size_t vb = (size_t)h.N * w.Kp * sizeof(T);
+        if (l > 0) CA(dalloc(p, &w.b[l], vb));
+        CA(dalloc(p, &w.xa[l], vb));
+        CA(dalloc(p, &w.xb[l], vb));
+        CA(dalloc(p, &w.dd[l], vb));
+        const bool coarsest = (l == nlev - 1);
+        int deg = p->opt.smoother_degree;
+        if (coarsest) deg = h.N == 1 ? 1 : (p->opt.coarse_degree > 0 ? p->opt.coarse_degree : coarse_degree_auto(h, p->d[0]));
+        w.deg[l] = deg;
+        std::vector<std::vector<double>> C1, C2;
+        cheb_tables(h, p->var, p->d, p->K, w.Kp, deg, p->opt.smoother_ratio, coarsest, C1, C2);
+        if (coarsest && h.N == 1) {  // exact solve of the 1x1 system: x = b / (diag - d)
+            for (int s = 0; s < p->K; ++s) C2[0][s] = p->var ? 1.0 : 1.0 / (h.amax - p->d[s]);
+        }
+        w.c1[l].assign(deg, nullptr);
+        w.c2[l].assign(deg, nullptr);
+        for (int m = 0; m < deg; ++m) {
+            CA(dalloc(p, &w.c1[l][m], w.Kp * sizeof(double)));
+            CA(dalloc(p, &w.c2[l][m], w.Kp * sizeof(double)));
+            CK(cudaMemcpy(w.c1[l][m], C1[m].data(), w.Kp * sizeof(double), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(w.c2[l][m], C2[m].data(), w.Kp * sizeof(double), cudaMemcpyHostToDevice));
+        }
+    }
+    const size_t vb0 = (size_t)p->hl[0].N * w.Kp * sizeof(T);
+    CA(dalloc(p, &w.x, vb0));
+    CA(dalloc(p, &w.r, vb0));
+    CA(dalloc(p, &w.pa, vb0));
+    CA(dalloc(p, &w.pb, vb0));
+    CA(dalloc(p, &w.q, vb0));
+    std::vector<double> dsh(KMAXP, 0.0);
+    for (int s = 0; s < p->K; ++s) dsh[s] = p->d[s];
+    CA(dalloc(p, &w.dsh, KMAXP * sizeof(double)));
+    CK(cudaMemcpy(w.dsh, dsh.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice));
+    CA(dalloc(p, &w.scal, sizeof(Scal)));
+    CK(cudaMemset(w.scal, 0, sizeof(Scal)));
+    w.ready = true;
+    return BURA_OK;
+}
+
+// Symmetric V-cycle on level l for rhs b; returns the buffer holding the result.  With rz_fused
+// (level 0 only) the last smoothing step also forms r^T z and the CG beta of every system.
+template <class T>
+T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream_t s) {
+    const int nlev = (int)p->hl.size();
+    const int dim = p->dim;
+    const bool var = p->var;
+    const Launch& g = w.g[l];
+    const Lev& L = w.L[l];
+    const int deg = w.deg[l];
+    T* A = w.xa[l];
+    T* B = w.xb[l];
+    T* D = w.dd[l];
+    Red none{p->partial, w.scal, nullptr, RED_NONE};
+    Red beta{p->partial, w.scal, nullptr, RED_BETA};
+    if (l == nlev - 1) {  // coarsest: exact 1-point solve or a fixed Chebyshev polynomial
+        Ops<T>::cheb_zero(g, L, dim, var, b, A, ChebStep{w.c1[l][0], w.c2[l][0]}, w.dsh, s);
+        T* cur = A;
+        T* oth = B;
+        for (int m = 1; m < deg; ++m) {
+            Ops<T>::cheb_step(g, L, dim, var, cur, m == 1 ? cur : D, b, oth, m < deg - 1 ? D : nullptr,
+                              ChebStep{w.c1[l][m], w.c2[l][m]}, w.dsh, none, s);
+            std::swap(cur, oth);
+        }
+        if (rz_fused) Ops<T>::dot(g, L.N, b, cur, beta, s);
+        return cur;
+    }
+    // pre-smoothing from a zero initial guess
+    Ops<T>::cheb_zero(g, L, dim, var, b, A, ChebStep{w.c1[l][0], w.c2[l][0]}, w.dsh, s);
+    T* cur = A;
+    T* oth = B;
+    for (int m = 1; m < deg; ++m) {
+        Ops<T>::cheb_step(g, L, dim, var, cur, m == 1 ? cur : D, b, oth, m < deg - 1 ? D : nullptr,
+                          ChebStep{w.c1[l][m], w.c2[l][m]}, w.dsh, none, s);
+        std::swap(cur, oth);
+    }
+    // coarse-grid correction
+    Ops<T>::restrict_res(w.g[l + 1], L, w.L[l + 1], dim, var, cur, b, w.b[l + 1], w.dsh, s);
+    T* ec = vcycle<T>(p, w, l + 1, w.b[l + 1], false, s);
+    Ops<T>::prolong_add(g, L, w.L[l + 1], dim, ec, cur, s);
+    // post-smoothing with the same polynomial (symmetric preconditioner)
+    for (int m = 0; m < deg; ++m) {
+        const bool last = (m == deg - 1);
+        Ops<T>::cheb_step(g, L, dim, var, cur, m == 0 ? nullptr : D, b, oth, last ? nullptr : D,
+                          ChebStep{m == 0 ? nullptr : w.c1[l][m], w.c2[l][m]}, w.dsh,
+                          (rz_fused && last) ? beta : none, s);
+        std::swap(cur, oth);
+    }
+    return cur;
+}
+
+// Multi-shift PCG on the work set w: r holds the right-hand sides, x = 0, pa = 0 and the Scal
+// record is initialised by the caller.  Returns BURA_OK, BURA_ENOCONV or BURA_ENOTSPD.
+template <class T>
+int pcg(bura_plan* p, Work<T>& w, int max_it, int* iters_out, cudaStream_t s) {
+    const Launch& g = w.g[0];
+    const Lev& L = w.L[0];
+    Red ralpha{p->partial, w.scal, nullptr, RED_ALPHA};
+    Red rconv{p->partial, w.scal, nullptr, RED_CONV};
+    T* pold = w.pa;
+    T* pnew = w.pb;
+    T* z = vcycle<T>(p, w, 0, w.r, true, s);
+    CKL();
+    int it = 0;
+    int status = BURA_ENOCONV;
+    while (it < max_it) {
+        Ops<T>::spmv_p(g, L, p->dim, p->var, z, pold, pnew, w.q, ralpha, s);
+        std::swap(pold, pnew);
+        Ops<T>::cg_update(g, L.N, w.x, w.r, pold, w.q, rconv, s);
+        CKL();
+        ++it;
+        CK(cudaMemcpyAsync(&p->hscal->nactive, &w.scal->nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (p->hscal->breakdown) { status = BURA_ENOTSPD; break; }
+        if (p->hscal->nactive == 0) { status = BURA_OK; break; }
+        z = vcycle<T>(p, w, 0, w.r, true, s);
+        CKL();
+    }
+    // copy back the whole record for statistics
+    CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *iters_out = it;
+    return status;
+}
+
+int init_scal(bura_plan* p, Scal* dev, const double* thr, const int* active, cudaStream_t s) {
+    Scal h;
+    std::memset(&h, 0, sizeof(h));
+    int na = 0;
+    for (int j = 0; j < KMAXP; ++j) {
+        h.rz[j] = 1.0;
+        h.beta[j] = 0.0;
+        h.alpha[j] = 0.0;
+        h.dsh[j] = j < p->K ? p->d[j] : 0.0;
+        h.thr[j] = j < p->K ? thr[j] : 0.0;
+        h.active[j] = (j < p->K && active[j]) ? 1 : 0;
+        na += h.active[j];
+    }
+    h.nactive = na;
+    h.ticket = 0u;
+    *p->hscal = h;
+    CK(cudaMemcpyAsync(dev, p->hscal, sizeof(Scal), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return BURA_OK;
+}
+
+// Per-system absolute thresholds on ||r_j||^2 so that sum_j c_j ||r_j|| / (lambda_lo - d_j) <= tol ||f||.
+void thresholds(const bura_plan* p, double tol, double fnorm2, double* thr) {
+    for (int j = 0; j < p->K; ++j) {
+        const double t = tol * (p->lambda_lo - p->d[j]) / (p->K * p->c[j]);
+        thr[j] = t * t * fnorm2;
+    }
+}
+
+void finish_stats(bura_plan* p, const double* rr, double fnorm2) {
+    double eb = 0.0;
+    const double fn = std::sqrt(fnorm2);
+    for (int j = 0; j < p->K; ++j) {
+        const double rn = std::sqrt(std::max(rr[j], 0.0));
+        p->st.rel_res[j] = fn > 0 ? rn / fn : 0.0;
+        eb += p->c[j] * rn / (p->lambda_lo - p->d[j]);
+    }
+    p->st.err_bound = fn > 0 ? eb / fn : 0.0;
+}
+
+int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
+    Work<double>& w = p->w64;
+    const long long N = p->hl[0].N;
+    Ops<double>::broadcast(w.g[0], f, N, p->K, w.r, w.x, w.pa, s);
+    CKL();
+    Red store{p->partial, w.scal, p->red_out, RED_STORE};
+    Ops<double>::dot(w.g[0], N, w.r, w.r, store, s);
+    CKL();
+    CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double fnorm2 = p->hbuf[0];
+    double thr[KMAXP] = {0};
+    int act[KMAXP] = {0};
+    thresholds(p, tol, fnorm2, thr);
+    for (int j = 0; j < p->K; ++j) act[j] = fnorm2 > 0 ? 1 : 0;
+    CA(init_scal(p, w.scal, thr, act, s));
+    int it = 0;
+    int rc = BURA_OK;
+    if (fnorm2 > 0) rc = pcg<double>(p, w, p->opt.max_iters, &it, s);
+    p->st.iters = it;
+    p->st.outer = 1;
+    for (int j = 0; j <= p->k; ++j) p->st.shift_iters[j] = fnorm2 > 0 ? p->hscal->iters[j] : 0;
+    double rr[KMAXP] = {0};
+    for (int j = 0; j < p->K; ++j) rr[j] = fnorm2 > 0 ? p->hscal->rr[j] : 0.0;
+    finish_stats(p, rr, fnorm2);
+    return rc;
+}
+
+int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
+    Work<float>& w = p->w32;
+    const Launch& g64 = p->w64.g[0];
+    const Lev& L64 = p->w64.L[0];
+    const long long N = p->hl[0].N;
+    CK(cudaMemsetAsync(p->v64, 0, (size_t)N * g64.Kp * sizeof(double), s));
+    Red store{p->partial, p->scal_outer, p->red_out, RED_STORE};
+    double fnorm2 = -1.0;
+    double thr64[KMAXP] = {0};
+    double rr[KMAXP] = {0};
+    int total_it = 0, outer = 0;
+    int rc = BURA_ENOCONV;
+    int siters[KMAXP] = {0};
+    for (;;) {
+        launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s);
+        CKL();
+        CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int j = 0; j < p->K; ++j) rr[j] = p->hbuf[j];
+        if (fnorm2 < 0) {
+            fnorm2 = rr[0];
+            thresholds(p, tol, fnorm2, thr64);
+        }
+        int act[KMAXP] = {0};
+        int na = 0;
+        for (int j = 0; j < p->K; ++j) {
+            if (!std::isfinite(rr[j])) return BURA_ENOTSPD;
+            act[j] = rr[j] > thr64[j] ? 1 : 0;
+            na += act[j];
+        }
+        if (na == 0) { rc = BURA_OK; break; }
+        if (outer >= p->opt.max_outer) { rc = BURA_ENOCONV; break; }
+        double* hs = p->hbuf + KMAXP;
+        double* his = p->hbuf + 2 * KMAXP;
+        double thr[KMAXP] = {0};
+        for (int j = 0; j < KMAXP; ++j) {
+            const bool a = j < p->K && act[j];
+            hs[j] = a ? std::sqrt(rr[j]) : 0.0;
+            his[j] = a ? 1.0 / hs[j] : 0.0;
+            if (a) {
+                // relative target of this inner solve (the scaled rhs has unit norm)
+                const double need = 0.5 * std::sqrt(thr64[j] / rr[j]);
+                const double t = std::max(p->opt.inner_rtol, need);
+                thr[j] = t * t;
+            }
+        }
+        CK(cudaMemcpyAsync(p->scale, hs, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(p->invscale, his, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s);
+        CKL();
+        CA(init_scal(p, w.scal, thr, act, s));
+        int it = 0;
+        int irc = pcg<float>(p, w, p->opt.max_iters, &it, s);
+        if (irc == BURA_ENOTSPD) return irc;
+        for (int j = 0; j < p->K; ++j) siters[j] += p->hscal->iters[j];
+        total_it += it;
+        launch_correct64(g64, w.g[0], N, p->K, p->v64, w.x, p->scale, s);
+        CKL();
+        ++outer;
+    }
+    p->st.iters = total_it;
+    p->st.outer = outer;
+    for (int j = 0; j <= p->k; ++j) p->st.shift_iters[j] = siters[j];
+    finish_stats(p, rr, fnorm2);
+    return rc;
+}
+
+int solve_core(bura_plan* p, const double* f, double tol, cudaStream_t s) {
+    if (!(tol > 0)) return BURA_EINVAL;
+    CK(cudaSetDevice(p->dev));
+    std::memset(p->st.shift_iters, 0, sizeof(p->st.shift_iters));
+    std::memset(p->st.rel_res, 0, sizeof(p->st.rel_res));
+    return p->opt.precision == BURA_PREC_FP64 ? solve_fp64(p, f, tol, s) : solve_mixed(p, f, tol, s);
+}
+
+const double* solution_vectors(const bura_plan* p, int* Kp) {
+    if (p->opt.precision == BURA_PREC_FP64) { *Kp = p->w64.Kp; return p->w64.x; }
+    *Kp = p->w64.Kp;
+    return p->v64;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bura_default_options(bura_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = BURA_PREC_MIXED;
+    opt->smoother_degree = 2;
+    opt->smoother_ratio = 8.0;
+    opt->max_iters = 200;
+    opt->max_outer = 12;
+    opt->inner_rtol = 1e-5;
+    opt->coarse_degree = 0;
+}
+
+int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, int k, const bura_options* opt,
+               bura_plan** out) {
+    if (!grid || !out) return BURA_EINVAL;
+    *out = nullptr;
+    if (grid->dim != 2 && grid->dim != 3) return BURA_EINVAL;
+    if (grid->coef_kind != BURA_COEF_CONSTANT && grid->coef_kind != BURA_COEF_FACES) return BURA_EINVAL;
+    if (!(alpha > 0 && alpha < 1) || k < 1 || k > BURA_MAX_K) return BURA_EINVAL;
+    const int dim = grid->dim;
+    long long N = 1;
+    for (int a = 0; a < dim; ++a) {
+        if (grid->n[a] < 1) return BURA_EINVAL;
+        N *= grid->n[a];
+    }
+    const bool var = grid->coef_kind == BURA_COEF_FACES;
+    if (var && !faces) return BURA_EINVAL;
+    if ((long long)N * 16 >= (1LL << 31)) return BURA_ERANGE;
+    bura_options o;
+    bura_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != BURA_PREC_FP64 && o.precision != BURA_PREC_MIXED) return BURA_EINVAL;
+    if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio > 1) || o.max_iters < 1 ||
+        o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000)
+        return BURA_EINVAL;
+
+    bura_plan* p = new (std::nothrow) bura_plan();
+    if (!p) return BURA_ENOMEM;
+    auto fail = [&](int rc) { bura_destroy(p); return rc; };
+    p->dim = dim;
+    p->var = var;
+    p->k = k;
+    p->K = k + 1;
+    p->alpha = alpha;
+    p->opt = o;
+    p->c.assign(p->K, 0.0);
+    p->d.assign(p->K, 0.0);
+    int rc = bura_rational(alpha, k, p->c.data(), p->d.data(), &p->E);
+    if (rc != BURA_OK) return fail(rc);
+
+    // fine level
+    HostLevel h0;
+    h0.n[0] = grid->n[0];
+    h0.n[1] = grid->n[1];
+    h0.n[2] = dim == 3 ? grid->n[2] : 1;
+    h0.N = N;
+    for (int a = 0; a < 3; ++a) h0.h[a] = 1.0 / (h0.n[a] + 1);
+    if (var) {
+        const size_t sz[3] = {(size_t)h0.n[2] * h0.n[1] * (h0.n[0] + 1), (size_t)h0.n[2] * (h0.n[1] + 1) * h0.n[0],
+                              (size_t)(h0.n[2] + 1) * h0.n[1] * h0.n[0]};
+        for (int a = 0; a < dim; ++a) {
+            if (!faces[a]) return fail(BURA_EINVAL);
+            h0.a[a].assign(faces[a], faces[a] + sz[a]);
+            for (double v : h0.a[a])
+                if (!(v > 0) || !std::isfinite(v)) return fail(BURA_EINVAL);
+        }
+    }
+    p->Lambda = gershgorin(h0, dim, var);
+    p->hl.push_back(h0);
+    for (;;) {  // coarsen while every size is odd and >= 3
+        const HostLevel& f = p->hl.back();
+        bool ok = true;
+        for (int a = 0; a < dim; ++a) ok = ok && (f.n[a] >= 3) && (f.n[a] % 2 == 1);
+        if (!ok) break;
+        HostLevel c;
+        for (int a = 0; a < 3; ++a) c.n[a] = (a < dim) ? (f.n[a] - 1) / 2 : 1;
+        c.N = (long long)c.n[0] * c.n[1] * c.n[2];
+        for (int a = 0; a < 3; ++a) c.h[a] = 1.0 / (c.n[a] + 1);
+        if (var) coarsen_faces(f, c, dim);
+        p->hl.push_back(std::move(c));
+    }
+    for (auto& h : p->hl) {
+        for (int a = 0; a < 3; ++a) h.w[a] = (a < dim) ? 1.0 / (h.h[a] * h.h[a] * p->Lambda) : 0.0;
+        level_bounds(h, dim, var, p->Lambda);
+    }
+    p->lambda_lo = p->hl[0].lmin * (1.0 - 1e-12);
+
+    if (cudaGetDevice(&p->dev) != cudaSuccess) return fail(BURA_ECUDA);
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess || nsm <= 0)
+        return fail(BURA_ECUDA);
+    p->nsm = nsm;
+
+    rc = build_work<double>(p, p->w64);
+    if (rc != BURA_OK) return fail(rc);
+    if (o.precision == BURA_PREC_MIXED) {
+        rc = build_work<float>(p, p->w32);
+        if (rc != BURA_OK) return fail(rc);
+    }
+    const size_t v64b = (size_t)N * p->w64.Kp * sizeof(double);
+    if ((rc = dalloc(p, &p->v64, v64b)) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->r64, v64b)) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->partial, (size_t)nsm * 8 * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    {
+        std::vector<double> cc(KMAXP, 0.0);
+        for (int j = 0; j < p->K; ++j) cc[j] = p->c[j];
+        if (cudaMemcpy(p->cdev, cc.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(BURA_ECUDA);
+        Scal so;
+        std::memset(&so, 0, sizeof(so));
+        for (int j = 0; j < p->K; ++j) so.dsh[j] = p->d[j];
+        if (cudaMemcpy(p->scal_outer, &so, sizeof(Scal), cudaMemcpyHostToDevice) != cudaSuccess) return fail(BURA_ECUDA);
+    }
+    if (cudaMallocHost(&p->hscal, sizeof(Scal)) != cudaSuccess) { p->hscal = nullptr; return fail(BURA_ENOMEM); }
+    if (cudaMallocHost(&p->hbuf, 4 * KMAXP * sizeof(double)) != cudaSuccess) { p->hbuf = nullptr; return fail(BURA_ENOMEM); }
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(BURA_ECUDA);
+    p->st.Lambda = p->Lambda;
+    p->st.E = p->E;
+    p->st.k = k;
+    p->st.levels = (int)p->hl.size();
+    p->st.lambda_lo = p->lambda_lo;
+    *out = p;
+    return BURA_OK;
+}
+
+int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* stream) {
+    if (!p || !f || !u) return BURA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = solve_core(p, f, tol, s);
+    if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
+    int Kp = 0;
+    const double* v = solution_vectors(p, &Kp);
+    launch_weighted_sum(p->hl[0].N, Kp, p->K, v, p->cdev, u, s);
+    CKL();
+    return rc;
+}
+
+int bura_solve_host(bura_plan* p, const double* f, double* u, double tol, void* stream) {
+    if (!p || !f || !u) return BURA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t nb = (size_t)p->hl[0].N * sizeof(double);
+    CK(cudaSetDevice(p->dev));
+    if (!p->fdev) {
+        CA(dalloc(p, &p->fdev, nb));
+        CA(dalloc(p, &p->udev, nb));
+    }
+    CK(cudaMemcpyAsync(p->fdev, f, nb, cudaMemcpyHostToDevice, s));
+    int rc = bura_solve(p, p->fdev, p->udev, tol, stream);
+    if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
+    CK(cudaMemcpyAsync(u, p->udev, nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, void* stream) {
+    if (!p || !f || !V) return BURA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rc = solve_core(p, f, tol, s);
+    if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
+    int Kp = 0;
+    const double* v = solution_vectors(p, &Kp);
+    launch_gather_systems(p->hl[0].N, Kp, p->K, v, V, s);
+    CKL();
+    return rc;
+}
+
+int bura_apply_shifted(bura_plan* p, const double* x, double* y, void* stream) {
+    if (!p || !x || !y) return BURA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(p->dev));
+    const long long N = p->hl[0].N;
+    launch_scatter_systems(N, p->w64.Kp, p->K, x, p->v64, s);
+    Ops<double>::apply_shifted(p->w64.g[0], p->w64.L[0], p->dim, p->var, p->v64, p->r64, p->w64.dsh, s);
+    launch_gather_systems(N, p->w64.Kp, p->K, p->r64, y, s);
+    CKL();
+    return BURA_OK;
+}
+
+int bura_get_rational(const bura_plan* p, double* c, double* d, double* E) {
+    if (!p || !c || !d) return BURA_EINVAL;
+    for (int j = 0; j < p->K; ++j) { c[j] = p->c[j]; d[j] = p->d[j]; }
+    if (E) *E = p->E;
+    return BURA_OK;
+}
+
+int bura_get_stats(const bura_plan* p, bura_stats* st) {
+    if (!p || !st) return BURA_EINVAL;
+    *st = p->st;
+    return BURA_OK;
+}
+
+int bura_destroy(bura_plan* p) {
+    if (!p) return BURA_OK;
+    cudaSetDevice(p->dev);
+    for (void* q : p->allocs) cudaFree(q);
+    if (p->hscal) cudaFreeHost(p->hscal);
+    if (p->hbuf) cudaFreeHost(p->hbuf);
+    delete p;
+    return BURA_OK;
+}
+
+const char* bura_strerror(int status) {
+    switch (status) {
+        case BURA_OK: return "success";
+        case BURA_EINVAL: return "invalid argument";
+        case BURA_ENOMEM: return "out of memory";
+        case BURA_EREMEZ: return "rational approximation did not converge";
+        case BURA_ENOTSPD: return "CG breakdown (operator not SPD or non-finite values)";
+        case BURA_ENOCONV: return "tolerance not reached within the iteration caps";
+        case BURA_ETIMEOUT: return "device-side wait timed out";
+        case BURA_ECUDA: return "CUDA runtime error";
+        case BURA_ERANGE: return "size above the supported maximum";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,241 @@
+"""GPU parity of the CUDA path (through the C ABI) against the oracle.
+
+Tolerances (written out per test):
+  * operator apply (FP64): 1e-14 relative;
+  * FP64 solve: ||u - u_r|| / ||u_r|| <= 1e-10 with u_r the exact BURA value of eq. (Rgeneral);
+  * mixed FP32/FP64 solve at tol: ||u - u_r|| / ||u_r|| <= tol.
+The library's stopping rule bounds ||u - u_r|| by tol * ||f|| and ||u_r|| >= (1 - E) ||f|| on these
+operators (spec(A) in (0,1]), so the solve tolerance is the parity tolerance.
+"""
+import numpy as np
+import pytest
+
+from oracle import direct, exact, operators, tables
+from paper_1612_04846_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1612_04846_gb300 import build_lib, bura
+    build_lib.build(verbose=False)
+    return bura
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _opts(lib, precision, **kw):
+    o = lib.bura_default_options()
+    o.precision = precision
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _np_shape(shape):
+    return tuple(reversed(shape))  # (nx, ny[, nz]) -> numpy (.., ny, nx)
+
+
+def _solve(lib, shape, alpha, k, f, tol, precision, faces=None, **kw):
+    plan = lib.bura_setup(shape, alpha, k, faces=faces, options=_opts(lib, precision, **kw))
+    try:
+        fd = torch.from_numpy(f).cuda()
+        ud = torch.zeros_like(fd)
+        rc = lib.bura_solve(plan, fd, ud, tol)
+        torch.cuda.synchronize()
+        st = lib.bura_get_stats(plan)
+        c, d, E = lib.bura_get_rational(plan, k)
+        return ud.cpu().numpy(), st, rc, (c, d, E)
+    finally:
+        lib.bura_destroy(plan)
+
+
+# ------------------------------------------------------------------ the multi-shift operator
+@pytest.mark.parametrize("shape,var", [((31, 31), False), ((64, 64), False), ((17, 9), False), ((1, 1), False),
+                                       ((7, 7, 7), False), ((15, 9, 7), False), ((15, 15, 15), True),
+                                       ((33, 17), True), ((5, 1, 3), True)])
+def test_apply_shifted_matches_sparse_operator(lib, shape, var):
+    """y_j = (A - d_j I) x_j (FP64 kernel) equals the oracle's assembled scaled matrix (1e-14)."""
+    k = 5
+    nps = _np_shape(shape)
+    faces = W.block_lognormal_faces(nps, 2, 1e-2, 1.0, 11) if var else None
+    plan = lib.bura_setup(shape, 0.5, k, faces=faces, options=_opts(lib, lib.BURA_PREC_FP64))
+    try:
+        A, _ = operators.scaled_matrix(nps, faces)
+        c, d, _ = lib.bura_get_rational(plan, k)
+        N = A.shape[0]
+        rng = np.random.default_rng(5)
+        X = rng.standard_normal((k + 1, N))
+        Y = torch.zeros((k + 1, N), dtype=torch.float64, device="cuda")
+        lib.bura_apply_shifted(plan, torch.from_numpy(X).cuda(), Y)
+        Y = Y.cpu().numpy()
+        for j in range(k + 1):
+            ref = A @ X[j] - d[j] * X[j]
+            assert _rel(Y[j], ref) < 1e-14, j
+    finally:
+        lib.bura_destroy(plan)
+
+
+# ------------------------------------------------------------------ FP64 path
+@pytest.mark.parametrize("shape,alpha,k", [((64, 64), 0.5, 5), ((63, 63), 0.25, 7), ((127, 127), 0.75, 7),
+                                           ((31, 31), 0.1, 9), ((33, 17), 0.9, 6), ((255, 255), 0.5, 8)])
+def test_fp64_solve_matches_exact_bura_2d(lib, shape, alpha, k):
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 0)
+    u, st, rc, (c, d, E) = _solve(lib, shape, alpha, k, f, 1e-11, lib.BURA_PREC_FP64)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(alpha, k)
+    ur = exact.bura_value(nps, f, ref["c"], ref["d"])
+    assert _rel(u, ur) <= 1e-10, (st, _rel(u, ur))
+    assert st["err_bound"] <= 1e-11 * 1.0001
+
+
+@pytest.mark.parametrize("shape", [(15, 15, 15), (31, 31, 31), (7, 15, 31)])
+def test_fp64_solve_matches_exact_bura_3d(lib, shape):
+    nps = _np_shape(shape)
+    f = W.rhs_normal(nps, 3)
+    u, st, rc, _ = _solve(lib, shape, 0.5, 9, f, 1e-11, lib.BURA_PREC_FP64)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(0.5, 9)
+    assert _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"])) <= 1e-10
+
+
+@pytest.mark.parametrize("shape,alpha,k", [((15, 15, 15), 0.5, 9), ((31, 15), 0.25, 5)])
+def test_fp64_solve_variable_coefficients_matches_sparse_direct(lib, shape, alpha, k):
+    nps = _np_shape(shape)
+    faces = W.block_lognormal_faces(nps, 4, 1e-2, 1.0, 2)
+    f = W.rhs_normal(nps, 4)
+    u, st, rc, _ = _solve(lib, shape, alpha, k, f, 1e-11, lib.BURA_PREC_FP64, faces=faces)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(alpha, k)
+    A, _ = operators.scaled_matrix(nps, faces)
+    assert _rel(u, direct.bura_sparse(A, f, ref["c"], ref["d"])) <= 1e-10
+
+
+def test_fp64_each_system_matches(lib):
+    """bura_solve_systems: every v_j = (A - d_j I)^{-1} f separately (FP64, 1e-9 relative each)."""
+    shape, alpha, k = (63, 63), 0.5, 5
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 9)
+    plan = lib.bura_setup(shape, alpha, k, options=_opts(lib, lib.BURA_PREC_FP64))
+    try:
+        V = torch.zeros((k + 1, f.size), dtype=torch.float64, device="cuda")
+        lib.bura_solve_systems(plan, torch.from_numpy(f).cuda(), V, 1e-11)
+        V = V.cpu().numpy()
+        c, d, _ = lib.bura_get_rational(plan, k)
+        ref = exact.bura_components(nps, f, d)
+        for j in range(k + 1):
+            # ||e_j|| <= ||r_j|| / (lambda_lo - d_j) <= tol ||f|| / (K c_j) and ||v_j|| >= ||f|| / (1 - d_j)
+            assert _rel(V[j], ref[j]) <= 1e-11 * (1 - d[j]) / ((k + 1) * c[j]) + 1e-12, j
+    finally:
+        lib.bura_destroy(plan)
+
+
+# ------------------------------------------------------------------ mixed path
+@pytest.mark.parametrize("shape,alpha,k,tol", [((64, 64), 0.5, 5, 1e-6), ((127, 127), 0.25, 7, 1e-6),
+                                               ((255, 255), 0.75, 7, 1e-6), ((127, 127), 0.5, 7, 1e-8),
+                                               ((31, 31, 31), 0.5, 9, 1e-6)])
+def test_mixed_solve_within_tolerance(lib, shape, alpha, k, tol):
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 1)
+    u, st, rc, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(alpha, k)
+    err = _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"]))
+    assert err <= tol, (err, st)
+
+
+def test_mixed_variable_3d_within_tolerance(lib):
+    shape = (31, 31, 31)
+    nps = _np_shape(shape)
+    faces = W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 2)
+    f = W.rhs_normal(nps, 3)
+    u, st, rc, _ = _solve(lib, shape, 0.5, 9, f, 1e-6, lib.BURA_PREC_MIXED, faces=faces)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(0.5, 9)
+    A, _ = operators.scaled_matrix(nps, faces)
+    assert _rel(u, direct.bura_sparse(A, f, ref["c"], ref["d"])) <= 1e-6
+
+
+# ------------------------------------------------------------------ full size of the bench workload
+@pytest.mark.parametrize("alpha", [0.25, 0.5, 0.75])
+def test_full_size_1023_mixed_and_fp64(lib, alpha):
+    """The bench workload (2D 1023^2, k = 7, f ~ U[-1,1] seed 1): every output against the exact
+    BURA value from the sine transform, mixed at 1e-6 and FP64 at 1e-10."""
+    shape, k = (1023, 1023), 7
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 1)
+    ref = tables.entry(alpha, k)
+    ur = exact.bura_value(nps, f, ref["c"], ref["d"])
+    u, st, rc, _ = _solve(lib, shape, alpha, k, f, 1e-6, lib.BURA_PREC_MIXED)
+    assert rc == lib.BURA_OK and _rel(u, ur) <= 1e-6, st
+    u, st, rc, _ = _solve(lib, shape, alpha, k, f, 1e-11, lib.BURA_PREC_FP64)
+    assert rc == lib.BURA_OK and _rel(u, ur) <= 1e-10, st
+
+
+# ------------------------------------------------------------------ method-level properties
+def test_bura_error_bound_against_exact_fractional(lib):
+    """Lemma l:BURAerror (gamma = 1): ||u - A^{-alpha} f||_A <= E ||f||_{A^{-1}} + solver error."""
+    shape, alpha, k = (127, 127), 0.5, 6
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 7)
+    u, st, rc, (c, d, E) = _solve(lib, shape, alpha, k, f, 1e-10, lib.BURA_PREC_FP64)
+    A, _ = operators.scaled_matrix(nps)
+    diff = u - exact.fractional(nps, f, alpha)
+    lhs = np.sqrt(diff @ (A @ diff))
+    rhs = E * np.sqrt(f @ exact.apply_function(nps, f, lambda lam: 1.0 / lam))
+    assert lhs <= rhs * (1 + 1e-6)
+
+
+def test_host_entry_point_equals_device_entry_point(lib):
+    shape, alpha, k = (127, 127), 0.5, 5
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 2)
+    plan = lib.bura_setup(shape, alpha, k, options=_opts(lib, lib.BURA_PREC_MIXED))
+    try:
+        uh = np.zeros_like(f)
+        lib.bura_solve_host(plan, f, uh, 1e-6)
+        fd = torch.from_numpy(f).cuda()
+        ud = torch.zeros_like(fd)
+        lib.bura_solve(plan, fd, ud, 1e-6)
+        torch.cuda.synchronize()
+        assert np.array_equal(uh, ud.cpu().numpy())  # deterministic reductions: bitwise equal
+    finally:
+        lib.bura_destroy(plan)
+
+
+def test_zero_rhs_and_single_point(lib):
+    for shape in ((1, 1), (2, 2), (1, 5, 1)):
+        nps = _np_shape(shape)
+        for prec in (lib.BURA_PREC_FP64, lib.BURA_PREC_MIXED):
+            u, st, rc, _ = _solve(lib, shape, 0.5, 3, np.zeros(int(np.prod(shape))), 1e-8, prec)
+            assert rc == lib.BURA_OK and np.all(u == 0)
+            f = W.rhs_uniform(nps, 3)
+            u, st, rc, _ = _solve(lib, shape, 0.5, 3, f, 1e-9, prec)
+            ref = tables.entry(0.5, 3)
+            A, _ = operators.scaled_matrix(nps)
+            assert _rel(u, direct.bura_dense(A, f, ref["c"], ref["d"])) <= 1e-9
+
+
+def test_iteration_cap_reports_enoconv(lib):
+    shape = (127, 127)
+    f = W.rhs_uniform(_np_shape(shape), 4)
+    u, st, rc, _ = _solve(lib, shape, 0.5, 5, f, 1e-12, lib.BURA_PREC_FP64, max_iters=1)
+    assert rc == lib.BURA_ENOCONV and st["iters"] == 1
+
+
+def test_smallest_and_largest_tabulated_k(lib):
+    shape = (63, 63)
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 5)
+    for k in (1, 10):
+        u, st, rc, _ = _solve(lib, shape, 0.5, k, f, 1e-11, lib.BURA_PREC_FP64)
+        ref = tables.entry(0.5, k)
+        assert rc == lib.BURA_OK and _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"])) <= 1e-10

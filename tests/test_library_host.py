@@ -1,0 +1,108 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared entry point, validates
+arguments on the host, and its host-side rational approximation matches the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import tables
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1612_04846_gb300 import build_lib, bura
+    build_lib.build(verbose=False)
+    return bura
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(bura_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import ctypes
+    L = ctypes.CDLL(lib.LIB_PATH)
+    declared = _declared_symbols()
+    assert {"bura_setup", "bura_solve", "bura_destroy", "bura_rational"} <= declared
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert set(lib.EXPORTED) >= declared
+
+
+def test_default_options_and_strerror(lib):
+    o = lib.bura_default_options()
+    assert o.precision == lib.BURA_PREC_MIXED and o.smoother_degree == 2 and o.max_iters > 0
+    for code in range(0, -9, -1):
+        assert lib.bura_strerror(code) != "unknown status"
+    assert lib.bura_strerror(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("shape,alpha,k", [((0, 5), 0.5, 5), ((5, 5), 0.0, 5), ((5, 5), 1.0, 5),
+                                           ((5, 5), 0.5, 0), ((5, 5), 0.5, 13), ((5, 5, 5, 5), 0.5, 5)])
+def test_setup_rejects_bad_arguments_on_the_host(lib, shape, alpha, k):
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup(shape, alpha, k)
+    assert ei.value.code == lib.BURA_EINVAL
+
+
+def test_setup_rejects_nonpositive_coefficients(lib):
+    from paper_1612_04846_gb300 import workloads as W
+    faces = list(W.constant_faces((4, 5)))
+    faces[0] = faces[0].copy()
+    faces[0][1, 2] = 0.0
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup((5, 4), 0.5, 3, faces=faces)
+    assert ei.value.code == lib.BURA_EINVAL
+
+
+def test_setup_rejects_oversized_grid(lib):
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup((2048, 2048, 64), 0.5, 5)
+    assert ei.value.code == lib.BURA_ERANGE
+
+
+@pytest.mark.parametrize("alpha,k", [(a, k) for a in (0.1, 0.25, 0.5, 0.75, 0.9) for k in (1, 3, 5, 7, 9, 10)])
+def test_library_rational_matches_oracle(lib, alpha, k):
+    """The library's double-precision Remez (factored form + Newton) reproduces the oracle's
+    multi-precision Algorithm 1: E, c_j, d_j to 1e-11 relative."""
+    try:
+        ref = tables.entry(alpha, k)
+    except KeyError:
+        pytest.skip("no oracle table entry")
+    c, d, E = lib.bura_rational(alpha, k)
+    assert abs(E - ref["E"]) <= 1e-11 * ref["E"]
+    assert d[0] == 0.0
+    for a, b in zip(c, ref["c"]):
+        assert abs(a - b) <= 1e-11 * abs(b)
+    for a, b in zip(d[1:], ref["d"][1:]):
+        assert abs(a - b) <= 1e-11 * abs(b)
+
+
+def test_library_rational_edge_alphas(lib):
+    """Outside the tabulated alphas: positivity, ordering, c_0 = E and the Stahl asymptotics."""
+    import math
+    for alpha in (0.02, 0.05, 0.95, 0.98):
+        for k in (1, 6, 12):
+            c, d, E = lib.bura_rational(alpha, k)
+            assert np.all(c > 0) and d[0] == 0 and np.all(np.diff(d) < 0)
+            assert abs(c[0] - E) <= 1e-12 * E
+            if k >= 6:
+                g = 1 - alpha
+                stahl = 4 ** (1 + g) * math.sin(math.pi * g) * math.exp(-2 * math.pi * math.sqrt(g * k))
+                assert 0.6 < stahl / E < 1.8, (alpha, k, stahl, E)
+
+
+def test_library_rational_rejects_bad_input(lib):
+    for a, k in ((0.0, 5), (1.0, 5), (0.5, 0), (0.5, 13)):
+        with pytest.raises(lib.BuraError) as ei:
+            lib.bura_rational(a, k)
+        assert ei.value.code == lib.BURA_EINVAL
