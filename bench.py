@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput of the BURA fractional solve on one or more GB300s (one process per GPU).
+
+Workload (one "step" = one complete BURA solve through the C ABI):
+  2D 5-point finite-difference Laplacian, 1023 x 1023 interior grid (N = 1,046,529), homogeneous
+  Dirichlet, A = h^2 Atilde / 8, BURA degree k = 7 (8 shifted systems), alpha cycling through
+  0.25 / 0.5 / 0.75, f i.i.d. uniform[-1, 1] (PCG64 seed 1 + 1000 * rank), FP32 multigrid-PCG inner
+  solves in FP64 iterative refinement, tolerance 1e-6 on ||u - u_r|| / ||f||.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+For N > 1 run under torch.distributed.run; ranks solve independent right-hand sides (weak scaling,
+no collective on the data path) and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BURA solves/s and Gunknown·shifts/s at 1e-6 rel err; %HBM peak; p50/p99 ms"
+SHAPE = (1023, 1023)
+K_DEG = 7
+ALPHAS = (0.25, 0.5, 0.75)
+TOL = 1e-6
+WORKLOAD = ("2D 5-point FD Laplacian 1023x1023 (N=1046529), Dirichlet, A scaled by 8/h^2, "
+            "alpha in {0.25,0.5,0.75}, k=7, f~U[-1,1] seed 1, FP32 MG-PCG inner + FP64 refinement, tol 1e-6")
+CSRC = os.path.join(ROOT, "paper_1612_04846_gb300", "csrc")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=6)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
+    ap.add_argument("--profile-steps", type=int, default=6, help="solves timed kernel by kernel for the roofline")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed helpers (CPU-testable)
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def rank_seed(rank):
+    """Each rank solves its own right-hand side (independent problems, weak scaling)."""
+    return 1 + 1000 * rank
+
+
+def reduce_max(value, device=None):
+    """Maximum of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def aggregate(steps_per_rank, world, max_seconds):
+    """Whole-job throughput: units processed by all ranks / max-over-ranks time."""
+    return steps_per_rank * world / max_seconds
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sources_sha():
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, fn), "rb") as fh:
+            h.update(fn.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it matches these sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("sources_sha") != sources_sha():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    return None if ent is None else float(ent["dram_bytes_per_launch_full_size"])
+
+
+# ------------------------------------------------------------------ oracle leg (CPU)
+def oracle_timing(budget_s, seed, steps=None):
+    """The oracle (exact sine-transform BURA value, oracle/exact.py) on the host cores.
+    Returns (solves/s, samples, seconds)."""
+    from oracle import exact, tables
+    from paper_1612_04846_gb300 import workloads as W
+    nps = tuple(reversed(SHAPE))
+    f = W.rhs_uniform(nps, seed)
+    ents = {a: tables.entry(a, K_DEG) for a in ALPHAS}
+    n, t0 = 0, time.perf_counter()
+    times = []
+    while True:
+        a = ALPHAS[n % len(ALPHAS)]
+        s0 = time.perf_counter()
+        exact.bura_value(nps, f, ents[a]["c"], ents[a]["d"])
+        times.append(time.perf_counter() - s0)
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el >= budget_s):
+            break
+    return n / sum(times), n, sum(times), times
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(max(0, args.warmup)):
+        oracle_timing(0, rank_seed(0), steps=1)
+    val, n, secs, times = oracle_timing(0, rank_seed(0), steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * secs / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": 1, "parallelism": "none (host oracle)"},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full solves of the workload by the oracle's DST-I eigenbasis "
+                                       "evaluation (scipy.fft, 1 worker)" % n},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1612_04846_gb300 import build_lib, bura
+    from paper_1612_04846_gb300 import workloads as W
+    build_lib.build(verbose=False)
+
+    nps = tuple(reversed(SHAPE))
+    N = int(np.prod(SHAPE))
+    f_host = W.rhs_uniform(nps, rank_seed(rank))
+    f = torch.from_numpy(f_host).to(dev)
+    u = torch.zeros_like(f)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_plan(alpha, precision):
+        o = bura.bura_default_options()
+        o.precision = precision
+        return bura.bura_setup(SHAPE, alpha, K_DEG, options=o)
+
+    plans = {a: make_plan(a, bura.BURA_PREC_MIXED) for a in ALPHAS}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step(i, plan_set, tol=TOL, out=u):
+        rc = bura.bura_solve(plan_set[ALPHAS[i % len(ALPHAS)]], f, out, tol, stream)
+        if rc != bura.BURA_OK:
+            raise RuntimeError("solve did not converge: %s" % bura.bura_strerror(rc))
+
+    for i in range(args.warmup):
+        step(i, plans)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, L2 flushed between solves (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step(i, plans)
+        ev[i][1].record(stream)
+        launches += bura.bura_get_stats(plans[ALPHAS[i % len(ALPHAS)]])["launches"]
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    per = [a.elapsed_time(b) for a, b in ev]  # ms
+    total_s = sum(per) / 1e3
+    max_s = reduce_max(total_s, dev)
+    value = aggregate(args.steps, ws, max_s)
+    per_sorted = sorted(per)
+    p50 = per_sorted[len(per) // 2]
+    p99 = per_sorted[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
+    per_alpha = {}
+    for j, a in enumerate(ALPHAS):
+        sel = per[j::len(ALPHAS)]
+        st = bura.bura_get_stats(plans[a])
+        per_alpha["%.2f" % a] = {"ms_mean": sum(sel) / len(sel), "inner_iters": st["iters"], "outer": st["outer"],
+                                 "err_bound": st["err_bound"]}
+
+    # ---- kernel-level timing of the same solves (events around every fine-level launch)
+    prof_plan = plans[0.5]
+    bura.bura_set_profiling(prof_plan, 1)
+    for i in range(args.profile_steps):
+        flush.zero_()
+        bura.bura_solve(prof_plan, f, u, TOL, stream)
+    torch.cuda.synchronize()
+    prof = bura.bura_get_profile(prof_plan)
+    bura.bura_set_profiling(prof_plan, 0)
+    prof_total = sum(p["ms"] for p in prof)
+    dom = max(prof, key=lambda p: p["ms"])
+    peak, peak_kind = measured_hbm_peak()
+    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+    traffic = ncu_traffic(dom["name"])
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": traffic, "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                "ms_per_launch": dom["ms"] / dom["launches"], "share_of_fine_kernel_time": dom["ms"] / prof_total,
+                "kernels": {p["name"]: {"launches_per_solve": p["launches"] / args.profile_steps,
+                                        "ms_per_launch": p["ms"] / p["launches"],
+                                        "GBps": p["bytes"] / (p["ms"] / 1e3) / 1e9} for p in prof}}
+
+    # ---- FP64 one-system-at-a-time-precision comparison: plain FP64 multi-shift MG-PCG
+    p64 = make_plan(0.5, bura.BURA_PREC_FP64)
+    n64 = max(3, args.steps // 10)
+    bura.bura_solve(p64, f, u, TOL, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t64 = 0.0
+    for i in range(n64):
+        flush.zero_()
+        e0.record(stream)
+        bura.bura_solve(p64, f, u, TOL, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1)
+    fp64_solves = n64 / (t64 / 1e3)
+    bura.bura_destroy(p64)
+
+    # ---- end to end through the host-buffer entry point (H2D of f and D2H of u inside the timing)
+    fh = torch.from_numpy(f_host).pin_memory().numpy()
+    uh = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    ne2e = max(3, args.steps // 2)
+    for i in range(2):
+        bura.bura_solve_host(plans[ALPHAS[i % 3]], fh, uh, TOL, stream)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ne2e):
+        bura.bura_solve_host(plans[ALPHAS[i % 3]], fh, uh, TOL, stream)
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e = {"value": aggregate(ne2e, ws, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8, "entry_point": "bura_solve_host"}
+
+    # ---- CPU baseline: the oracle on this host (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import exact, tables
+        val, n, secs, _ = oracle_timing(12.0, rank_seed(0))
+        # parity of this run against the oracle on the same input (not part of the timing)
+        errs = {}
+        for a in ALPHAS:
+            bura.bura_solve(plans[a], f, u, TOL, stream)
+            torch.cuda.synchronize()
+            ent = tables.entry(a, K_DEG)
+            ur = exact.bura_value(nps, f_host, ent["c"], ent["d"])
+            errs["%.2f" % a] = float(np.linalg.norm(u.cpu().numpy() - ur) / np.linalg.norm(ur))
+        cpu = {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "%d full solves of the workload (%.1f s) by the oracle's DST-I eigenbasis evaluation "
+                         "of sum_j c_j (A - d_j I)^-1 f (scipy.fft, 1 worker)" % (n, secs),
+               "rel_err_gpu_vs_oracle": errs}
+
+    for a in ALPHAS:
+        bura.bura_destroy(plans[a])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "global_batch": ws, "grid": list(SHAPE), "k": K_DEG,
+                           "alphas": list(ALPHAS), "tol": TOL, "precision": "fp32 inner / fp64 refinement",
+                           "l2": "flushed (256 MB write) between timed solves, outside the events",
+                           "parallelism": "replicas: one independent solve per rank"},
+                "Gunknown_shifts_per_s": value * N * (K_DEG + 1) / 1e9,
+                "p50_ms": p50, "p99_ms": p99, "per_alpha": per_alpha,
+                "fp64_path_solves_per_s": fp64_solves,
+                "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist.is_initialized():
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -86,7 +86,16 @@ typedef struct {
     double rel_res[BURA_MAX_K + 1];  /* final ||f - (A - d_j I) v_j|| / ||f|| per system */
     double err_bound;                /* sum_j c_j ||r_j|| / ((lambda_lo - d_j) ||f||): bound on ||u - u_r|| / ||f|| */
     double lambda_lo;                /* lower bound on lambda_min(A) used by the stopping test */
+    long long launches;              /* CUDA kernels launched by the last solve */
 } bura_stats;
+
+/* Per-kernel timing of the fine-level kernels (see bura_set_profiling). */
+typedef struct {
+    const char* name;   /* static kernel name, e.g. "cheb_step_f32" */
+    long long launches; /* timed launches since profiling was enabled */
+    double ms;          /* summed CUDA-event durations of those launches */
+    double bytes;       /* summed algorithmic bytes (data a launch must read and write at least) */
+} bura_kernel_prof;
 
 typedef struct bura_plan bura_plan;
 
@@ -154,6 +163,19 @@ int bura_get_rational(const bura_plan* plan, double* c, double* d, double* E);
 
 /* Statistics of the last solve (host struct). */
 int bura_get_stats(const bura_plan* plan, bura_stats* stats);
+
+/*
+ * Enable (1) or disable (0) per-kernel timing: every fine-level kernel launch of later solves is
+ * bracketed by CUDA events recorded on the solve stream, and its duration and algorithmic bytes are
+ * accumulated per kernel type.  Enabling resets the counters.  Costs one event pair per launch.
+ */
+int bura_set_profiling(bura_plan* plan, int enable);
+
+/*
+ * Copy up to max_entries per-kernel records (kernel types with at least one timed launch) into the
+ * host array out; *n_out receives the number written.
+ */
+int bura_get_profile(const bura_plan* plan, int max_entries, bura_kernel_prof* out, int* n_out);
 
 /* Frees every device and host resource of the plan (NULL is accepted). */
 int bura_destroy(bura_plan* plan);

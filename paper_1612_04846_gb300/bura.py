@@ -37,13 +37,18 @@ class bura_stats(C.Structure):
     _fields_ = [("Lambda", C.c_double), ("E", C.c_double), ("k", C.c_int), ("levels", C.c_int),
                 ("iters", C.c_int), ("outer", C.c_int), ("shift_iters", C.c_int * (BURA_MAX_K + 1)),
                 ("rel_res", C.c_double * (BURA_MAX_K + 1)), ("err_bound", C.c_double),
-                ("lambda_lo", C.c_double)]
+                ("lambda_lo", C.c_double), ("launches", C.c_longlong)]
 
     def to_dict(self):
         k = self.k
         return {"Lambda": self.Lambda, "E": self.E, "k": k, "levels": self.levels, "iters": self.iters,
                 "outer": self.outer, "shift_iters": list(self.shift_iters)[: k + 1],
-                "rel_res": list(self.rel_res)[: k + 1], "err_bound": self.err_bound, "lambda_lo": self.lambda_lo}
+                "rel_res": list(self.rel_res)[: k + 1], "err_bound": self.err_bound, "lambda_lo": self.lambda_lo,
+                "launches": self.launches}
+
+
+class bura_kernel_prof(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double), ("bytes", C.c_double)]
 
 
 class BuraError(RuntimeError):
@@ -77,10 +82,13 @@ def _lib():
         L.bura_get_rational.argtypes = [P, dp, dp, dp]
         L.bura_get_stats.argtypes = [P, C.POINTER(bura_stats)]
         L.bura_destroy.argtypes = [P]
+        L.bura_set_profiling.argtypes = [P, I]
+        L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
         L.bura_strerror.argtypes = [I]
         L.bura_strerror.restype = C.c_char_p
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
-                     "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy"):
+                     "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
+                     "bura_set_profiling", "bura_get_profile"):
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -195,10 +203,23 @@ def bura_get_stats(plan):
     return st.to_dict()
 
 
+def bura_set_profiling(plan, enable):
+    return _check(_lib().bura_set_profiling(plan, int(bool(enable))), "bura_set_profiling")
+
+
+def bura_get_profile(plan, max_entries=64):
+    """List of dicts {name, launches, ms, bytes} of the timed fine-level kernels."""
+    arr = (bura_kernel_prof * max_entries)()
+    n = C.c_int()
+    _check(_lib().bura_get_profile(plan, max_entries, arr, C.byref(n)), "bura_get_profile")
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+            for i in range(n.value)]
+
+
 def bura_destroy(plan):
     return _check(_lib().bura_destroy(plan), "bura_destroy")
 
 
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
-            "bura_strerror"]
+            "bura_strerror", "bura_set_profiling", "bura_get_profile"]

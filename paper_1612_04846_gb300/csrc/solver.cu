@@ -41,6 +41,28 @@ struct Work {
 
 int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
 
+// Kernel types for launch counting and per-kernel timing (fine level only).
+enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PROLONG, K_DOT, K_BCAST, K_RES64, K_CAST, K_CORR64,
+           K_WSUM, K_GATHER, K_NK };
+const char* const kNames[K_NK][2] = {
+    {"spmv_p_f64", "spmv_p_f32"},       {"cg_update_f64", "cg_update_f32"}, {"cheb_zero_f64", "cheb_zero_f32"},
+    {"cheb_step_f64", "cheb_step_f32"}, {"restrict_res_f64", "restrict_res_f32"},
+    {"prolong_add_f64", "prolong_add_f32"}, {"dot_f64", "dot_f32"}, {"broadcast_f64", "broadcast_f32"},
+    {"residual64", "residual64"},       {"cast_scaled", "cast_scaled"}, {"correct64", "correct64"},
+    {"weighted_sum", "weighted_sum"},   {"gather_systems", "gather_systems"}};
+
+struct Tracer {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // 2 per timed launch
+    struct Rec { int slot; double bytes; };
+    std::vector<Rec> pending;
+    long long n[2 * K_NK] = {0};
+    double ms[2 * K_NK] = {0};
+    double bytes[2 * K_NK] = {0};
+    long long launches = 0;  // every launch of the current solve
+};
+constexpr size_t kMaxTimed = 4096;
+
 }  // namespace
 
 struct bura_plan {
@@ -68,6 +90,7 @@ struct bura_plan {
     double* udev = nullptr;
     std::vector<void*> allocs;
     bura_stats st{};
+    Tracer tr;
 };
 
 namespace {
@@ -100,6 +123,34 @@ int dalloc(bura_plan* p, P** ptr, size_t bytes) {
         int rc_ = (expr);             \
         if (rc_ != BURA_OK) return rc_; \
     } while (0)
+
+// Count a launch; when profiling and the launch works on the fine level, bracket it by events.
+template <class F>
+void traced(bura_plan* p, int kid, bool is_f32, bool fine, double bytes, cudaStream_t s, F&& launch) {
+    Tracer& t = p->tr;
+    ++t.launches;
+    const bool rec = t.on && fine && t.pending.size() < kMaxTimed;
+    if (rec) cudaEventRecord(t.ev[2 * t.pending.size()], s);
+    launch();
+    if (rec) {
+        cudaEventRecord(t.ev[2 * t.pending.size() + 1], s);
+        t.pending.push_back({kid * 2 + (is_f32 ? 1 : 0), bytes});
+    }
+}
+
+// Fold the timed launches of the finished solve into the per-kernel totals (stream must be idle).
+void collect_trace(bura_plan* p) {
+    Tracer& t = p->tr;
+    for (size_t i = 0; i < t.pending.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]) == cudaSuccess) {
+            t.n[t.pending[i].slot] += 1;
+            t.ms[t.pending[i].slot] += ms;
+            t.bytes[t.pending[i].slot] += t.pending[i].bytes;
+        }
+    }
+    t.pending.clear();
+}
 
 Launch make_launch(int Kp, int W, long long N, int nsm) {
     Launch g;
@@ -332,6 +383,16 @@ int build_work(bura_plan* p, Work<T>& w) {
     return BURA_OK;
 }
 
+// Algorithmic bytes of `vec` multi-shift vectors of level l (K systems, not the padding) plus,
+// for variable coefficients, the face coefficients a stencil kernel reads.
+template <class T>
+double vbytes(const bura_plan* p, int l, double vec, bool stencil) {
+    const double N = (double)p->hl[l].N;
+    double b = vec * N * p->K * sizeof(T);
+    if (stencil && p->var) b += N * p->dim * sizeof(T);
+    return b;
+}
+
 // Symmetric V-cycle on level l for rhs b; returns the buffer holding the result.  With rz_fused
 // (level 0 only) the last smoothing step also forms r^T z and the CG beta of every system.
 template <class T>
@@ -342,42 +403,45 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     const Launch& g = w.g[l];
     const Lev& L = w.L[l];
     const int deg = w.deg[l];
+    const bool f32 = sizeof(T) == 4;
+    const bool fine = (l == 0);
     T* A = w.xa[l];
     T* B = w.xb[l];
     T* D = w.dd[l];
     Red none{p->partial, w.scal, nullptr, RED_NONE};
     Red beta{p->partial, w.scal, nullptr, RED_BETA};
-    if (l == nlev - 1) {  // coarsest: exact 1-point solve or a fixed Chebyshev polynomial
+    auto step = [&](T* xin, T* din, T* xout, T* dout, int m, bool c1, const Red& red) {
+        const double vec = 2.0 + (din ? 1.0 : 0.0) + (dout ? 1.0 : 0.0);
+        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, vec, true), s, [&] {
+            Ops<T>::cheb_step(g, L, dim, var, xin, din, b, xout, dout, ChebStep{c1 ? w.c1[l][m] : nullptr, w.c2[l][m]},
+                              w.dsh, red, s);
+        });
+    };
+    traced(p, K_CHEB0, f32, fine, vbytes<T>(p, l, 2.0, var), s, [&] {
         Ops<T>::cheb_zero(g, L, dim, var, b, A, ChebStep{w.c1[l][0], w.c2[l][0]}, w.dsh, s);
-        T* cur = A;
-        T* oth = B;
-        for (int m = 1; m < deg; ++m) {
-            Ops<T>::cheb_step(g, L, dim, var, cur, m == 1 ? cur : D, b, oth, m < deg - 1 ? D : nullptr,
-                              ChebStep{w.c1[l][m], w.c2[l][m]}, w.dsh, none, s);
-            std::swap(cur, oth);
-        }
-        if (rz_fused) Ops<T>::dot(g, L.N, b, cur, beta, s);
-        return cur;
-    }
-    // pre-smoothing from a zero initial guess
-    Ops<T>::cheb_zero(g, L, dim, var, b, A, ChebStep{w.c1[l][0], w.c2[l][0]}, w.dsh, s);
+    });
     T* cur = A;
     T* oth = B;
     for (int m = 1; m < deg; ++m) {
-        Ops<T>::cheb_step(g, L, dim, var, cur, m == 1 ? cur : D, b, oth, m < deg - 1 ? D : nullptr,
-                          ChebStep{w.c1[l][m], w.c2[l][m]}, w.dsh, none, s);
+        step(cur, m == 1 ? cur : D, oth, m < deg - 1 ? D : nullptr, m, true, none);
         std::swap(cur, oth);
     }
+    if (l == nlev - 1) {  // coarsest: exact 1-point solve or a fixed Chebyshev polynomial
+        if (rz_fused)
+            traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, cur, beta, s); });
+        return cur;
+    }
     // coarse-grid correction
-    Ops<T>::restrict_res(w.g[l + 1], L, w.L[l + 1], dim, var, cur, b, w.b[l + 1], w.dsh, s);
+    traced(p, K_RESTRICT, f32, fine, vbytes<T>(p, l, 2.0, true) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
+        Ops<T>::restrict_res(w.g[l + 1], L, w.L[l + 1], dim, var, cur, b, w.b[l + 1], w.dsh, s);
+    });
     T* ec = vcycle<T>(p, w, l + 1, w.b[l + 1], false, s);
-    Ops<T>::prolong_add(g, L, w.L[l + 1], dim, ec, cur, s);
+    traced(p, K_PROLONG, f32, fine, vbytes<T>(p, l, 2.0, false) + vbytes<T>(p, l + 1, 1.0, false), s,
+           [&] { Ops<T>::prolong_add(g, L, w.L[l + 1], dim, ec, cur, s); });
     // post-smoothing with the same polynomial (symmetric preconditioner)
     for (int m = 0; m < deg; ++m) {
         const bool last = (m == deg - 1);
-        Ops<T>::cheb_step(g, L, dim, var, cur, m == 0 ? nullptr : D, b, oth, last ? nullptr : D,
-                          ChebStep{m == 0 ? nullptr : w.c1[l][m], w.c2[l][m]}, w.dsh,
-                          (rz_fused && last) ? beta : none, s);
+        step(cur, m == 0 ? nullptr : D, oth, last ? nullptr : D, m, m != 0, (rz_fused && last) ? beta : none);
         std::swap(cur, oth);
     }
     return cur;
@@ -393,14 +457,17 @@ int pcg(bura_plan* p, Work<T>& w, int max_it, int* iters_out, cudaStream_t s) {
     Red rconv{p->partial, w.scal, nullptr, RED_CONV};
     T* pold = w.pa;
     T* pnew = w.pb;
+    const bool f32 = sizeof(T) == 4;
     T* z = vcycle<T>(p, w, 0, w.r, true, s);
     CKL();
     int it = 0;
     int status = BURA_ENOCONV;
     while (it < max_it) {
-        Ops<T>::spmv_p(g, L, p->dim, p->var, z, pold, pnew, w.q, ralpha, s);
+        traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s,
+               [&] { Ops<T>::spmv_p(g, L, p->dim, p->var, z, pold, pnew, w.q, ralpha, s); });
         std::swap(pold, pnew);
-        Ops<T>::cg_update(g, L.N, w.x, w.r, pold, w.q, rconv, s);
+        traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s,
+               [&] { Ops<T>::cg_update(g, L.N, w.x, w.r, pold, w.q, rconv, s); });
         CKL();
         ++it;
         CK(cudaMemcpyAsync(&p->hscal->nactive, &w.scal->nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -460,10 +527,12 @@ void finish_stats(bura_plan* p, const double* rr, double fnorm2) {
 int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     Work<double>& w = p->w64;
     const long long N = p->hl[0].N;
-    Ops<double>::broadcast(w.g[0], f, N, p->K, w.r, w.x, w.pa, s);
+    traced(p, K_BCAST, false, true, (double)N * 8 + vbytes<double>(p, 0, 3.0, false), s,
+           [&] { Ops<double>::broadcast(w.g[0], f, N, p->K, w.r, w.x, w.pa, s); });
     CKL();
     Red store{p->partial, w.scal, p->red_out, RED_STORE};
-    Ops<double>::dot(w.g[0], N, w.r, w.r, store, s);
+    traced(p, K_DOT, false, true, vbytes<double>(p, 0, 1.0, false), s,
+           [&] { Ops<double>::dot(w.g[0], N, w.r, w.r, store, s); });
     CKL();
     CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -499,7 +568,8 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     int rc = BURA_ENOCONV;
     int siters[KMAXP] = {0};
     for (;;) {
-        launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s);
+        traced(p, K_RES64, false, true, (double)N * 8 + vbytes<double>(p, 0, 2.0, true), s,
+               [&] { launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s); });
         CKL();
         CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -533,7 +603,8 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
         }
         CK(cudaMemcpyAsync(p->scale, hs, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(p->invscale, his, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s);
+        traced(p, K_CAST, false, true, vbytes<double>(p, 0, 1.0, false) + vbytes<float>(p, 0, 3.0, false), s,
+               [&] { launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s); });
         CKL();
         CA(init_scal(p, w.scal, thr, act, s));
         int it = 0;
@@ -541,7 +612,8 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
         if (irc == BURA_ENOTSPD) return irc;
         for (int j = 0; j < p->K; ++j) siters[j] += p->hscal->iters[j];
         total_it += it;
-        launch_correct64(g64, w.g[0], N, p->K, p->v64, w.x, p->scale, s);
+        traced(p, K_CORR64, false, true, vbytes<double>(p, 0, 2.0, false) + vbytes<float>(p, 0, 1.0, false), s,
+               [&] { launch_correct64(g64, w.g[0], N, p->K, p->v64, w.x, p->scale, s); });
         CKL();
         ++outer;
     }
@@ -555,6 +627,7 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
 int solve_core(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     if (!(tol > 0)) return BURA_EINVAL;
     CK(cudaSetDevice(p->dev));
+    p->tr.launches = 0;
     std::memset(p->st.shift_iters, 0, sizeof(p->st.shift_iters));
     std::memset(p->st.rel_res, 0, sizeof(p->st.rel_res));
     return p->opt.precision == BURA_PREC_FP64 ? solve_fp64(p, f, tol, s) : solve_mixed(p, f, tol, s);
@@ -707,8 +780,15 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     int Kp = 0;
     const double* v = solution_vectors(p, &Kp);
-    launch_weighted_sum(p->hl[0].N, Kp, p->K, v, p->cdev, u, s);
+    const double N = (double)p->hl[0].N;
+    traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s,
+           [&] { launch_weighted_sum(p->hl[0].N, Kp, p->K, v, p->cdev, u, s); });
     CKL();
+    p->st.launches = p->tr.launches;
+    if (p->tr.on) {
+        CK(cudaStreamSynchronize(s));
+        collect_trace(p);
+    }
     return rc;
 }
 
@@ -736,8 +816,14 @@ int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, voi
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     int Kp = 0;
     const double* v = solution_vectors(p, &Kp);
-    launch_gather_systems(p->hl[0].N, Kp, p->K, v, V, s);
+    traced(p, K_GATHER, false, true, 2.0 * p->hl[0].N * p->K * 8.0, s,
+           [&] { launch_gather_systems(p->hl[0].N, Kp, p->K, v, V, s); });
     CKL();
+    p->st.launches = p->tr.launches;
+    if (p->tr.on) {
+        CK(cudaStreamSynchronize(s));
+        collect_trace(p);
+    }
     return rc;
 }
 
@@ -766,9 +852,43 @@ int bura_get_stats(const bura_plan* p, bura_stats* st) {
     return BURA_OK;
 }
 
+int bura_set_profiling(bura_plan* p, int enable) {
+    if (!p) return BURA_EINVAL;
+    CK(cudaSetDevice(p->dev));
+    Tracer& t = p->tr;
+    if (enable && t.ev.empty()) {
+        t.ev.resize(2 * kMaxTimed);
+        for (auto& e : t.ev) CK(cudaEventCreate(&e));
+    }
+    t.on = enable != 0;
+    t.pending.clear();
+    if (enable) {
+        std::memset(t.n, 0, sizeof(t.n));
+        std::memset(t.ms, 0, sizeof(t.ms));
+        std::memset(t.bytes, 0, sizeof(t.bytes));
+    }
+    return BURA_OK;
+}
+
+int bura_get_profile(const bura_plan* p, int max_entries, bura_kernel_prof* out, int* n_out) {
+    if (!p || !n_out || (max_entries > 0 && !out)) return BURA_EINVAL;
+    int n = 0;
+    for (int slot = 0; slot < 2 * K_NK && n < max_entries; ++slot) {
+        if (p->tr.n[slot] == 0) continue;
+        out[n].name = kNames[slot / 2][slot % 2];
+        out[n].launches = p->tr.n[slot];
+        out[n].ms = p->tr.ms[slot];
+        out[n].bytes = p->tr.bytes[slot];
+        ++n;
+    }
+    *n_out = n;
+    return BURA_OK;
+}
+
 int bura_destroy(bura_plan* p) {
     if (!p) return BURA_OK;
     cudaSetDevice(p->dev);
+    for (auto& e : p->tr.ev) cudaEventDestroy(e);
     for (void* q : p->allocs) cudaFree(q);
     if (p->hscal) cudaFreeHost(p->hscal);
     if (p->hbuf) cudaFreeHost(p->hbuf);
