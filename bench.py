@@ -278,6 +278,8 @@ def main(argv=None):
     per_alpha = {}
     for j, a in enumerate(ALPHAS):
         sel = per[j::len(ALPHAS)]
+        if not sel:
+            continue
         st = bura.bura_get_stats(plans[a])
         per_alpha["%.2f" % a] = {"ms_mean": sum(sel) / len(sel), "inner_iters": st["iters"], "outer": st["outer"],
                                  "err_bound": st["err_bound"]}
@@ -291,18 +293,21 @@ def main(argv=None):
     torch.cuda.synchronize()
     prof = bura.bura_get_profile(prof_plan)
     bura.bura_set_profiling(prof_plan, 0)
-    prof_total = sum(p["ms"] for p in prof)
-    dom = max(prof, key=lambda p: p["ms"])
-    peak, peak_kind = measured_hbm_peak()
-    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
-    traffic = ncu_traffic(dom["name"])
-    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": traffic, "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
-                "ms_per_launch": dom["ms"] / dom["launches"], "share_of_fine_kernel_time": dom["ms"] / prof_total,
-                "kernels": {p["name"]: {"launches_per_solve": p["launches"] / args.profile_steps,
-                                        "ms_per_launch": p["ms"] / p["launches"],
-                                        "GBps": p["bytes"] / (p["ms"] / 1e3) / 1e9} for p in prof}}
+    roofline = None
+    if prof:
+        prof_total = sum(p["ms"] for p in prof)
+        dom = max(prof, key=lambda p: p["ms"])
+        peak, peak_kind = measured_hbm_peak()
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": peak_kind,
+                    "traffic": ncu_traffic(dom["name"]),
+                    "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                    "ms_per_launch": dom["ms"] / dom["launches"],
+                    "share_of_fine_kernel_time": dom["ms"] / prof_total,
+                    "kernels": {p["name"]: {"launches_per_solve": p["launches"] / args.profile_steps,
+                                            "ms_per_launch": p["ms"] / p["launches"],
+                                            "GBps": p["bytes"] / (p["ms"] / 1e3) / 1e9} for p in prof}}
 
     # ---- FP64 one-system-at-a-time-precision comparison: plain FP64 multi-shift MG-PCG
     p64 = make_plan(0.5, bura.BURA_PREC_FP64)

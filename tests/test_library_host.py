@@ -73,18 +73,28 @@ def test_setup_rejects_oversized_grid(lib):
 @pytest.mark.parametrize("alpha,k", [(a, k) for a in (0.1, 0.25, 0.5, 0.75, 0.9) for k in (1, 3, 5, 7, 9, 10)])
 def test_library_rational_matches_oracle(lib, alpha, k):
     """The library's double-precision Remez (factored form + Newton) reproduces the oracle's
-    multi-precision Algorithm 1: E, c_j, d_j to 1e-11 relative."""
+    multi-precision Algorithm 1.  What the solve uses is the function r(t) = t sum_j c_j/(t - d_j)
+    on the spectrum: it must agree with the oracle's to 2e-15 absolute on [0, 1].  The coefficients
+    themselves are ill-conditioned functions of r (a change of r by one rounding unit moves them by
+    about eps/E relative), so they are compared to 1e-11 + 4e-17/E relative."""
     try:
         ref = tables.entry(alpha, k)
     except KeyError:
         pytest.skip("no oracle table entry")
     c, d, E = lib.bura_rational(alpha, k)
-    assert abs(E - ref["E"]) <= 1e-11 * ref["E"]
+    assert abs(E - ref["E"]) <= 1e-11 * ref["E"] + 2e-16
     assert d[0] == 0.0
+    rtol = 1e-11 + 4e-17 / ref["E"]
     for a, b in zip(c, ref["c"]):
-        assert abs(a - b) <= 1e-11 * abs(b)
+        assert abs(a - b) <= rtol * abs(b)
     for a, b in zip(d[1:], ref["d"][1:]):
-        assert abs(a - b) <= 1e-11 * abs(b)
+        assert abs(a - b) <= rtol * abs(b)
+    t = np.concatenate([np.logspace(-40, 0, 2000), np.linspace(0.001, 1, 1000)])
+
+    def r(cc, dd):
+        return t * sum(cj / (t - dj) for cj, dj in zip(cc, dd))
+
+    assert np.max(np.abs(r(c, d) - r(ref["c"], ref["d"]))) <= 2e-15
 
 
 def test_library_rational_edge_alphas(lib):
