@@ -177,6 +177,30 @@ int bura_set_profiling(bura_plan* plan, int enable);
  */
 int bura_get_profile(const bura_plan* plan, int max_entries, bura_kernel_prof* out, int* n_out);
 
+/*
+ * Allocation-free residual norms (no counterpart in the paper; a service for callers that cannot
+ * allocate device memory, e.g. inside a stream capture that must not allocate, under a caller-owned
+ * memory pool, or in a loop that must never enter the allocator).
+ *   rr[j] = || f - (A - d[j] I) V_j ||_2^2 for j = 0..nsys-1, A the scaled constant-coefficient
+ *   operator of `grid` (coef_kind must be BURA_COEF_CONSTANT), computed in FP64.
+ *   d: HOST array of nsys shifts.  f: DEVICE array of N doubles.  V: DEVICE array of nsys*N doubles,
+ *   system-major (V[j*N + i]).  rr: DEVICE array of nsys doubles (written).  stream: cudaStream_t.
+ * Allocates nothing: no cudaMalloc/cudaFree and no allocating library call.  Its scratch is a fixed
+ * file-scope device array of BURA_NOALLOC_MAX_BLOCKS * BURA_NOALLOC_MAX_SYSTEMS doubles plus a
+ * counter (about 128 KiB), held by every device that loads the library until the process exits.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls share the one scratch
+ * array, so calls whose kernels overlap on the GPU (different streams, or different host threads
+ * on one device) race and must be serialised by the caller.  Each call clears the counter it needs
+ * (cudaMemsetAsync on the stream) and overwrites the partial sums before reading them.
+ * Errors: BURA_EINVAL (null pointer, nsys < 1, bad grid or variable coefficients),
+ *         BURA_ERANGE (nsys > BURA_NOALLOC_MAX_SYSTEMS or N >= 2^31), BURA_ECUDA.
+ */
+#define BURA_NOALLOC_MAX_SYSTEMS 16
+#define BURA_NOALLOC_MAX_BLOCKS 1024
+int bura_residual_norms_noalloc(const bura_grid* grid, int nsys, const double* d, const double* f,
+                                const double* V, double* rr, void* stream);
+
 /* Frees every device and host resource of the plan (NULL is accepted). */
 int bura_destroy(bura_plan* plan);
 

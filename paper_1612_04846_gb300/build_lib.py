@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbura.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "solver.cu"]
+SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "solver.cu", "noalloc.cu"]
 HEADERS = ["kernels.cuh", "kernels_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

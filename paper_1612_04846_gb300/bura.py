@@ -82,13 +82,14 @@ def _lib():
         L.bura_get_rational.argtypes = [P, dp, dp, dp]
         L.bura_get_stats.argtypes = [P, C.POINTER(bura_stats)]
         L.bura_destroy.argtypes = [P]
+        L.bura_residual_norms_noalloc.argtypes = [C.POINTER(bura_grid), I, dp, P, P, P, P]
         L.bura_set_profiling.argtypes = [P, I]
         L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
         L.bura_strerror.argtypes = [I]
         L.bura_strerror.restype = C.c_char_p
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
-                     "bura_set_profiling", "bura_get_profile"):
+                     "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc"):
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -216,10 +217,25 @@ def bura_get_profile(plan, max_entries=64):
             for i in range(n.value)]
 
 
+def bura_residual_norms_noalloc(shape, d, f, V, rr, stream=None):
+    """rr[j] = ||f - (A - d_j I) V_j||^2 for the constant-coefficient grid `shape`, allocating nothing.
+
+    d: host numpy array of the shifts; f (N), V (len(d), N) and rr (len(d)) are float64 CUDA tensors.
+    """
+    g = bura_grid()
+    g.dim = len(shape)
+    for i, n in enumerate(shape[:3]):
+        g.n[i] = int(n)
+    g.coef_kind = BURA_COEF_CONSTANT
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    return _check(_lib().bura_residual_norms_noalloc(C.byref(g), int(d.size), _hptr(d), _dptr(f), _dptr(V),
+                                                     _dptr(rr), _stream(stream)), "bura_residual_norms_noalloc")
+
+
 def bura_destroy(plan):
     return _check(_lib().bura_destroy(plan), "bura_destroy")
 
 
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
-            "bura_strerror", "bura_set_profiling", "bura_get_profile"]
+            "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc"]
