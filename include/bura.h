@@ -71,7 +71,9 @@ typedef struct {
     int max_outer;        /* cap on FP64 refinement steps (mixed precision); default 12 */
     double inner_rtol;    /* relative residual reduction of one FP32 inner solve; default 1e-5 */
     int coarse_degree;    /* Chebyshev degree on the coarsest level when it has > 1 point; 0 = auto */
-    int reserved[8];
+    int block_points;     /* grid points per CTA of the level sweeps (CTA = points x 16-byte chunks); 0 = auto */
+    int blocks_per_sm;    /* CTAs per SM of the grid-stride sweeps; 0 = auto */
+    int reserved[6];
 } bura_options;
 
 /* Statistics of the last bura_solve*/
@@ -206,6 +208,10 @@ int bura_destroy(bura_plan* plan);
 
 /* Static description of a status code. */
 const char* bura_strerror(int status);
+
+/* Name and description of the CUDA runtime error behind the last BURA_ECUDA / BURA_ENOMEM returned
+ * by this library in this process ("no error" if none); a static string. */
+const char* bura_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ class bura_grid(C.Structure):
 class bura_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("smoother_degree", C.c_int), ("smoother_ratio", C.c_double),
                 ("max_iters", C.c_int), ("max_outer", C.c_int), ("inner_rtol", C.c_double),
-                ("coarse_degree", C.c_int), ("reserved", C.c_int * 8)]
+                ("coarse_degree", C.c_int), ("block_points", C.c_int), ("blocks_per_sm", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class bura_stats(C.Structure):
@@ -54,7 +55,10 @@ class bura_kernel_prof(C.Structure):
 class BuraError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__("%s failed: %s (%d)" % (where, _lib().bura_strerror(code).decode(), code))
+        msg = "%s failed: %s (%d)" % (where, _lib().bura_strerror(code).decode(), code)
+        if code in (BURA_ECUDA, BURA_ENOMEM):
+            msg += " [%s]" % _lib().bura_last_cuda_error().decode()
+        super().__init__(msg)
 
 
 _LIB = None
@@ -87,6 +91,8 @@ def _lib():
         L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
         L.bura_strerror.argtypes = [I]
         L.bura_strerror.restype = C.c_char_p
+        L.bura_last_cuda_error.argtypes = []
+        L.bura_last_cuda_error.restype = C.c_char_p
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
                      "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc"):
@@ -238,4 +244,5 @@ def bura_destroy(plan):
 
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
-            "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc"]
+            "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
+            "bura_last_cuda_error"]

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace bura {
 
 constexpr int KMAXP = 16;  // largest padded number of systems per point
@@ -49,7 +51,9 @@ struct Scal {
     int nactive;
     int breakdown;
     unsigned int ticket;  // last-block ticket, reset by the last block
-    int pad;
+    int it;               // PCG iterations done in the current inner solve
+    int max_it;           // cap on it (device-side loop control)
+    int parity;           // which of the two direction buffers holds the current p
 };
 
 // Chebyshev step coefficients of one level: d_m = c1 d_{m-1} + c2 Dinv res (c2 includes 1/(diag - d)
@@ -66,6 +70,39 @@ struct Red {
     Scal* scal;
     double* out;       // RED_STORE destination [Kp]
     int op;
+    unsigned long long cond;  // cudaGraphConditionalHandle of a captured PCG loop (0: none)
+};
+
+// One level of the single-CTA coarse V-cycle: its vectors live in the CTA's shared memory at the
+// given byte offsets.  c1/c2 hold deg rows of Kp Chebyshev coefficients (global memory).
+struct CoarseLevel {
+    Lev L;
+    unsigned int b, xa, xb, dd;  // shared-memory byte offsets
+    unsigned int result;         // offset of the buffer holding this level's V-cycle result
+    const double* c1;
+    const double* c2;
+    unsigned int cofs;  // shared-memory byte offset of a copy of c1 then c2 (kNoCopy: read them from global)
+    int deg;
+};
+
+constexpr unsigned int kNoCopy = 0xffffffffu;
+constexpr int kMaxCoarseLevels = 16;
+// Grid sweeps run CTAs of at most 256 threads; the register cap of 64 keeps 8 CTAs of 128 threads
+// (or 4 of 256) resident per SM, so one wave covers the whole grid.
+constexpr int kSweepThreads = 256;
+constexpr int kSweepMinBlocks = 4;
+constexpr int kCoarseThreads = 512;            // CTA size of the single-CTA coarse V-cycle
+constexpr size_t kCoarseSmem = 200 * 1024;     // shared memory budget of that CTA's vectors
+constexpr size_t kCoarseTables = 16 * 1024;    // and of its copies of the small Chebyshev tables
+struct CoarseArgs {
+    int nlev;
+    int Kp;
+    const double* dsh;
+    const void* b_in;  // right-hand side of the first coarse level (global)
+    void* x_out;       // its V-cycle result (global)
+    unsigned int smem_bytes;
+    unsigned int dsh_ofs;  // shared-memory byte offset of a copy of the shifts (KMAXP doubles)
+    CoarseLevel lev[kMaxCoarseLevels];
 };
 
 struct Launch {
@@ -76,22 +113,50 @@ struct Launch {
 template <class T>
 struct Ops {
     static void broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s);
-    static void spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, const T* pold, T* pnew, T* q,
+    static void spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, T* pa, T* pb, T* q,
                        const Red& red, cudaStream_t s);
-    static void cg_update(const Launch& g, long long N, T* x, T* r, const T* p, const T* q, const Red& red,
-                          cudaStream_t s);
+    static void cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, const T* pb, const T* q,
+                          const Red& red, cudaStream_t s);
     static void cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStep cs,
                           const double* dsh, cudaStream_t s);
     static void cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,
                           T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s);
+    static void cheb_pre2(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* xout, T* dout,
+                          ChebStep cs0, ChebStep cs1, const double* dsh, cudaStream_t s);
+    static void post_prolong(const Launch& g, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x,
+                             const T* ec, const T* b, T* xout, T* dout, ChebStep cs, const double* dsh,
+                             const Red& red, cudaStream_t s);
     static void restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x,
                              const T* b, T* bc, const double* dsh, cudaStream_t s);
     static void prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x,
                             cudaStream_t s);
+    static void coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s);
+    static cudaError_t prepare_coarse(int dim, bool var, size_t smem_bytes);
     static void apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const double* dsh,
                               cudaStream_t s);
     static void dot(const Launch& g, long long N, const T* a, const T* b, const Red& red, cudaStream_t s);
 };
+
+// Programmatic dependent launch: every kernel waits for its predecessor's completion (and memory
+// flush) before touching dependent data, and lets its successor start launching early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // FP64 refinement and output kernels.
 void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
@@ -101,6 +166,9 @@ void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K
 void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
                       const double* scale, cudaStream_t s);
 void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s);
+void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s);
+void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const double* invscale, float* r32,
+                   float* x32, float* p32, cudaStream_t s);
 void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s);
 void launch_scatter_systems(long long N, int Kp, int K, const double* X, double* x, cudaStream_t s);
 void launch_gather_systems_f(long long N, int Kp, int K, const float* v, double* V, cudaStream_t s);

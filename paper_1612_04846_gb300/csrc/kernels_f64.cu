@@ -17,17 +17,19 @@ __global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const 
     for (int q = 0; q < W; ++q) d[q] = dsh[off + q];
     LoadPlain<double> ld{v};
     Accum<double> acc;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < L.N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= L.N) continue;
-        double vc[W], Av[W], diag;
-        stencil<double, DIM, VAR>(L, Kp, P, off, ld, vc, Av, diag);
-        const double fv = __ldg(f + P);
-        double rv[W];
-        for (int q = 0; q < W; ++q) rv[q] = fv - fma(-d[q], vc[q], Av[q]);
-        vst(r + (size_t)P * Kp + off, rv);
-        acc.add(rv, rv);
-    }
+    sweep_u<StencilState<double>>(
+        L.N, blockIdx.x, gridDim.x,
+        [&](int P, StencilState<double>& st) {
+            stencil<double, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag);
+            st.bv[0] = __ldg(f + P);
+        },
+        [&](int P, StencilState<double>& st) {
+            double rv[W];
+            for (int q = 0; q < W; ++q) rv[q] = st.bv[0] - fma(-d[q], st.xc[q], st.Ax[q]);
+            vst(r + (size_t)P * Kp + off, rv);
+            acc.add(rv, rv);
+        });
+    pdl_trigger();
     reduce_finish<double>(acc, red, Kp);
 }
 
@@ -90,6 +92,47 @@ __global__ void k_correct64(int N, int Kp64, int Kp32, int K, double* __restrict
 void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
                       const double* scale, cudaStream_t s) {
     k_correct64<<<g64.blocks, dim3(g64.C, g64.PPB), 0, s>>>((int)N, g64.Kp, g32.Kp, K, v, e, scale);
+}
+
+// ||f||^2 of a plain FP64 vector (red.out[0]); threads laid out as (1, 256) with two lanes of which
+// the second stays zero, so the shared reduction machinery applies unchanged.
+__global__ void k_norm2(int N, const double* __restrict__ f, Red red) {
+    Accum<double> acc;
+    for (int P = blockIdx.x * blockDim.y + threadIdx.y; P < N; P += gridDim.x * blockDim.y) {
+        const double a[2] = {f[P], 0.0};
+        acc.add(a, a);
+    }
+    reduce_finish<double>(acc, red, 2);
+}
+
+void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s) {
+    long long b = (N + 255) / 256;
+    const int blocks = (int)(b < nsm * 8 ? (b > 0 ? b : 1) : nsm * 8);
+    k_norm2<<<blocks, dim3(1, 256), 256 * 2 * sizeof(double), s>>>((int)N, f, red);
+}
+
+// r32 = f * invscale_j for every active system (the residual of the zero initial guess); x32 = p32 = 0.
+__global__ void k_cast_f(int N, int Kp32, int K, const double* __restrict__ f, const double* __restrict__ invscale,
+                         float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32) {
+    const int off = threadIdx.x * 4;
+    double is[4];
+    for (int q = 0; q < 4; ++q) is[q] = (off + q < K) ? invscale[off + q] : 0.0;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= N) continue;
+        const double fv = f[P];
+        float rv[4], zv[4];
+        for (int q = 0; q < 4; ++q) { rv[q] = (float)(fv * is[q]); zv[q] = 0.f; }
+        const size_t base = (size_t)P * Kp32 + off;
+        vst(r32 + base, rv);
+        vst(x32 + base, zv);
+        vst(p32 + base, zv);
+    }
+}
+
+void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const double* invscale, float* r32,
+                   float* x32, float* p32, cudaStream_t s) {
+    k_cast_f<<<g32.blocks, dim3(g32.C, g32.PPB), 0, s>>>((int)N, g32.Kp, K, f, invscale, r32, x32, p32);
 }
 
 // u = sum_j c_j v_j (FP64, fixed order j = 0..K-1); one thread per point.

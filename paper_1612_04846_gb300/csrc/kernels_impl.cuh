@@ -1,5 +1,10 @@
 // Kernel templates of the multi-shift MG-PCG; instantiated for float and double in
 // kernels_f32.cu / kernels_f64.cu.  See kernels.cuh for the data layout.
+//
+// Every per-level operation is a __device__ "sweep" over the points of one level, distributed over
+// CTAs by (first tile, tile stride).  The grid kernels pass (blockIdx.x, gridDim.x); the single-CTA
+// coarse kernel runs the whole small-level part of the V-cycle with (0, 1) and __syncthreads()
+// between dependent sweeps.
 #pragma once
 #include "kernels.cuh"
 
@@ -8,13 +13,6 @@ namespace bura {
 template <class T>
 __device__ __forceinline__ void vld(const T* p, T (&o)[VecT<T>::W]) {
     typename VecT<T>::V v = *reinterpret_cast<const typename VecT<T>::V*>(p);
-    if constexpr (VecT<T>::W == 2) { o[0] = v.x; o[1] = v.y; }
-    else { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
-}
-
-template <class T>
-__device__ __forceinline__ void vldg(const T* p, T (&o)[VecT<T>::W]) {
-    typename VecT<T>::V v = __ldg(reinterpret_cast<const typename VecT<T>::V*>(p));
     if constexpr (VecT<T>::W == 2) { o[0] = v.x; o[1] = v.y; }
     else { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 }
@@ -54,7 +52,6 @@ struct Accum {
     }
 };
 
-// Coordinates of point P on a level.
 struct Coord { int i, j, l; };
 template <int DIM>
 __device__ __forceinline__ Coord coord(const Lev& L, int P) {
@@ -84,7 +81,7 @@ __device__ __forceinline__ Wts<T> weights(const Lev& L, int P, const Coord& c) {
     if (VAR) {
         const T* fx = reinterpret_cast<const T*>(L.fx);
         const T* fy = reinterpret_cast<const T*>(L.fy);
-        const size_t row = (size_t)c.l * L.ny + c.j;             // (l, j) row of x-faces: nx+1 each
+        const size_t row = (size_t)c.l * L.ny + c.j;  // (l, j) row of x-faces: nx+1 each
         w.xm = __ldg(fx + row * (L.nx + 1) + c.i);
         w.xp = __ldg(fx + row * (L.nx + 1) + c.i + 1);
         const size_t ybase = ((size_t)c.l * (L.ny + 1) + c.j) * L.nx + c.i;
@@ -105,23 +102,112 @@ __device__ __forceinline__ Wts<T> weights(const Lev& L, int P, const Coord& c) {
     return w;
 }
 
+template <class T, int DIM, bool VAR>
+__device__ __forceinline__ T diag_at(const Lev& L, int P) {
+    const Coord c = coord<DIM>(L, P);
+    const Wts<T> w = weights<T, DIM, VAR>(L, P, c);
+    T dg = w.xm + w.xp + w.ym + w.yp;
+    if (DIM == 3) dg += w.zm + w.zp;
+    return dg;
+}
+
+// ------------------------------------------------------------------ value loaders
+// A loader returns the W values of chunk `off` at point P (idx = P*Kp + off).
 template <class T>
 struct LoadPlain {
     const T* x;
-    __device__ __forceinline__ void operator()(size_t idx, T (&o)[VecT<T>::W]) const { vld(x + idx, o); }
+    __device__ __forceinline__ void operator()(int, size_t idx, T (&o)[VecT<T>::W]) const { vld(x + idx, o); }
 };
 
-// p_new = z + beta * p_old evaluated on the fly (the p update fused into the operator apply).
+// p_new = z + beta p_old evaluated on the fly (the CG p update fused into the operator apply).
 template <class T>
 struct LoadPUpd {
     const T* z;
     const T* p;
     T beta[VecT<T>::W];
-    __device__ __forceinline__ void operator()(size_t idx, T (&o)[VecT<T>::W]) const {
+    __device__ __forceinline__ void operator()(int, size_t idx, T (&o)[VecT<T>::W]) const {
         T a[VecT<T>::W], b[VecT<T>::W];
-        vldg(z + idx, a);
-        vldg(p + idx, b);
+        vld(z + idx, a);
+        vld(p + idx, b);
         for (int v = 0; v < VecT<T>::W; ++v) o[v] = fma(beta[v], b[v], a[v]);
+    }
+};
+
+// First Chebyshev iterate from a zero guess, x1 = c2_0 Dinv b, evaluated on the fly.
+template <class T, int DIM, bool VAR>
+struct LoadCheb0 {
+    Lev L;
+    const T* b;
+    T c2[VecT<T>::W];
+    T d[VecT<T>::W];
+    __device__ __forceinline__ void operator()(int P, size_t idx, T (&o)[VecT<T>::W]) const {
+        vld(b + idx, o);
+        if (VAR) {
+            const T dg = diag_at<T, DIM, VAR>(L, P);
+            for (int v = 0; v < VecT<T>::W; ++v) o[v] = c2[v] * o[v] / (dg - d[v]);
+        } else {
+            for (int v = 0; v < VecT<T>::W; ++v) o[v] *= c2[v];
+        }
+    }
+};
+
+// x + P ec (bilinear / trilinear prolongation of the coarse correction, added on the fly).
+template <class T, int DIM>
+__device__ __forceinline__ void prolong_at(const Lev& Lf, const Lev& Lc, int Kp, int off, int P, const T* ec,
+                                           T (&sum)[VecT<T>::W]) {
+    constexpr int W = VecT<T>::W;
+    const Coord c = coord<DIM>(Lf, P);
+    const int fc[3] = {c.i, c.j, c.l};
+    const int cn[3] = {Lc.nx, Lc.ny, Lc.nz};
+    int lo[3], hi[3];
+    T wl[3], wh[3];
+    for (int a = 0; a < 3; ++a) {
+        if (a >= DIM) { lo[a] = hi[a] = 0; wl[a] = T(1); wh[a] = T(0); continue; }
+        const int f = fc[a];
+        if (f & 1) { lo[a] = hi[a] = (f - 1) >> 1; wl[a] = T(1); wh[a] = T(0); }
+        else {
+            lo[a] = (f >> 1) - 1; hi[a] = f >> 1;
+            wl[a] = lo[a] >= 0 ? T(0.5) : T(0);
+            wh[a] = hi[a] < cn[a] ? T(0.5) : T(0);
+            if (lo[a] < 0) lo[a] = 0;
+            if (hi[a] >= cn[a]) hi[a] = cn[a] - 1;
+        }
+    }
+    for (int v = 0; v < W; ++v) sum[v] = T(0);
+    const int nz = DIM == 3 ? 2 : 1;
+    for (int dz = 0; dz < nz; ++dz) {
+        const int zc = dz ? hi[2] : lo[2];
+        const T wz = dz ? wh[2] : wl[2];
+        if (wz == T(0)) continue;
+        for (int dy = 0; dy < 2; ++dy) {
+            const int yc = dy ? hi[1] : lo[1];
+            const T wy = dy ? wh[1] : wl[1];
+            if (wy == T(0)) continue;
+            for (int dx = 0; dx < 2; ++dx) {
+                const int xc = dx ? hi[0] : lo[0];
+                const T wx = dx ? wh[0] : wl[0];
+                if (wx == T(0)) continue;
+                const int Pc = (zc * Lc.ny + yc) * Lc.nx + xc;
+                T e[W];
+                vld(ec + (size_t)Pc * Kp + off, e);
+                const T wt = wx * wy * wz;
+                for (int v = 0; v < W; ++v) sum[v] = fma(wt, e[v], sum[v]);
+            }
+        }
+    }
+}
+
+template <class T, int DIM>
+struct LoadProlong {
+    Lev Lf, Lc;
+    int Kp, off;
+    const T* x;
+    const T* ec;
+    __device__ __forceinline__ void operator()(int P, size_t idx, T (&o)[VecT<T>::W]) const {
+        T s[VecT<T>::W];
+        prolong_at<T, DIM>(Lf, Lc, Kp, off, P, ec, s);
+        vld(x + idx, o);
+        for (int v = 0; v < VecT<T>::W; ++v) o[v] += s[v];
     }
 };
 
@@ -135,19 +221,20 @@ __device__ __forceinline__ void stencil(const Lev& L, int Kp, int P, int off, co
     diag = w.xm + w.xp + w.ym + w.yp;
     if (DIM == 3) diag += w.zm + w.zp;
     const size_t base = (size_t)P * Kp + off;
-    ld(base, xc);
+    ld(P, base, xc);
     T acc[W];
     for (int v = 0; v < W; ++v) acc[v] = diag * xc[v];
     T n[W];
-    if (c.i > 0) { ld(base - Kp, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.xm, n[v], acc[v]); }
-    if (c.i < L.nx - 1) { ld(base + Kp, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.xp, n[v], acc[v]); }
+    if (c.i > 0) { ld(P - 1, base - Kp, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.xm, n[v], acc[v]); }
+    if (c.i < L.nx - 1) { ld(P + 1, base + Kp, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.xp, n[v], acc[v]); }
     const size_t sy = (size_t)L.nx * Kp;
-    if (c.j > 0) { ld(base - sy, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.ym, n[v], acc[v]); }
-    if (c.j < L.ny - 1) { ld(base + sy, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.yp, n[v], acc[v]); }
+    if (c.j > 0) { ld(P - L.nx, base - sy, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.ym, n[v], acc[v]); }
+    if (c.j < L.ny - 1) { ld(P + L.nx, base + sy, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.yp, n[v], acc[v]); }
     if (DIM == 3) {
         const size_t sz = (size_t)L.plane * Kp;
-        if (c.l > 0) { ld(base - sz, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.zm, n[v], acc[v]); }
-        if (c.l < L.nz - 1) { ld(base + sz, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.zp, n[v], acc[v]); }
+        const int pz = (int)L.plane;
+        if (c.l > 0) { ld(P - pz, base - sz, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.zm, n[v], acc[v]); }
+        if (c.l < L.nz - 1) { ld(P + pz, base + sz, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.zp, n[v], acc[v]); }
     }
     for (int v = 0; v < W; ++v) Ax[v] = acc[v];
 }
@@ -245,21 +332,172 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     if (tid == 0) {
         red.scal->ticket = 0u;
         if (red.op == RED_CONV) {
+            Scal* S = red.scal;
             int na = 0;
-            for (int s = 0; s < Kp; ++s) na += red.scal->active[s] ? 1 : 0;
-            red.scal->nactive = na;
+            for (int s = 0; s < Kp; ++s) na += S->active[s] ? 1 : 0;
+            S->nactive = na;
+            S->it += 1;
+            S->parity ^= 1;
+            // device-side loop control of a captured PCG loop (conditional WHILE node)
+            if (red.cond) {
+                const bool go = na > 0 && !S->breakdown && S->it < S->max_it;
+                cudaGraphSetConditional(red.cond, go ? 1u : 0u);
+            }
         }
     }
 }
 
-// ------------------------------------------------------------------ kernels
+// ------------------------------------------------------------------ sweeps (per level)
+#define BURA_SWEEP(NPTS)                                                                  \
+    for (int tile = b0; (long long)tile * blockDim.y < (NPTS); tile += nb)                \
+        if (const int P = tile * blockDim.y + threadIdx.y; P < (NPTS))
+
+// Two-phase sweep: every thread takes U tiles per grid-stride step, issues the loads of all U first
+// (`load(P, state)`) and only then computes and stores (`finish(P, state)`), so U independent load
+// chains are in flight per thread.  The per-thread order of points is fixed (deterministic sums).
+constexpr int kUnroll = 2;
+template <class State, class LoadF, class FinishF>
+__device__ __forceinline__ void sweep_u(long long N, int b0, int nb, LoadF&& load, FinishF&& finish) {
+    for (int t0 = b0 * kUnroll; (long long)t0 * blockDim.y < N; t0 += nb * kUnroll) {
+        State st[kUnroll];
+        int P[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            P[u] = (t0 + u) * (int)blockDim.y + (int)threadIdx.y;
+            if (P[u] < N) load(P[u], st[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (P[u] < N) finish(P[u], st[u]);
+    }
+}
+
 template <class T>
-__global__ void k_broadcast(const double* __restrict__ f, int N, int Kp, int K, T* r, T* x, T* p) {
+struct StencilState {
+    T xc[VecT<T>::W], Ax[VecT<T>::W], bv[VecT<T>::W], dv[VecT<T>::W];
+    T diag;
+};
+
+// x = c2_0 Dinv b (first Chebyshev step from a zero initial guess; pointwise).
+template <class T, int DIM, bool VAR>
+__device__ __forceinline__ void sw_cheb_zero(const Lev& L, int Kp, const T* b, T* x, ChebStep cs, const double* dsh,
+                                             int b0, int nb) {
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= N) continue;
+    LoadCheb0<T, DIM, VAR> ld;
+    ld.L = L;
+    ld.b = b;
+    for (int v = 0; v < W; ++v) { ld.c2[v] = (T)cs.c2[off + v]; ld.d[v] = (T)dsh[off + v]; }
+    BURA_SWEEP(L.N) {
+        T xv[W];
+        const size_t base = (size_t)P * Kp + off;
+        ld(P, base, xv);
+        vst(x + base, xv);
+    }
+}
+
+// One Chebyshev step: res = b - (A - dI) xin; dnew = c1 din + c2 Dinv res; xout = xin + dnew.
+// The input iterate comes from a loader (plain, first-step-from-zero, or prolongation-corrected);
+// din may be null (c1 = 0) and is the loader's own value when din_is_x; dout may be null.
+template <class T, int DIM, bool VAR, class LD>
+__device__ __forceinline__ void sw_cheb_step(const Lev& L, int Kp, const LD& ld, const T* din, bool din_is_x,
+                                             const T* b, T* xout, T* dout, ChebStep cs, const double* dsh,
+                                             Accum<T>* acc, int b0, int nb) {
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    T c1[W], c2[W], d[W];
+    for (int v = 0; v < W; ++v) {
+        c1[v] = cs.c1 ? (T)cs.c1[off + v] : T(0);
+        c2[v] = (T)cs.c2[off + v];
+        d[v] = (T)dsh[off + v];
+    }
+    sweep_u<StencilState<T>>(
+        L.N, b0, nb,
+        [&](int P, StencilState<T>& st) {
+            stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag);
+            const size_t base = (size_t)P * Kp + off;
+            vld(b + base, st.bv);
+            if (din_is_x) { for (int v = 0; v < W; ++v) st.dv[v] = st.xc[v]; }
+            else if (din) vld(din + base, st.dv);
+            else for (int v = 0; v < W; ++v) st.dv[v] = T(0);
+        },
+        [&](int P, StencilState<T>& st) {
+            const size_t base = (size_t)P * Kp + off;
+            T xo[W];
+            for (int v = 0; v < W; ++v) {
+                const T res = st.bv[v] - fma(-d[v], st.xc[v], st.Ax[v]);
+                T g = c2[v] * res;
+                if (VAR) g = g / (st.diag - d[v]);
+                st.dv[v] = fma(c1[v], st.dv[v], g);
+                xo[v] = st.xc[v] + st.dv[v];
+            }
+            vst(xout + base, xo);
+            if (dout) vst(dout + base, st.dv);
+            if (acc) acc->add(st.bv, xo);
+        });
+}
+
+// bc = R (b - (A - dI) x): full weighting, R = P^T / 2^DIM with 1D weights (1/4, 1/2, 1/4).
+template <class T, int DIM, bool VAR>
+__device__ __forceinline__ void sw_restrict(const Lev& Lf, const Lev& Lc, int Kp, const T* x, const T* b, T* bc,
+                                            const double* dsh, int b0, int nb) {
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    T d[W];
+    for (int v = 0; v < W; ++v) d[v] = (T)dsh[off + v];
+    const T w1[3] = {T(0.25), T(0.5), T(0.25)};
+    LoadPlain<T> ld{x};
+    struct St { T sum[VecT<T>::W]; };
+    sweep_u<St>(
+        Lc.N, b0, nb,
+        [&](int P, St& st) {
+            const Coord cc = coord<DIM>(Lc, P);
+            const int fi = 2 * cc.i + 1, fj = 2 * cc.j + 1, fl = (DIM == 3) ? 2 * cc.l + 1 : 0;
+            for (int v = 0; v < W; ++v) st.sum[v] = T(0);
+            const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
+            for (int dz = zlo; dz <= zhi; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int Pf = ((fl + dz) * Lf.ny + (fj + dy)) * Lf.nx + (fi + dx);
+                        T xc[W], Ax[W], diag;
+                        stencil<T, DIM, VAR>(Lf, Kp, Pf, off, ld, xc, Ax, diag);
+                        T bv[W];
+                        vld(b + (size_t)Pf * Kp + off, bv);
+                        T wt = w1[dx + 1] * w1[dy + 1];
+                        if (DIM == 3) wt *= w1[dz + 1];
+                        for (int v = 0; v < W; ++v) st.sum[v] = fma(wt, bv[v] - fma(-d[v], xc[v], Ax[v]), st.sum[v]);
+                    }
+        },
+        [&](int P, St& st) { vst(bc + (size_t)P * Kp + off, st.sum); });
+}
+
+// x += P ec (prolongation of the coarse correction; pointwise on the fine level).
+template <class T, int DIM>
+__device__ __forceinline__ void sw_prolong_add(const Lev& Lf, const Lev& Lc, int Kp, const T* ec, T* x, int b0,
+                                               int nb) {
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    struct St { T sum[VecT<T>::W], xv[VecT<T>::W]; };
+    sweep_u<St>(
+        Lf.N, b0, nb,
+        [&](int P, St& st) {
+            prolong_at<T, DIM>(Lf, Lc, Kp, off, P, ec, st.sum);
+            vld(x + (size_t)P * Kp + off, st.xv);
+        },
+        [&](int P, St& st) {
+            for (int v = 0; v < W; ++v) st.xv[v] += st.sum[v];
+            vst(x + (size_t)P * Kp + off, st.xv);
+        });
+}
+
+// ------------------------------------------------------------------ grid kernels
+template <class T>
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_broadcast(const double* __restrict__ f, int N, int Kp, int K, T* r, T* x, T* p) {
+    pdl_wait();
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    const int b0 = blockIdx.x, nb = gridDim.x;
+    BURA_SWEEP(N) {
         const T fv = (T)f[P];
         T rv[W], zv[W];
         for (int v = 0; v < W; ++v) { rv[v] = (off + v < K) ? fv : T(0); zv[v] = T(0); }
@@ -270,214 +508,149 @@ __global__ void k_broadcast(const double* __restrict__ f, int N, int Kp, int K, 
     }
 }
 
+// The two direction buffers pa/pb alternate roles each iteration; the parity lives in the Scal
+// record (toggled by the last block of k_cg_update), so a captured loop body can stay fixed.
 template <class T, int DIM, bool VAR>
-__global__ void k_spmv_p(Lev L, int Kp, const T* __restrict__ z, const T* __restrict__ pold, T* __restrict__ pnew,
-                         T* __restrict__ q, Red red) {
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_spmv_p(Lev L, int Kp, const T* __restrict__ z, T* pa, T* pb, T* __restrict__ q, Red red) {
+    pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
+    const int b0 = blockIdx.x, nb = gridDim.x;
+    const int par = red.scal->parity;
+    const T* __restrict__ pold = par ? pb : pa;
+    T* __restrict__ pnew = par ? pa : pb;
     LoadPUpd<T> ld;
     ld.z = z;
     ld.p = pold;
     T dsh[W];
     for (int v = 0; v < W; ++v) { ld.beta[v] = (T)red.scal->beta[off + v]; dsh[v] = (T)red.scal->dsh[off + v]; }
     Accum<T> acc;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < L.N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= L.N) continue;
-        T pc[W], Ax[W], diag;
-        stencil<T, DIM, VAR>(L, Kp, P, off, ld, pc, Ax, diag);
-        T qv[W];
-        for (int v = 0; v < W; ++v) qv[v] = fma(-dsh[v], pc[v], Ax[v]);
-        const size_t base = (size_t)P * Kp + off;
-        vst(pnew + base, pc);
-        vst(q + base, qv);
-        acc.add(pc, qv);
-    }
+    sweep_u<StencilState<T>>(
+        L.N, b0, nb, [&](int P, StencilState<T>& st) { stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag); },
+        [&](int P, StencilState<T>& st) {
+            T qv[W];
+            for (int v = 0; v < W; ++v) qv[v] = fma(-dsh[v], st.xc[v], st.Ax[v]);
+            const size_t base = (size_t)P * Kp + off;
+            vst(pnew + base, st.xc);
+            vst(q + base, qv);
+            acc.add(st.xc, qv);
+        });
+    pdl_trigger();
     reduce_finish<T>(acc, red, Kp);
 }
 
 template <class T>
-__global__ void k_cg_update(int N, int Kp, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cg_update(int N, int Kp, T* __restrict__ x, T* __restrict__ r, const T* pa, const T* pb,
                             const T* __restrict__ q, Red red) {
+    pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
+    const int b0 = blockIdx.x, nb = gridDim.x;
+    const T* __restrict__ p = red.scal->parity ? pa : pb;  // the direction k_spmv_p just wrote
     T a[W];
     for (int v = 0; v < W; ++v) a[v] = (T)red.scal->alpha[off + v];
     Accum<T> acc;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= N) continue;
-        const size_t base = (size_t)P * Kp + off;
-        T xv[W], rv[W], pv[W], qv[W];
-        vld(x + base, xv);
-        vld(r + base, rv);
-        vldg(p + base, pv);
-        vldg(q + base, qv);
-        for (int v = 0; v < W; ++v) { xv[v] = fma(a[v], pv[v], xv[v]); rv[v] = fma(-a[v], qv[v], rv[v]); }
-        vst(x + base, xv);
-        vst(r + base, rv);
-        acc.add(rv, rv);
-    }
+    struct St { T xv[VecT<T>::W], rv[VecT<T>::W], pv[VecT<T>::W], qv[VecT<T>::W]; };
+    sweep_u<St>(
+        N, b0, nb,
+        [&](int P, St& st) {
+            const size_t base = (size_t)P * Kp + off;
+            vld(x + base, st.xv);
+            vld(r + base, st.rv);
+            vld(p + base, st.pv);
+            vld(q + base, st.qv);
+        },
+        [&](int P, St& st) {
+            const size_t base = (size_t)P * Kp + off;
+            for (int v = 0; v < W; ++v) {
+                st.xv[v] = fma(a[v], st.pv[v], st.xv[v]);
+                st.rv[v] = fma(-a[v], st.qv[v], st.rv[v]);
+            }
+            vst(x + base, st.xv);
+            vst(r + base, st.rv);
+            acc.add(st.rv, st.rv);
+        });
+    pdl_trigger();
     reduce_finish<T>(acc, red, Kp);
 }
 
-// x = c2 Dinv b (first Chebyshev step from a zero initial guess; pointwise).
 template <class T, int DIM, bool VAR>
-__global__ void k_cheb_zero(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ x, ChebStep cs,
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_zero(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ x, ChebStep cs,
                             const double* __restrict__ dsh) {
-    constexpr int W = VecT<T>::W;
-    const int off = threadIdx.x * W;
-    T c2[W], d[W];
-    for (int v = 0; v < W; ++v) { c2[v] = (T)cs.c2[off + v]; d[v] = (T)dsh[off + v]; }
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < L.N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= L.N) continue;
-        const size_t base = (size_t)P * Kp + off;
-        T bv[W], xv[W];
-        vldg(b + base, bv);
-        if (VAR) {
-            const Coord c = coord<DIM>(L, P);
-            const Wts<T> w = weights<T, DIM, VAR>(L, P, c);
-            T diag = w.xm + w.xp + w.ym + w.yp;
-            if (DIM == 3) diag += w.zm + w.zp;
-            for (int v = 0; v < W; ++v) xv[v] = c2[v] * bv[v] / (diag - d[v]);
-        } else {
-            for (int v = 0; v < W; ++v) xv[v] = c2[v] * bv[v];
-        }
-        vst(x + base, xv);
-    }
+    pdl_wait();
+    sw_cheb_zero<T, DIM, VAR>(L, Kp, b, x, cs, dsh, blockIdx.x, gridDim.x);
 }
 
-// One Chebyshev step: res = b - (A - dI) xin; dnew = c1 din + c2 Dinv res; xout = xin + dnew.
-// din may be null (c1 = 0); dout may be null; red.op != RED_NONE accumulates b . xout.
+// Plain Chebyshev step (input iterate read from xin).
 template <class T, int DIM, bool VAR>
-__global__ void k_cheb_step(Lev L, int Kp, const T* __restrict__ xin, const T* __restrict__ din,
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_step(Lev L, int Kp, const T* __restrict__ xin, const T* __restrict__ din,
                             const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStep cs,
                             const double* __restrict__ dsh, Red red) {
-    constexpr int W = VecT<T>::W;
-    const int off = threadIdx.x * W;
-    T c1[W], c2[W], d[W];
-    for (int v = 0; v < W; ++v) {
-        c1[v] = cs.c1 ? (T)cs.c1[off + v] : T(0);
-        c2[v] = (T)cs.c2[off + v];
-        d[v] = (T)dsh[off + v];
-    }
+    pdl_wait();
     LoadPlain<T> ld{xin};
     Accum<T> acc;
     const bool dot = red.op != RED_NONE;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < L.N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= L.N) continue;
-        T xc[W], Ax[W], diag;
-        stencil<T, DIM, VAR>(L, Kp, P, off, ld, xc, Ax, diag);
-        const size_t base = (size_t)P * Kp + off;
-        T bv[W], dv[W], xo[W];
-        vldg(b + base, bv);
-        if (din) vld(din + base, dv);
-        else for (int v = 0; v < W; ++v) dv[v] = T(0);
-        for (int v = 0; v < W; ++v) {
-            const T res = bv[v] - fma(-d[v], xc[v], Ax[v]);
-            T g = c2[v] * res;
-            if (VAR) g = g / (diag - d[v]);
-            dv[v] = fma(c1[v], dv[v], g);
-            xo[v] = xc[v] + dv[v];
-        }
-        vst(xout + base, xo);
-        if (dout) vst(dout + base, dv);
-        if (dot) acc.add(bv, xo);
-    }
+    sw_cheb_step<T, DIM, VAR>(L, Kp, ld, din, false, b, xout, dout, cs, dsh, dot ? &acc : nullptr, blockIdx.x,
+                              gridDim.x);
+    pdl_trigger();
     if (dot) reduce_finish<T>(acc, red, Kp);
 }
 
-// bc = R (b - (A - dI) x): full weighting, R = P^T / 2^DIM with 1D weights (1/4, 1/2, 1/4).
+// First two Chebyshev steps from a zero guess in one sweep: x1 = c2_0 Dinv b is evaluated at the
+// stencil points on the fly (d_1 = x1), then the second step is applied.
 template <class T, int DIM, bool VAR>
-__global__ void k_restrict_res(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ b,
-                               T* __restrict__ bc, const double* __restrict__ dsh) {
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_pre2(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout,
+                            ChebStep cs0, ChebStep cs1, const double* __restrict__ dsh) {
+    pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
-    T d[W];
-    for (int v = 0; v < W; ++v) d[v] = (T)dsh[off + v];
-    const T w1[3] = {T(0.25), T(0.5), T(0.25)};
-    LoadPlain<T> ld{x};
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < Lc.N; tile += gridDim.x) {
-        const int Pc = tile * blockDim.y + threadIdx.y;
-        if (Pc >= Lc.N) continue;
-        const Coord cc = coord<DIM>(Lc, Pc);
-        const int fi = 2 * cc.i + 1, fj = 2 * cc.j + 1, fl = (DIM == 3) ? 2 * cc.l + 1 : 0;
-        T sum[W];
-        for (int v = 0; v < W; ++v) sum[v] = T(0);
-        const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
-        for (int dz = zlo; dz <= zhi; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int P = ((fl + dz) * Lf.ny + (fj + dy)) * Lf.nx + (fi + dx);
-                    T xc[W], Ax[W], diag;
-                    stencil<T, DIM, VAR>(Lf, Kp, P, off, ld, xc, Ax, diag);
-                    T bv[W];
-                    vldg(b + (size_t)P * Kp + off, bv);
-                    T wt = w1[dx + 1] * w1[dy + 1];
-                    if (DIM == 3) wt *= w1[dz + 1];
-                    for (int v = 0; v < W; ++v) sum[v] = fma(wt, bv[v] - fma(-d[v], xc[v], Ax[v]), sum[v]);
-                }
-        vst(bc + (size_t)Pc * Kp + off, sum);
-    }
+    LoadCheb0<T, DIM, VAR> ld;
+    ld.L = L;
+    ld.b = b;
+    for (int v = 0; v < W; ++v) { ld.c2[v] = (T)cs0.c2[off + v]; ld.d[v] = (T)dsh[off + v]; }
+    sw_cheb_step<T, DIM, VAR>(L, Kp, ld, nullptr, true, b, xout, dout, cs1, dsh, nullptr, blockIdx.x, gridDim.x);
 }
 
-// x += P ec: bilinear / trilinear interpolation (coarse node I sits on fine node 2I+1).
+// First post-smoothing step with the coarse-grid correction added on the fly: xin = x + P ec.
+template <class T, int DIM, bool VAR>
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_post_prolong(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ ec,
+                               const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStep cs,
+                               const double* __restrict__ dsh, Red red) {
+    pdl_wait();
+    constexpr int W = VecT<T>::W;
+    LoadProlong<T, DIM> ld{Lf, Lc, Kp, (int)threadIdx.x * W, x, ec};
+    Accum<T> acc;
+    const bool dot = red.op != RED_NONE;
+    sw_cheb_step<T, DIM, VAR>(Lf, Kp, ld, nullptr, false, b, xout, dout, cs, dsh, dot ? &acc : nullptr, blockIdx.x,
+                              gridDim.x);
+    pdl_trigger();
+    if (dot) reduce_finish<T>(acc, red, Kp);
+}
+
 template <class T, int DIM>
-__global__ void k_prolong_add(Lev Lf, Lev Lc, int Kp, const T* __restrict__ ec, T* __restrict__ x) {
-    constexpr int W = VecT<T>::W;
-    const int off = threadIdx.x * W;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < Lf.N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= Lf.N) continue;
-        const Coord c = coord<DIM>(Lf, P);
-        int ci[3][2], nc[3];
-        T cw[3][2];
-        const int fc[3] = {c.i, c.j, c.l};
-        const int cn[3] = {Lc.nx, Lc.ny, Lc.nz};
-        for (int a = 0; a < DIM; ++a) {
-            const int f = fc[a];
-            nc[a] = 0;
-            if (f & 1) {
-                ci[a][0] = (f - 1) >> 1; cw[a][0] = T(1); nc[a] = 1;
-            } else {
-                const int lo = (f >> 1) - 1, hi = f >> 1;
-                if (lo >= 0) { ci[a][nc[a]] = lo; cw[a][nc[a]] = T(0.5); ++nc[a]; }
-                if (hi < cn[a]) { ci[a][nc[a]] = hi; cw[a][nc[a]] = T(0.5); ++nc[a]; }
-            }
-        }
-        if (DIM == 2) { nc[2] = 1; ci[2][0] = 0; cw[2][0] = T(1); }
-        T sum[W];
-        for (int v = 0; v < W; ++v) sum[v] = T(0);
-        for (int a2 = 0; a2 < nc[2]; ++a2)
-            for (int a1 = 0; a1 < nc[1]; ++a1)
-                for (int a0 = 0; a0 < nc[0]; ++a0) {
-                    const int Pc = (ci[2][a2] * Lc.ny + ci[1][a1]) * Lc.nx + ci[0][a0];
-                    const T wt = cw[0][a0] * cw[1][a1] * cw[2][a2];
-                    T e[W];
-                    vldg(ec + (size_t)Pc * Kp + off, e);
-                    for (int v = 0; v < W; ++v) sum[v] = fma(wt, e[v], sum[v]);
-                }
-        const size_t base = (size_t)P * Kp + off;
-        T xv[W];
-        vld(x + base, xv);
-        for (int v = 0; v < W; ++v) xv[v] += sum[v];
-        vst(x + base, xv);
-    }
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_prolong_add(Lev Lf, Lev Lc, int Kp, const T* __restrict__ ec, T* __restrict__ x) {
+    pdl_wait();
+    sw_prolong_add<T, DIM>(Lf, Lc, Kp, ec, x, blockIdx.x, gridDim.x);
 }
 
 template <class T, int DIM, bool VAR>
-__global__ void k_apply_shifted(Lev L, int Kp, const T* __restrict__ x, T* __restrict__ y,
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_restrict_res(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ b,
+                               T* __restrict__ bc, const double* __restrict__ dsh) {
+    pdl_wait();
+    sw_restrict<T, DIM, VAR>(Lf, Lc, Kp, x, b, bc, dsh, blockIdx.x, gridDim.x);
+}
+
+template <class T, int DIM, bool VAR>
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_apply_shifted(Lev L, int Kp, const T* __restrict__ x, T* __restrict__ y,
                                 const double* __restrict__ dsh) {
+    pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
+    const int b0 = blockIdx.x, nb = gridDim.x;
     T d[W];
     for (int v = 0; v < W; ++v) d[v] = (T)dsh[off + v];
     LoadPlain<T> ld{x};
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < L.N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= L.N) continue;
+    BURA_SWEEP(L.N) {
         T xc[W], Ax[W], diag;
         stencil<T, DIM, VAR>(L, Kp, P, off, ld, xc, Ax, diag);
         for (int v = 0; v < W; ++v) Ax[v] = fma(-d[v], xc[v], Ax[v]);
@@ -486,19 +659,110 @@ __global__ void k_apply_shifted(Lev L, int Kp, const T* __restrict__ x, T* __res
 }
 
 template <class T>
-__global__ void k_dot(int N, int Kp, const T* __restrict__ a, const T* __restrict__ b, Red red) {
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_dot(int N, int Kp, const T* __restrict__ a, const T* __restrict__ b, Red red) {
+    pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
+    const int b0 = blockIdx.x, nb = gridDim.x;
     Accum<T> acc;
-    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
-        const int P = tile * blockDim.y + threadIdx.y;
-        if (P >= N) continue;
-        T av[W], bv[W];
-        vldg(a + (size_t)P * Kp + off, av);
-        vldg(b + (size_t)P * Kp + off, bv);
-        acc.add(av, bv);
-    }
+    struct St { T av[VecT<T>::W], bv[VecT<T>::W]; };
+    sweep_u<St>(
+        N, b0, nb,
+        [&](int P, St& st) {
+            vld(a + (size_t)P * Kp + off, st.av);
+            vld(b + (size_t)P * Kp + off, st.bv);
+        },
+        [&](int, St& st) { acc.add(st.av, st.bv); });
+    pdl_trigger();
     reduce_finish<T>(acc, red, Kp);
+}
+
+// ------------------------------------------------------------------ single-CTA coarse V-cycle
+// Runs levels l0..nlev-1 of the V-cycle (all with few points) in one CTA with every vector in shared
+// memory: the same sweeps as the grid kernels with (first tile, stride) = (0, 1) and __syncthreads()
+// between dependent sweeps.  b of level l0 is read from and its result written to global memory.
+template <class T, int DIM, bool VAR>
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char csm[];
+    auto at = [&](unsigned int off) { return reinterpret_cast<T*>(csm + off); };
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    {
+        const int n = (int)(a.lev[0].L.N * a.Kp);
+        const T* src = reinterpret_cast<const T*>(a.b_in);
+        T* dst = at(a.lev[0].b);
+        for (int i = tid; i < n; i += nthr) dst[i] = src[i];
+        // the shifts and the small Chebyshev tables are read by every sweep: keep them on chip
+        double* ds = reinterpret_cast<double*>(csm + a.dsh_ofs);
+        for (int i = tid; i < KMAXP; i += nthr) ds[i] = a.dsh[i];
+        for (int l = 0; l < a.nlev; ++l) {
+            const CoarseLevel& c = a.lev[l];
+            if (c.cofs == kNoCopy) continue;
+            double* t = reinterpret_cast<double*>(csm + c.cofs);
+            const int m = c.deg * a.Kp;
+            for (int i = tid; i < m; i += nthr) { t[i] = c.c1[i]; t[m + i] = c.c2[i]; }
+        }
+    }
+    __syncthreads();
+    const double* dsh = reinterpret_cast<const double*>(csm + a.dsh_ofs);
+    auto tab1 = [&](const CoarseLevel& c) {
+        return c.cofs == kNoCopy ? c.c1 : reinterpret_cast<const double*>(csm + c.cofs);
+    };
+    auto tab2 = [&](const CoarseLevel& c) {
+        return c.cofs == kNoCopy ? c.c2 : reinterpret_cast<const double*>(csm + c.cofs) + c.deg * a.Kp;
+    };
+    // down: pre-smoothing and restriction
+    for (int l = 0; l < a.nlev; ++l) {
+        const CoarseLevel& c = a.lev[l];
+        const int deg = c.deg;
+        T* A = at(c.xa);
+        T* B = at(c.xb);
+        T* D = at(c.dd);
+        const T* b = at(c.b);
+        sw_cheb_zero<T, DIM, VAR>(c.L, a.Kp, b, A, ChebStep{tab1(c), tab2(c)}, dsh, 0, 1);
+        __syncthreads();
+        T* cur = A;
+        T* oth = B;
+        for (int m = 1; m < deg; ++m) {
+            LoadPlain<T> ld{cur};
+            sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 1 ? cur : D, false, b, oth, m < deg - 1 ? D : nullptr,
+                                      ChebStep{tab1(c) + m * a.Kp, tab2(c) + m * a.Kp}, dsh, nullptr, 0, 1);
+            __syncthreads();
+            T* t = cur; cur = oth; oth = t;
+        }
+        if (l + 1 < a.nlev) {
+            sw_restrict<T, DIM, VAR>(c.L, a.lev[l + 1].L, a.Kp, cur, b, at(a.lev[l + 1].b), dsh, 0, 1);
+            __syncthreads();
+        }
+    }
+    // up: correction and post-smoothing (the coarsest level has no post-smoothing)
+    for (int l = a.nlev - 2; l >= 0; --l) {
+        const CoarseLevel& c = a.lev[l];
+        const int deg = c.deg;
+        T* A = at(c.xa);
+        T* B = at(c.xb);
+        T* D = at(c.dd);
+        const T* b = at(c.b);
+        T* cur = ((deg - 1) % 2 == 0) ? A : B;  // where the pre-smoothing ended
+        T* oth = cur == A ? B : A;
+        sw_prolong_add<T, DIM>(c.L, a.lev[l + 1].L, a.Kp, at(a.lev[l + 1].result), cur, 0, 1);
+        __syncthreads();
+        for (int m = 0; m < deg; ++m) {
+            LoadPlain<T> ld{cur};
+            sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 0 ? nullptr : D, false, b, oth, m < deg - 1 ? D : nullptr,
+                                      ChebStep{m == 0 ? nullptr : tab1(c) + m * a.Kp, tab2(c) + m * a.Kp}, dsh, nullptr,
+                                      0, 1);
+            __syncthreads();
+            T* t = cur; cur = oth; oth = t;
+        }
+    }
+    {
+        const int n = (int)(a.lev[0].L.N * a.Kp);
+        const T* src = at(a.lev[0].result);
+        T* dst = reinterpret_cast<T*>(a.x_out);
+        for (int i = tid; i < n; i += nthr) dst[i] = src[i];
+    }
 }
 
 // ------------------------------------------------------------------ host launchers
@@ -513,58 +777,95 @@ inline size_t shm(const Launch& g, int W) { return (size_t)g.C * g.PPB * W * siz
         else KERNEL<T, 3, true>__VA_ARGS__;                                          \
     } while (0)
 
+#define BURA_DISPATCH_PDL(dim, var, KERNEL, GRID, BLOCK, SMEM, S, ...)                                 \
+    do {                                                                                             \
+        if (dim == 2 && !var) launch_pdl(KERNEL<T, 2, false>, GRID, BLOCK, SMEM, S, __VA_ARGS__);    \
+        else if (dim == 2 && var) launch_pdl(KERNEL<T, 2, true>, GRID, BLOCK, SMEM, S, __VA_ARGS__); \
+        else if (dim == 3 && !var) launch_pdl(KERNEL<T, 3, false>, GRID, BLOCK, SMEM, S, __VA_ARGS__); \
+        else launch_pdl(KERNEL<T, 3, true>, GRID, BLOCK, SMEM, S, __VA_ARGS__);                      \
+    } while (0)
+
 template <class T>
 void Ops<T>::broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s) {
-    k_broadcast<T><<<g.blocks, blk(g), 0, s>>>(f, (int)N, g.Kp, K, r, x, p);
+    launch_pdl(k_broadcast<T>, dim3(g.blocks), blk(g), 0, s, f, (int)N, g.Kp, K, r, x, p);
 }
 
 template <class T>
-void Ops<T>::spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, const T* pold, T* pnew, T* q,
+void Ops<T>::spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, T* pa, T* pb, T* q,
                     const Red& red, cudaStream_t s) {
-    const size_t sh = shm(g, VecT<T>::W);
-    BURA_DISPATCH(dim, var, k_spmv_p, <<<g.blocks, blk(g), sh, s>>>(L, g.Kp, z, pold, pnew, q, red));
+    BURA_DISPATCH_PDL(dim, var, k_spmv_p, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, L, g.Kp, z, pa, pb, q, red);
 }
 
 template <class T>
-void Ops<T>::cg_update(const Launch& g, long long N, T* x, T* r, const T* p, const T* q, const Red& red,
-                       cudaStream_t s) {
-    k_cg_update<T><<<g.blocks, blk(g), shm(g, VecT<T>::W), s>>>((int)N, g.Kp, x, r, p, q, red);
+void Ops<T>::cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, const T* pb, const T* q,
+                       const Red& red, cudaStream_t s) {
+    launch_pdl(k_cg_update<T>, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, (int)N, g.Kp, x, r, pa, pb, q, red);
 }
 
 template <class T>
 void Ops<T>::cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStep cs,
                        const double* dsh, cudaStream_t s) {
-    BURA_DISPATCH(dim, var, k_cheb_zero, <<<g.blocks, blk(g), 0, s>>>(L, g.Kp, b, x, cs, dsh));
+    BURA_DISPATCH_PDL(dim, var, k_cheb_zero, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, x, cs, dsh);
 }
 
 template <class T>
 void Ops<T>::cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,
                        T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s) {
     const size_t sh = red.op != RED_NONE ? shm(g, VecT<T>::W) : 0;
-    BURA_DISPATCH(dim, var, k_cheb_step, <<<g.blocks, blk(g), sh, s>>>(L, g.Kp, xin, din, b, xout, dout, cs, dsh, red));
+    BURA_DISPATCH_PDL(dim, var, k_cheb_step, dim3(g.blocks), blk(g), sh, s, L, g.Kp, xin, din, b, xout, dout, cs, dsh,
+                      red);
+}
+
+template <class T>
+void Ops<T>::cheb_pre2(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* xout, T* dout, ChebStep cs0,
+                       ChebStep cs1, const double* dsh, cudaStream_t s) {
+    BURA_DISPATCH_PDL(dim, var, k_cheb_pre2, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, xout, dout, cs0, cs1, dsh);
+}
+
+template <class T>
+void Ops<T>::post_prolong(const Launch& g, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x, const T* ec,
+                          const T* b, T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red,
+                          cudaStream_t s) {
+    const size_t sh = red.op != RED_NONE ? shm(g, VecT<T>::W) : 0;
+    BURA_DISPATCH_PDL(dim, var, k_post_prolong, dim3(g.blocks), blk(g), sh, s, Lf, Lc, g.Kp, x, ec, b, xout, dout, cs,
+                      dsh, red);
 }
 
 template <class T>
 void Ops<T>::restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x, const T* b,
                           T* bc, const double* dsh, cudaStream_t s) {
-    BURA_DISPATCH(dim, var, k_restrict_res, <<<gc.blocks, blk(gc), 0, s>>>(Lf, Lc, gc.Kp, x, b, bc, dsh));
+    BURA_DISPATCH_PDL(dim, var, k_restrict_res, dim3(gc.blocks), blk(gc), 0, s, Lf, Lc, gc.Kp, x, b, bc, dsh);
 }
 
 template <class T>
 void Ops<T>::prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x, cudaStream_t s) {
-    if (dim == 2) k_prolong_add<T, 2><<<gf.blocks, blk(gf), 0, s>>>(Lf, Lc, gf.Kp, ec, x);
-    else k_prolong_add<T, 3><<<gf.blocks, blk(gf), 0, s>>>(Lf, Lc, gf.Kp, ec, x);
+    if (dim == 2) launch_pdl(k_prolong_add<T, 2>, dim3(gf.blocks), blk(gf), 0, s, Lf, Lc, gf.Kp, ec, x);
+    else launch_pdl(k_prolong_add<T, 3>, dim3(gf.blocks), blk(gf), 0, s, Lf, Lc, gf.Kp, ec, x);
+}
+
+template <class T>
+cudaError_t Ops<T>::prepare_coarse(int dim, bool var, size_t smem_bytes) {
+    const int b = (int)smem_bytes;
+    if (dim == 2 && !var) return cudaFuncSetAttribute(k_coarse_cycle<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dim == 2 && var) return cudaFuncSetAttribute(k_coarse_cycle<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dim == 3 && !var) return cudaFuncSetAttribute(k_coarse_cycle<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return cudaFuncSetAttribute(k_coarse_cycle<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+template <class T>
+void Ops<T>::coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s) {
+    BURA_DISPATCH_PDL(dim, var, k_coarse_cycle, dim3(1), blk(g1), (size_t)a.smem_bytes, s, a);
 }
 
 template <class T>
 void Ops<T>::apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const double* dsh,
                            cudaStream_t s) {
-    BURA_DISPATCH(dim, var, k_apply_shifted, <<<g.blocks, blk(g), 0, s>>>(L, g.Kp, x, y, dsh));
+    BURA_DISPATCH_PDL(dim, var, k_apply_shifted, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, y, dsh);
 }
 
 template <class T>
 void Ops<T>::dot(const Launch& g, long long N, const T* a, const T* b, const Red& red, cudaStream_t s) {
-    k_dot<T><<<g.blocks, blk(g), shm(g, VecT<T>::W), s>>>((int)N, g.Kp, a, b, red);
+    launch_pdl(k_dot<T>, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, (int)N, g.Kp, a, b, red);
 }
 
 }  // namespace bura

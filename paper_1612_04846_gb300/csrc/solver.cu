@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -32,36 +33,57 @@ struct Work {
     std::vector<Lev> L;
     T *x = nullptr, *r = nullptr, *pa = nullptr, *pb = nullptr, *q = nullptr;
     std::vector<T*> b, xa, xb, dd;
-    std::vector<std::vector<double*>> c1, c2;  // [level][step]
+    std::vector<double*> c1, c2;  // [level] -> deg rows of Kp coefficients
     std::vector<int> deg;
+    int lc = -1;                  // first level run by the single-CTA coarse kernel (-1: none)
+    size_t coarse_smem = 0;       // its shared-memory bytes
+    Launch gc{};                  // launch shape of that kernel
     double* dsh = nullptr;
     Scal* scal = nullptr;
     bool ready = false;
+    // the PCG loop captured once as a graph with a device-side conditional WHILE node
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    long long body_launches = 0;
 };
 
 int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
 
 // Kernel types for launch counting and per-kernel timing (fine level only).
-enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PROLONG, K_DOT, K_BCAST, K_RES64, K_CAST, K_CORR64,
-           K_WSUM, K_GATHER, K_NK };
-const char* const kNames[K_NK][2] = {
-    {"spmv_p_f64", "spmv_p_f32"},       {"cg_update_f64", "cg_update_f32"}, {"cheb_zero_f64", "cheb_zero_f32"},
-    {"cheb_step_f64", "cheb_step_f32"}, {"restrict_res_f64", "restrict_res_f32"},
-    {"prolong_add_f64", "prolong_add_f32"}, {"dot_f64", "dot_f32"}, {"broadcast_f64", "broadcast_f32"},
-    {"residual64", "residual64"},       {"cast_scaled", "cast_scaled"}, {"correct64", "correct64"},
-    {"weighted_sum", "weighted_sum"},   {"gather_systems", "gather_systems"}};
+enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
+           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_NK };
+// [kernel][f32][coarser level]
+const char* const kNames[K_NK][2][2] = {
+    {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
+    {{"cg_update_f64", "cg_update_f64@coarse"}, {"cg_update_f32", "cg_update_f32@coarse"}},
+    {{"cheb_zero_f64", "cheb_zero_f64@coarse"}, {"cheb_zero_f32", "cheb_zero_f32@coarse"}},
+    {{"cheb_step_f64", "cheb_step_f64@coarse"}, {"cheb_step_f32", "cheb_step_f32@coarse"}},
+    {{"restrict_res_f64", "restrict_res_f64@coarse"}, {"restrict_res_f32", "restrict_res_f32@coarse"}},
+    {{"cheb_pre2_f64", "cheb_pre2_f64@coarse"}, {"cheb_pre2_f32", "cheb_pre2_f32@coarse"}},
+    {{"prolong_add_f64", "prolong_add_f64@coarse"}, {"prolong_add_f32", "prolong_add_f32@coarse"}},
+    {{"coarse_cycle_f64", "coarse_cycle_f64@coarse"}, {"coarse_cycle_f32", "coarse_cycle_f32@coarse"}},
+    {{"dot_f64", "dot_f64@coarse"}, {"dot_f32", "dot_f32@coarse"}},
+    {{"broadcast_f64", "broadcast_f64"}, {"broadcast_f32", "broadcast_f32"}},
+    {{"norm2", "norm2"}, {"norm2", "norm2"}},
+    {{"residual64", "residual64"}, {"residual64", "residual64"}},
+    {{"cast_scaled", "cast_scaled"}, {"cast_scaled", "cast_scaled"}},
+    {{"correct64", "correct64"}, {"correct64", "correct64"}},
+    {{"weighted_sum", "weighted_sum"}, {"weighted_sum", "weighted_sum"}},
+    {{"gather_systems", "gather_systems"}, {"gather_systems", "gather_systems"}}};
+constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
     bool on = false;
     std::vector<cudaEvent_t> ev;  // 2 per timed launch
     struct Rec { int slot; double bytes; };
     std::vector<Rec> pending;
-    long long n[2 * K_NK] = {0};
-    double ms[2 * K_NK] = {0};
-    double bytes[2 * K_NK] = {0};
+    long long n[K_NK * 4] = {0};
+    double ms[K_NK * 4] = {0};
+    double bytes[K_NK * 4] = {0};
     long long launches = 0;  // every launch of the current solve
 };
-constexpr size_t kMaxTimed = 4096;
+constexpr size_t kMaxTimed = 16384;
 
 }  // namespace
 
@@ -91,6 +113,7 @@ struct bura_plan {
     std::vector<void*> allocs;
     bura_stats st{};
     Tracer tr;
+    cudaStream_t cap = nullptr;  // private stream used only to capture the PCG loop graphs
 };
 
 namespace {
@@ -105,6 +128,11 @@ cudaError_t g_last = cudaSuccess;
         }                                         \
     } while (0)
 #define CKL() CK(cudaGetLastError())
+#define CK_VOID(call)                             \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) g_last = e_;       \
+    } while (0)
 
 template <class P>
 int dalloc(bura_plan* p, P** ptr, size_t bytes) {
@@ -124,17 +152,18 @@ int dalloc(bura_plan* p, P** ptr, size_t bytes) {
         if (rc_ != BURA_OK) return rc_; \
     } while (0)
 
-// Count a launch; when profiling and the launch works on the fine level, bracket it by events.
+// Count a launch; when profiling, bracket it by events (finest-level and coarser-level launches are
+// accumulated separately).
 template <class F>
 void traced(bura_plan* p, int kid, bool is_f32, bool fine, double bytes, cudaStream_t s, F&& launch) {
     Tracer& t = p->tr;
     ++t.launches;
-    const bool rec = t.on && fine && t.pending.size() < kMaxTimed;
+    const bool rec = t.on && t.pending.size() < kMaxTimed;
     if (rec) cudaEventRecord(t.ev[2 * t.pending.size()], s);
     launch();
     if (rec) {
         cudaEventRecord(t.ev[2 * t.pending.size() + 1], s);
-        t.pending.push_back({kid * 2 + (is_f32 ? 1 : 0), bytes});
+        t.pending.push_back({(kid * 2 + (is_f32 ? 1 : 0)) * 2 + (fine ? 0 : 1), bytes});
     }
 }
 
@@ -152,13 +181,14 @@ void collect_trace(bura_plan* p) {
     t.pending.clear();
 }
 
-Launch make_launch(int Kp, int W, long long N, int nsm) {
+Launch make_launch(int Kp, int W, long long N, int nsm, int block_points, int blocks_per_sm) {
     Launch g;
     g.Kp = Kp;
     g.C = Kp / W;
-    g.PPB = g.C <= 4 ? 64 : 32;
+    g.PPB = block_points > 0 ? block_points : (g.C <= 4 ? 64 : 32);
+    if (g.PPB * g.C > kSweepThreads) g.PPB = kSweepThreads / g.C;
     long long tiles = (N + g.PPB - 1) / g.PPB;
-    long long cap = (long long)nsm * 8;
+    long long cap = (long long)nsm * (blocks_per_sm > 0 ? blocks_per_sm : 8);
     g.blocks = (int)std::max(1LL, std::min(tiles, cap));
     return g;
 }
@@ -316,12 +346,12 @@ int build_work(bura_plan* p, Work<T>& w) {
     w.xa.assign(nlev, nullptr);
     w.xb.assign(nlev, nullptr);
     w.dd.assign(nlev, nullptr);
-    w.c1.resize(nlev);
-    w.c2.resize(nlev);
+    w.c1.assign(nlev, nullptr);
+    w.c2.assign(nlev, nullptr);
     w.deg.resize(nlev);
     for (int l = 0; l < nlev; ++l) {
         const HostLevel& h = p->hl[l];
-        w.g[l] = make_launch(w.Kp, w.W, h.N, p->nsm);
+        w.g[l] = make_launch(w.Kp, w.W, h.N, p->nsm, p->opt.block_points, p->opt.blocks_per_sm);
         Lev& L = w.L[l];
         L.nx = h.n[0];
         L.ny = h.n[1];
@@ -345,7 +375,7 @@ int build_work(bura_plan* p, Work<T>& w) {
             }
         }
         const size_t vb = (size_t)h.N * w.Kp * sizeof(T);
-        if (l > 0) CA(dalloc(p, &w.b[l], vb));
+        CA(dalloc(p, &w.b[l], vb));  // level 0 uses the CG residual instead; kept for the coarse CTA
         CA(dalloc(p, &w.xa[l], vb));
         CA(dalloc(p, &w.xb[l], vb));
         CA(dalloc(p, &w.dd[l], vb));
@@ -358,15 +388,34 @@ int build_work(bura_plan* p, Work<T>& w) {
         if (coarsest && h.N == 1) {  // exact solve of the 1x1 system: x = b / (diag - d)
             for (int s = 0; s < p->K; ++s) C2[0][s] = p->var ? 1.0 : 1.0 / (h.amax - p->d[s]);
         }
-        w.c1[l].assign(deg, nullptr);
-        w.c2[l].assign(deg, nullptr);
-        for (int m = 0; m < deg; ++m) {
-            CA(dalloc(p, &w.c1[l][m], w.Kp * sizeof(double)));
-            CA(dalloc(p, &w.c2[l][m], w.Kp * sizeof(double)));
-            CK(cudaMemcpy(w.c1[l][m], C1[m].data(), w.Kp * sizeof(double), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(w.c2[l][m], C2[m].data(), w.Kp * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<double> f1((size_t)deg * w.Kp), f2((size_t)deg * w.Kp);
+        for (int m = 0; m < deg; ++m)
+            for (int s = 0; s < w.Kp; ++s) {
+                f1[(size_t)m * w.Kp + s] = C1[m][s];
+                f2[(size_t)m * w.Kp + s] = C2[m][s];
+            }
+        CA(dalloc(p, &w.c1[l], f1.size() * sizeof(double)));
+        CA(dalloc(p, &w.c2[l], f2.size() * sizeof(double)));
+        CK(cudaMemcpy(w.c1[l], f1.data(), f1.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w.c2[l], f2.data(), f2.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // the smallest levels run together in one CTA with all their vectors in shared memory
+    w.lc = -1;
+    w.coarse_smem = 0;
+    for (int l = 0; l < nlev; ++l) {
+        size_t bytes = 0;
+        for (int m = l; m < nlev; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.Kp * sizeof(T) + 15) / 16 * 16);
+        if (bytes <= kCoarseSmem && nlev - l <= kMaxCoarseLevels) {
+            w.lc = l;
+            w.coarse_smem = bytes;
+            break;
         }
     }
+    w.gc.Kp = w.Kp;
+    w.gc.C = w.C;
+    w.gc.PPB = kCoarseThreads / w.C;
+    w.gc.blocks = 1;
+    if (w.lc >= 0) CK(Ops<T>::prepare_coarse(p->dim, p->var, w.coarse_smem + kCoarseTables + KMAXP * sizeof(double)));
     const size_t vb0 = (size_t)p->hl[0].N * w.Kp * sizeof(T);
     CA(dalloc(p, &w.x, vb0));
     CA(dalloc(p, &w.r, vb0));
@@ -393,11 +442,64 @@ double vbytes(const bura_plan* p, int l, double vec, bool stencil) {
     return b;
 }
 
+template <class T>
+ChebStep step_of(const Work<T>& w, int l, int m, bool with_c1 = true) {
+    return ChebStep{with_c1 ? w.c1[l] + (size_t)m * w.Kp : nullptr, w.c2[l] + (size_t)m * w.Kp};
+}
+
+// Launch the single-CTA V-cycle over levels w.lc..nlev-1 for the right-hand side b (global); the
+// result of level lc is written to w.xa[lc].  Inside the CTA every level has b, xa, xb, dd in shared
+// memory; a level's pre-smoothing (zero step + deg-1 steps) ends in xa when deg-1 is even and its
+// post-smoothing toggles deg more times (the coarsest level has no post-smoothing).
+template <class T>
+T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
+    const int nlev = (int)p->hl.size();
+    CoarseArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nlev = nlev - w.lc;
+    a.Kp = w.Kp;
+    a.dsh = w.dsh;
+    a.b_in = b;
+    a.x_out = w.xa[w.lc];
+    unsigned int off = 0;
+    unsigned int cof = (unsigned int)w.coarse_smem;  // small tables follow the vectors
+    a.dsh_ofs = cof;
+    cof += KMAXP * sizeof(double);
+    for (int i = 0; i < a.nlev; ++i) {
+        const int l = w.lc + i;
+        const unsigned int vb = (unsigned int)((((size_t)p->hl[l].N * w.Kp * sizeof(T)) + 15) / 16 * 16);
+        CoarseLevel& c = a.lev[i];
+        c.L = w.L[l];
+        c.b = off;
+        c.xa = off + vb;
+        c.xb = off + 2 * vb;
+        c.dd = off + 3 * vb;
+        off += 4 * vb;
+        const int deg = w.deg[l];
+        const unsigned int pre = ((deg - 1) % 2 == 0) ? c.xa : c.xb;
+        const unsigned int other = pre == c.xa ? c.xb : c.xa;
+        c.result = (l == nlev - 1 || deg % 2 == 0) ? pre : other;
+        c.c1 = w.c1[l];
+        c.c2 = w.c2[l];
+        c.deg = deg;
+        const unsigned int tb = (unsigned int)(2 * deg * w.Kp * sizeof(double));
+        if (tb <= 4096 && cof + tb <= w.coarse_smem + KMAXP * sizeof(double) + kCoarseTables) {
+            c.cofs = cof;
+            cof += tb;
+        } else {
+            c.cofs = kNoCopy;
+        }
+    }
+    a.smem_bytes = cof;
+    traced(p, K_COARSE, sizeof(T) == 4, w.lc == 0, 0.0, s,
+           [&] { Ops<T>::coarse_cycle(w.gc, p->dim, p->var, a, s); });
+    return w.xa[w.lc];
+}
+
 // Symmetric V-cycle on level l for rhs b; returns the buffer holding the result.  With rz_fused
 // (level 0 only) the last smoothing step also forms r^T z and the CG beta of every system.
 template <class T>
 T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream_t s) {
-    const int nlev = (int)p->hl.size();
     const int dim = p->dim;
     const bool var = p->var;
     const Launch& g = w.g[l];
@@ -405,33 +507,41 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     const int deg = w.deg[l];
     const bool f32 = sizeof(T) == 4;
     const bool fine = (l == 0);
+    Red none{p->partial, w.scal, nullptr, RED_NONE, 0};
+    Red beta{p->partial, w.scal, nullptr, RED_BETA, 0};
+    if (l == w.lc) {  // the rest of the hierarchy in one CTA
+        T* res = coarse_part(p, w, b, s);
+        if (rz_fused)
+            traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, res, beta, s); });
+        return res;
+    }
     T* A = w.xa[l];
     T* B = w.xb[l];
     T* D = w.dd[l];
-    Red none{p->partial, w.scal, nullptr, RED_NONE};
-    Red beta{p->partial, w.scal, nullptr, RED_BETA};
-    auto step = [&](T* xin, T* din, T* xout, T* dout, int m, bool c1, const Red& red) {
-        const double vec = 2.0 + (din ? 1.0 : 0.0) + (dout ? 1.0 : 0.0);
-        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, vec, true), s, [&] {
-            Ops<T>::cheb_step(g, L, dim, var, xin, din, b, xout, dout, ChebStep{c1 ? w.c1[l][m] : nullptr, w.c2[l][m]},
-                              w.dsh, red, s);
-        });
-    };
-    traced(p, K_CHEB0, f32, fine, vbytes<T>(p, l, 2.0, var), s, [&] {
-        Ops<T>::cheb_zero(g, L, dim, var, b, A, ChebStep{w.c1[l][0], w.c2[l][0]}, w.dsh, s);
-    });
     T* cur = A;
     T* oth = B;
-    for (int m = 1; m < deg; ++m) {
-        step(cur, m == 1 ? cur : D, oth, m < deg - 1 ? D : nullptr, m, true, none);
-        std::swap(cur, oth);
+    // pre-smoothing from a zero initial guess; the first two Chebyshev steps share one sweep
+    if (deg == 1) {
+        traced(p, K_CHEB0, f32, fine, vbytes<T>(p, l, 2.0, var), s,
+               [&] { Ops<T>::cheb_zero(g, L, dim, var, b, A, step_of(w, l, 0), w.dsh, s); });
+    } else {
+        traced(p, K_PRE2, f32, fine, vbytes<T>(p, l, deg > 2 ? 3.0 : 2.0, true), s, [&] {
+            Ops<T>::cheb_pre2(g, L, dim, var, b, A, deg > 2 ? D : nullptr, step_of(w, l, 0), step_of(w, l, 1), w.dsh, s);
+        });
+        for (int m = 2; m < deg; ++m) {
+            T* dout = m < deg - 1 ? D : nullptr;
+            traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0 + (dout ? 1.0 : 0.0), true), s, [&] {
+                Ops<T>::cheb_step(g, L, dim, var, cur, D, b, oth, dout, step_of(w, l, m), w.dsh, none, s);
+            });
+            std::swap(cur, oth);
+        }
     }
-    if (l == nlev - 1) {  // coarsest: exact 1-point solve or a fixed Chebyshev polynomial
+    if (l == (int)p->hl.size() - 1) {  // coarsest level on the grid kernels: the Chebyshev solve above
         if (rz_fused)
             traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, cur, beta, s); });
         return cur;
     }
-    // coarse-grid correction
+    // coarse-grid correction: residual + restriction, then the coarser levels
     traced(p, K_RESTRICT, f32, fine, vbytes<T>(p, l, 2.0, true) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
         Ops<T>::restrict_res(w.g[l + 1], L, w.L[l + 1], dim, var, cur, b, w.b[l + 1], w.dsh, s);
     });
@@ -441,47 +551,91 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     // post-smoothing with the same polynomial (symmetric preconditioner)
     for (int m = 0; m < deg; ++m) {
         const bool last = (m == deg - 1);
-        step(cur, m == 0 ? nullptr : D, oth, last ? nullptr : D, m, m != 0, (rz_fused && last) ? beta : none);
+        T* din = m == 0 ? nullptr : D;
+        T* dout = last ? nullptr : D;
+        const Red& red = (rz_fused && last) ? beta : none;
+        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 3.0 + (din ? 1.0 : 0.0) + (dout ? 1.0 : 0.0), true), s, [&] {
+            Ops<T>::cheb_step(g, L, dim, var, cur, din, b, oth, dout, step_of(w, l, m, m != 0), w.dsh, red, s);
+        });
         std::swap(cur, oth);
     }
     return cur;
 }
 
+// One PCG iteration body: z = M r (with r.z and beta), p = z + beta p and q = (A - dI) p (with p.q and
+// alpha), x += alpha p, r -= alpha q (with r.r, convergence and loop control).
+template <class T>
+int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) {
+    const Launch& g = w.g[0];
+    const Lev& L = w.L[0];
+    const bool f32 = sizeof(T) == 4;
+    Red ralpha{p->partial, w.scal, nullptr, RED_ALPHA, 0};
+    Red rconv{p->partial, w.scal, nullptr, RED_CONV, cond};
+    T* z = vcycle<T>(p, w, 0, w.r, true, s);
+    traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s,
+           [&] { Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s); });
+    traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s,
+           [&] { Ops<T>::cg_update(g, L.N, w.x, w.r, w.pa, w.pb, w.q, rconv, s); });
+    CKL();
+    return BURA_OK;
+}
+
+// Capture the PCG loop once: a conditional WHILE node whose body is one iteration; the last block
+// of k_cg_update clears the condition when every system has converged, on breakdown, or at the cap.
+template <class T>
+int build_graph(bura_plan* p, Work<T>& w) {
+    if (w.exec) return BURA_OK;
+    CK(cudaGraphCreate(&w.graph, 0));
+    CK(cudaGraphConditionalHandleCreate(&w.cond, w.graph, 1u, cudaGraphCondAssignDefault));
+    // the parameter struct holds a union with no default constructor: start from zeroed storage
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = w.cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, w.graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(p->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long before = p->tr.launches;
+    const bool was_on = p->tr.on;
+    p->tr.on = false;
+    int rc = pcg_body<T>(p, w, (unsigned long long)w.cond, p->cap);
+    p->tr.on = was_on;
+    w.body_launches = p->tr.launches - before;
+    p->tr.launches = before;
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->cap, &captured);
+    if (rc != BURA_OK) return rc;
+    CK(e);
+    CK(cudaGraphInstantiate(&w.exec, w.graph, 0));
+    return BURA_OK;
+}
+
 // Multi-shift PCG on the work set w: r holds the right-hand sides, x = 0, pa = 0 and the Scal
 // record is initialised by the caller.  Returns BURA_OK, BURA_ENOCONV or BURA_ENOTSPD.
 template <class T>
-int pcg(bura_plan* p, Work<T>& w, int max_it, int* iters_out, cudaStream_t s) {
-    const Launch& g = w.g[0];
-    const Lev& L = w.L[0];
-    Red ralpha{p->partial, w.scal, nullptr, RED_ALPHA};
-    Red rconv{p->partial, w.scal, nullptr, RED_CONV};
-    T* pold = w.pa;
-    T* pnew = w.pb;
-    const bool f32 = sizeof(T) == 4;
-    T* z = vcycle<T>(p, w, 0, w.r, true, s);
-    CKL();
-    int it = 0;
-    int status = BURA_ENOCONV;
-    while (it < max_it) {
-        traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s,
-               [&] { Ops<T>::spmv_p(g, L, p->dim, p->var, z, pold, pnew, w.q, ralpha, s); });
-        std::swap(pold, pnew);
-        traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s,
-               [&] { Ops<T>::cg_update(g, L.N, w.x, w.r, pold, w.q, rconv, s); });
-        CKL();
-        ++it;
-        CK(cudaMemcpyAsync(&p->hscal->nactive, &w.scal->nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+int pcg(bura_plan* p, Work<T>& w, int* iters_out, cudaStream_t s) {
+    if (p->tr.on) {  // per-kernel timing: launch the same iteration directly, one sync per iteration
+        for (;;) {
+            CA(pcg_body<T>(p, w, 0, s));
+            CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const Scal& h = *p->hscal;
+            if (h.breakdown || h.nactive == 0 || h.it >= h.max_it) break;
+        }
+    } else {
+        CA(build_graph<T>(p, w));
+        CK(cudaGraphLaunch(w.exec, s));
+        CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (p->hscal->breakdown) { status = BURA_ENOTSPD; break; }
-        if (p->hscal->nactive == 0) { status = BURA_OK; break; }
-        z = vcycle<T>(p, w, 0, w.r, true, s);
-        CKL();
+        p->tr.launches += w.body_launches * p->hscal->it;
     }
-    // copy back the whole record for statistics
-    CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    *iters_out = it;
-    return status;
+    const Scal& h = *p->hscal;
+    *iters_out = h.it;
+    if (h.breakdown) return BURA_ENOTSPD;
+    return h.nactive == 0 ? BURA_OK : BURA_ENOCONV;
 }
 
 int init_scal(bura_plan* p, Scal* dev, const double* thr, const int* active, cudaStream_t s) {
@@ -499,9 +653,11 @@ int init_scal(bura_plan* p, Scal* dev, const double* thr, const int* active, cud
     }
     h.nactive = na;
     h.ticket = 0u;
+    h.it = 0;
+    h.max_it = p->opt.max_iters;
+    h.parity = 0;
     *p->hscal = h;
     CK(cudaMemcpyAsync(dev, p->hscal, sizeof(Scal), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));
     return BURA_OK;
 }
 
@@ -529,10 +685,8 @@ int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     const long long N = p->hl[0].N;
     traced(p, K_BCAST, false, true, (double)N * 8 + vbytes<double>(p, 0, 3.0, false), s,
            [&] { Ops<double>::broadcast(w.g[0], f, N, p->K, w.r, w.x, w.pa, s); });
-    CKL();
-    Red store{p->partial, w.scal, p->red_out, RED_STORE};
-    traced(p, K_DOT, false, true, vbytes<double>(p, 0, 1.0, false), s,
-           [&] { Ops<double>::dot(w.g[0], N, w.r, w.r, store, s); });
+    Red store{p->partial, p->scal_outer, p->red_out, RED_STORE, 0};
+    traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
     CKL();
     CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -544,7 +698,7 @@ int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     CA(init_scal(p, w.scal, thr, act, s));
     int it = 0;
     int rc = BURA_OK;
-    if (fnorm2 > 0) rc = pcg<double>(p, w, p->opt.max_iters, &it, s);
+    if (fnorm2 > 0) rc = pcg<double>(p, w, &it, s);
     p->st.iters = it;
     p->st.outer = 1;
     for (int j = 0; j <= p->k; ++j) p->st.shift_iters[j] = fnorm2 > 0 ? p->hscal->iters[j] : 0;
@@ -560,23 +714,28 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     const Lev& L64 = p->w64.L[0];
     const long long N = p->hl[0].N;
     CK(cudaMemsetAsync(p->v64, 0, (size_t)N * g64.Kp * sizeof(double), s));
-    Red store{p->partial, p->scal_outer, p->red_out, RED_STORE};
-    double fnorm2 = -1.0;
+    Red store{p->partial, p->scal_outer, p->red_out, RED_STORE, 0};
+    // the residual of the zero initial guess is f itself: only its norm is needed
+    traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
+    CKL();
+    CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double fnorm2 = p->hbuf[0];
     double thr64[KMAXP] = {0};
     double rr[KMAXP] = {0};
+    thresholds(p, tol, fnorm2, thr64);
+    for (int j = 0; j < p->K; ++j) rr[j] = fnorm2;
     int total_it = 0, outer = 0;
     int rc = BURA_ENOCONV;
     int siters[KMAXP] = {0};
     for (;;) {
-        traced(p, K_RES64, false, true, (double)N * 8 + vbytes<double>(p, 0, 2.0, true), s,
-               [&] { launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s); });
-        CKL();
-        CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        for (int j = 0; j < p->K; ++j) rr[j] = p->hbuf[j];
-        if (fnorm2 < 0) {
-            fnorm2 = rr[0];
-            thresholds(p, tol, fnorm2, thr64);
+        if (outer > 0) {
+            traced(p, K_RES64, false, true, (double)N * 8 + vbytes<double>(p, 0, 2.0, true), s,
+                   [&] { launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s); });
+            CKL();
+            CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int j = 0; j < p->K; ++j) rr[j] = p->hbuf[j];
         }
         int act[KMAXP] = {0};
         int na = 0;
@@ -603,12 +762,16 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
         }
         CK(cudaMemcpyAsync(p->scale, hs, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(p->invscale, his, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
-        traced(p, K_CAST, false, true, vbytes<double>(p, 0, 1.0, false) + vbytes<float>(p, 0, 3.0, false), s,
-               [&] { launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s); });
+        if (outer == 0)
+            traced(p, K_CAST, false, true, (double)N * 8 + vbytes<float>(p, 0, 3.0, false), s,
+                   [&] { launch_cast_f(w.g[0], N, p->K, f, p->invscale, w.r, w.x, w.pa, s); });
+        else
+            traced(p, K_CAST, false, true, vbytes<double>(p, 0, 1.0, false) + vbytes<float>(p, 0, 3.0, false), s,
+                   [&] { launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s); });
         CKL();
         CA(init_scal(p, w.scal, thr, act, s));
         int it = 0;
-        int irc = pcg<float>(p, w, p->opt.max_iters, &it, s);
+        int irc = pcg<float>(p, w, &it, s);
         if (irc == BURA_ENOTSPD) return irc;
         for (int j = 0; j < p->K; ++j) siters[j] += p->hscal->iters[j];
         total_it += it;
@@ -676,7 +839,8 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if (opt) o = *opt;
     if (o.precision != BURA_PREC_FP64 && o.precision != BURA_PREC_MIXED) return BURA_EINVAL;
     if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio > 1) || o.max_iters < 1 ||
-        o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000)
+        o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000 ||
+        o.block_points < 0 || o.block_points > 1024 || o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
         return BURA_EINVAL;
 
     bura_plan* p = new (std::nothrow) bura_plan();
@@ -731,6 +895,10 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     p->lambda_lo = p->hl[0].lmin * (1.0 - 1e-12);
 
     if (cudaGetDevice(&p->dev) != cudaSuccess) return fail(BURA_ECUDA);
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        p->cap = nullptr;
+        return fail(BURA_ECUDA);
+    }
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess || nsm <= 0)
         return fail(BURA_ECUDA);
@@ -745,7 +913,8 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     const size_t v64b = (size_t)N * p->w64.Kp * sizeof(double);
     if ((rc = dalloc(p, &p->v64, v64b)) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->r64, v64b)) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->partial, (size_t)nsm * 8 * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    const size_t max_blocks = (size_t)nsm * std::max(8, o.blocks_per_sm);
+    if ((rc = dalloc(p, &p->partial, max_blocks * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
@@ -873,9 +1042,9 @@ int bura_set_profiling(bura_plan* p, int enable) {
 int bura_get_profile(const bura_plan* p, int max_entries, bura_kernel_prof* out, int* n_out) {
     if (!p || !n_out || (max_entries > 0 && !out)) return BURA_EINVAL;
     int n = 0;
-    for (int slot = 0; slot < 2 * K_NK && n < max_entries; ++slot) {
+    for (int slot = 0; slot < kSlots && n < max_entries; ++slot) {
         if (p->tr.n[slot] == 0) continue;
-        out[n].name = kNames[slot / 2][slot % 2];
+        out[n].name = kNames[slot / 4][(slot / 2) % 2][slot % 2];
         out[n].launches = p->tr.n[slot];
         out[n].ms = p->tr.ms[slot];
         out[n].bytes = p->tr.bytes[slot];
@@ -889,11 +1058,22 @@ int bura_destroy(bura_plan* p) {
     if (!p) return BURA_OK;
     cudaSetDevice(p->dev);
     for (auto& e : p->tr.ev) cudaEventDestroy(e);
+    if (p->w64.exec) cudaGraphExecDestroy(p->w64.exec);
+    if (p->w64.graph) cudaGraphDestroy(p->w64.graph);
+    if (p->w32.exec) cudaGraphExecDestroy(p->w32.exec);
+    if (p->w32.graph) cudaGraphDestroy(p->w32.graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
     for (void* q : p->allocs) cudaFree(q);
     if (p->hscal) cudaFreeHost(p->hscal);
     if (p->hbuf) cudaFreeHost(p->hbuf);
     delete p;
     return BURA_OK;
+}
+
+const char* bura_last_cuda_error(void) {
+    static thread_local char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", cudaGetErrorName(g_last), cudaGetErrorString(g_last));
+    return buf;
 }
 
 const char* bura_strerror(int status) {
