@@ -305,8 +305,8 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
         double tot = 0.0;
         for (int g = 0; g < G; ++g) tot += sm[g * Kp + tid];
         red.partial[(size_t)blockIdx.x * Kp + tid] = tot;
+        __threadfence();  // only the writers of the partials need their stores visible before the ticket
     }
-    __threadfence();
     __syncthreads();
     if (tid == 0) {
         const unsigned t = atomicAdd(&red.scal->ticket, 1u);
@@ -315,10 +315,24 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    // every partial is read once, coalesced, with several loads in flight per thread; thread t always
+    // adds system t % Kp in a fixed order, so the sum does not depend on block finishing order
     part = 0.0;
     if (tid < Kp * G) {
         const int s = tid % Kp, g = tid / Kp;
-        for (int b = g; b < (int)gridDim.x; b += G) part += __ldcg(red.partial + (size_t)b * Kp + s);
+        const int nbk = (int)gridDim.x;
+        int b = g;
+        for (; b + 3 * G < nbk; b += 4 * G) {
+            const double v0 = __ldcg(red.partial + (size_t)b * Kp + s);
+            const double v1 = __ldcg(red.partial + (size_t)(b + G) * Kp + s);
+            const double v2 = __ldcg(red.partial + (size_t)(b + 2 * G) * Kp + s);
+            const double v3 = __ldcg(red.partial + (size_t)(b + 3 * G) * Kp + s);
+            part += v0;
+            part += v1;
+            part += v2;
+            part += v3;
+        }
+        for (; b < nbk; b += G) part += __ldcg(red.partial + (size_t)b * Kp + s);
     }
     __syncthreads();
     if (tid < Kp * G) sm[tid] = part;

@@ -811,10 +811,10 @@ void bura_default_options(bura_options* opt) {
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = BURA_PREC_MIXED;
     opt->smoother_degree = 2;
-    opt->smoother_ratio = 8.0;
+    opt->smoother_ratio = 4.0;
     opt->max_iters = 200;
     opt->max_outer = 12;
-    opt->inner_rtol = 1e-5;
+    opt->inner_rtol = 1e-4;
     opt->coarse_degree = 0;
 }
 
