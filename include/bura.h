@@ -70,7 +70,8 @@ typedef struct {
                              quarter of the spectrum, which full coarsening leaves to the smoother) */
     int max_iters;        /* cap on PCG iterations per (inner) solve; default 200 */
     int max_outer;        /* cap on FP64 refinement steps (mixed precision); default 12 */
-    double inner_rtol;    /* relative residual reduction of one FP32 inner solve; default 1e-4 */
+    double inner_rtol;    /* largest relative residual reduction asked of one FP32 inner solve; the FP64
+                             refinement plans ceil(log need / log inner_rtol) steps; default 1e-5 */
     int coarse_degree;    /* Chebyshev degree on the coarsest level when it has > 1 point; 0 = auto */
     int block_points;     /* grid points per CTA of the level sweeps (CTA = points x 16-byte chunks); 0 = auto */
     int blocks_per_sm;    /* CTAs per SM of the grid-stride sweeps; 0 = auto */

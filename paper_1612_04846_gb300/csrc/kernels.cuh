@@ -65,10 +65,14 @@ struct ChebStep {
 
 enum ReduceOp { RED_NONE = 0, RED_ALPHA = 1, RED_CONV = 2, RED_BETA = 3, RED_STORE = 4 };
 
+// Grid reductions are two-level: blocks in groups of kRedGroup; the last block of a group to finish
+// sums the group's block partials, and the last group to finish sums the group partials.
+constexpr int kRedGroup = 16;
 struct Red {
-    double* partial;   // [gridDim.x * Kp] scratch
+    double* partial;          // [gridDim.x * Kp] block partials, then [groups * Kp] group partials
+    unsigned int* tickets;    // [max groups + 1] counters, zero between reductions
     Scal* scal;
-    double* out;       // RED_STORE destination [Kp]
+    double* out;              // RED_STORE destination [Kp]
     int op;
     unsigned long long cond;  // cudaGraphConditionalHandle of a captured PCG loop (0: none)
 };
@@ -86,6 +90,7 @@ struct CoarseLevel {
 };
 
 constexpr unsigned int kNoCopy = 0xffffffffu;
+constexpr long long kExactPoints = 64;  // a coarse-CTA level this small is solved with dense inverses
 constexpr int kMaxCoarseLevels = 16;
 // Grid sweeps run CTAs of at most 256 threads; the register cap of 64 keeps 8 CTAs of 128 threads
 // (or 4 of 256) resident per SM, so one wave covers the whole grid.
@@ -102,6 +107,8 @@ struct CoarseArgs {
     void* x_out;       // its V-cycle result (global)
     unsigned int smem_bytes;
     unsigned int dsh_ofs;  // shared-memory byte offset of a copy of the shifts (KMAXP doubles)
+    int exact;             // level (index in lev[]) solved exactly by x = M_j b with dense inverses; -1: none
+    const void* minv;      // M_j[(row * n + col) * Kp + j], n = points of that level (global, element type T)
     CoarseLevel lev[kMaxCoarseLevels];
 };
 

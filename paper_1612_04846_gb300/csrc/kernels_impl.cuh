@@ -301,6 +301,11 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     __syncthreads();
     if (tid < Kp * G) sm[tid] = part;
     __syncthreads();
+    const int nblk = (int)gridDim.x;
+    const int group = (int)blockIdx.x / kRedGroup;
+    const int ngroups = (nblk + kRedGroup - 1) / kRedGroup;
+    const int gsize = min(kRedGroup, nblk - group * kRedGroup);
+    double* part2 = red.partial + (size_t)nblk * Kp;
     if (tid < Kp) {
         double tot = 0.0;
         for (int g = 0; g < G; ++g) tot += sm[g * Kp + tid];
@@ -308,31 +313,46 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
         __threadfence();  // only the writers of the partials need their stores visible before the ticket
     }
     __syncthreads();
+    // level 1: the last block of the group sums the group's block partials in block order
     if (tid == 0) {
-        const unsigned t = atomicAdd(&red.scal->ticket, 1u);
-        am_last = (t == gridDim.x - 1);
+        const unsigned t = atomicAdd(&red.tickets[group], 1u);
+        am_last = (t == (unsigned)gsize - 1);
     }
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    // every partial is read once, coalesced, with several loads in flight per thread; thread t always
-    // adds system t % Kp in a fixed order, so the sum does not depend on block finishing order
+    if (tid < Kp) {
+        const double* src = red.partial + (size_t)group * kRedGroup * Kp + tid;
+        double v[kRedGroup];
+#pragma unroll
+        for (int b = 0; b < kRedGroup; ++b) v[b] = b < gsize ? __ldcg(src + (size_t)b * Kp) : 0.0;
+        double tot = 0.0;
+#pragma unroll
+        for (int b = 0; b < kRedGroup; ++b) tot += v[b];
+        part2[(size_t)group * Kp + tid] = tot;
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        red.tickets[group] = 0u;
+        const unsigned t = atomicAdd(&red.tickets[ngroups], 1u);
+        am_last = (t == (unsigned)ngroups - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    // level 2: the last group sums the group partials in group order; thread t adds system t % Kp
     part = 0.0;
     if (tid < Kp * G) {
         const int s = tid % Kp, g = tid / Kp;
-        const int nbk = (int)gridDim.x;
         int b = g;
-        for (; b + 3 * G < nbk; b += 4 * G) {
-            const double v0 = __ldcg(red.partial + (size_t)b * Kp + s);
-            const double v1 = __ldcg(red.partial + (size_t)(b + G) * Kp + s);
-            const double v2 = __ldcg(red.partial + (size_t)(b + 2 * G) * Kp + s);
-            const double v3 = __ldcg(red.partial + (size_t)(b + 3 * G) * Kp + s);
+        for (; b + G < ngroups; b += 2 * G) {
+            const double v0 = __ldcg(part2 + (size_t)b * Kp + s);
+            const double v1 = __ldcg(part2 + (size_t)(b + G) * Kp + s);
             part += v0;
             part += v1;
-            part += v2;
-            part += v3;
         }
-        for (; b < nbk; b += G) part += __ldcg(red.partial + (size_t)b * Kp + s);
+        for (; b < ngroups; b += G) part += __ldcg(part2 + (size_t)b * Kp + s);
     }
     __syncthreads();
     if (tid < Kp * G) sm[tid] = part;
@@ -344,7 +364,7 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     }
     __syncthreads();
     if (tid == 0) {
-        red.scal->ticket = 0u;
+        red.tickets[ngroups] = 0u;
         if (red.op == RED_CONV) {
             Scal* S = red.scal;
             int na = 0;
@@ -734,6 +754,27 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
         T* B = at(c.xb);
         T* D = at(c.dd);
         const T* b = at(c.b);
+        if (l == a.exact) {  // dense exact solve of every shifted system: A = M_j b
+            constexpr int W = VecT<T>::W;
+            const int n = (int)c.L.N;
+            const int off = threadIdx.x * W;
+            const T* M = reinterpret_cast<const T*>(a.minv);
+            for (int i = threadIdx.y; i < n; i += blockDim.y) {
+                T acc[W];
+                for (int v = 0; v < W; ++v) acc[v] = T(0);
+                const T* row = M + (size_t)i * n * a.Kp + off;
+#pragma unroll 4
+                for (int jj = 0; jj < n; ++jj) {
+                    T m[W], bv[W];
+                    vld(row + (size_t)jj * a.Kp, m);
+                    vld(b + (size_t)jj * a.Kp + off, bv);
+                    for (int v = 0; v < W; ++v) acc[v] = fma(m[v], bv[v], acc[v]);
+                }
+                vst(A + (size_t)i * a.Kp + off, acc);
+            }
+            __syncthreads();
+            break;
+        }
         sw_cheb_zero<T, DIM, VAR>(c.L, a.Kp, b, A, ChebStep{tab1(c), tab2(c)}, dsh, 0, 1);
         __syncthreads();
         T* cur = A;

@@ -2,11 +2,14 @@
 // device workspaces) and the solve drivers (FP64 multi-shift PCG, and FP32 PCG inside FP64
 // iterative refinement), followed by the FP64 weighted sum u = sum_j c_j v_j (eq. (Rgeneral)).
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/bura.h"
@@ -25,30 +28,6 @@ struct HostLevel {
     double amax;         // max diagonal of the scaled level operator
     double lmin;         // lower bound on lambda_min of the scaled level operator
 };
-
-template <class T>
-struct Work {
-    int Kp = 0, W = 0, C = 0;
-    std::vector<Launch> g;
-    std::vector<Lev> L;
-    T *x = nullptr, *r = nullptr, *pa = nullptr, *pb = nullptr, *q = nullptr;
-    std::vector<T*> b, xa, xb, dd;
-    std::vector<double*> c1, c2;  // [level] -> deg rows of Kp coefficients
-    std::vector<int> deg;
-    int lc = -1;                  // first level run by the single-CTA coarse kernel (-1: none)
-    size_t coarse_smem = 0;       // its shared-memory bytes
-    Launch gc{};                  // launch shape of that kernel
-    double* dsh = nullptr;
-    Scal* scal = nullptr;
-    bool ready = false;
-    // the PCG loop captured once as a graph with a device-side conditional WHILE node
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle cond = 0;
-    long long body_launches = 0;
-};
-
-int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
 
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
@@ -85,6 +64,33 @@ struct Tracer {
 };
 constexpr size_t kMaxTimed = 16384;
 
+template <class T>
+struct Work {
+    int Kp = 0, W = 0, C = 0;
+    std::vector<Launch> g;
+    std::vector<Lev> L;
+    T *x = nullptr, *r = nullptr, *pa = nullptr, *pb = nullptr, *q = nullptr;
+    std::vector<T*> b, xa, xb, dd;
+    std::vector<double*> c1, c2;  // [level] -> deg rows of Kp coefficients
+    std::vector<int> deg;
+    int lc = -1;                  // first level run by the single-CTA coarse kernel (-1: none)
+    int le = -1;                  // level solved exactly with dense inverses inside that CTA (-1: none)
+    T* minv = nullptr;            // the inverses, [row][col][Kp]
+    size_t coarse_smem = 0;       // its shared-memory bytes
+    Launch gc{};                  // launch shape of that kernel
+    double* dsh = nullptr;
+    Scal* scal = nullptr;
+    bool ready = false;
+    // the PCG loop captured once as a graph with a device-side conditional WHILE node
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    long long body_launches = 0;
+};
+
+int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
+
+
 }  // namespace
 
 struct bura_plan {
@@ -102,6 +108,7 @@ struct bura_plan {
     double* r64 = nullptr;   // FP64 residuals, Kp64 layout
     double* cdev = nullptr;  // c_j, Kp64 entries
     double* partial = nullptr;
+    unsigned int* tickets = nullptr;
     double* red_out = nullptr;  // [KMAXP]
     double* scale = nullptr;    // [KMAXP] refinement scales
     double* invscale = nullptr;
@@ -158,12 +165,13 @@ template <class F>
 void traced(bura_plan* p, int kid, bool is_f32, bool fine, double bytes, cudaStream_t s, F&& launch) {
     Tracer& t = p->tr;
     ++t.launches;
+    const int slot = (kid * 2 + (is_f32 ? 1 : 0)) * 2 + (fine ? 0 : 1);
     const bool rec = t.on && t.pending.size() < kMaxTimed;
     if (rec) cudaEventRecord(t.ev[2 * t.pending.size()], s);
     launch();
     if (rec) {
         cudaEventRecord(t.ev[2 * t.pending.size() + 1], s);
-        t.pending.push_back({(kid * 2 + (is_f32 ? 1 : 0)) * 2 + (fine ? 0 : 1), bytes});
+        t.pending.push_back({slot, bytes});
     }
 }
 
@@ -324,6 +332,65 @@ void cheb_tables(const HostLevel& h, bool var, const std::vector<double>& d, int
     }
 }
 
+// Dense (A_l - d_j I)^{-1} of a tiny level for every system j, laid out [row][col][Kp] (zero for the
+// padding systems); Gauss-Jordan elimination with partial pivoting in FP64.
+void dense_inverses(const HostLevel& h, int dim, bool var, const std::vector<double>& d, int K, int Kp,
+                    std::vector<double>& out) {
+    const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
+    const int n = (int)h.N;
+    std::vector<double> A((size_t)n * n, 0.0);
+    auto id = [&](int i, int j, int l) { return (l * ny + j) * nx + i; };
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const int P = id(i, j, l);
+                double w[6];
+                if (var) {
+                    w[0] = h.a[0][((size_t)l * ny + j) * (nx + 1) + i] * h.w[0];
+                    w[1] = h.a[0][((size_t)l * ny + j) * (nx + 1) + i + 1] * h.w[0];
+                    w[2] = h.a[1][((size_t)l * (ny + 1) + j) * nx + i] * h.w[1];
+                    w[3] = h.a[1][((size_t)l * (ny + 1) + j + 1) * nx + i] * h.w[1];
+                    w[4] = dim == 3 ? h.a[2][((size_t)l * ny + j) * nx + i] * h.w[2] : 0.0;
+                    w[5] = dim == 3 ? h.a[2][((size_t)(l + 1) * ny + j) * nx + i] * h.w[2] : 0.0;
+                } else {
+                    w[0] = w[1] = h.w[0];
+                    w[2] = w[3] = h.w[1];
+                    w[4] = w[5] = dim == 3 ? h.w[2] : 0.0;
+                }
+                A[(size_t)P * n + P] = w[0] + w[1] + w[2] + w[3] + w[4] + w[5];
+                if (i > 0) A[(size_t)P * n + id(i - 1, j, l)] = -w[0];
+                if (i < nx - 1) A[(size_t)P * n + id(i + 1, j, l)] = -w[1];
+                if (j > 0) A[(size_t)P * n + id(i, j - 1, l)] = -w[2];
+                if (j < ny - 1) A[(size_t)P * n + id(i, j + 1, l)] = -w[3];
+                if (l > 0) A[(size_t)P * n + id(i, j, l - 1)] = -w[4];
+                if (l < nz - 1) A[(size_t)P * n + id(i, j, l + 1)] = -w[5];
+            }
+    out.assign((size_t)n * n * Kp, 0.0);
+    std::vector<double> M((size_t)n * 2 * n);
+    for (int s = 0; s < K; ++s) {
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < 2 * n; ++c)
+                M[(size_t)r * 2 * n + c] = c < n ? A[(size_t)r * n + c] - (r == c ? d[s] : 0.0) : (c - n == r ? 1.0 : 0.0);
+        for (int c = 0; c < n; ++c) {
+            int pr = c;
+            for (int r = c + 1; r < n; ++r)
+                if (std::fabs(M[(size_t)r * 2 * n + c]) > std::fabs(M[(size_t)pr * 2 * n + c])) pr = r;
+            if (pr != c)
+                for (int k2 = 0; k2 < 2 * n; ++k2) std::swap(M[(size_t)pr * 2 * n + k2], M[(size_t)c * 2 * n + k2]);
+            const double piv = M[(size_t)c * 2 * n + c];
+            for (int k2 = 0; k2 < 2 * n; ++k2) M[(size_t)c * 2 * n + k2] /= piv;
+            for (int r = 0; r < n; ++r) {
+                if (r == c) continue;
+                const double fct = M[(size_t)r * 2 * n + c];
+                if (fct == 0.0) continue;
+                for (int k2 = 0; k2 < 2 * n; ++k2) M[(size_t)r * 2 * n + k2] -= fct * M[(size_t)c * 2 * n + k2];
+            }
+        }
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c) out[((size_t)r * n + c) * Kp + s] = M[(size_t)r * 2 * n + n + c];
+    }
+}
+
 int coarse_degree_auto(const HostLevel& h, double d0) {
     if (h.N == 1) return 1;
     const double mds = -d0;
@@ -399,17 +466,31 @@ int build_work(bura_plan* p, Work<T>& w) {
         CK(cudaMemcpy(w.c1[l], f1.data(), f1.size() * sizeof(double), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(w.c2[l], f2.data(), f2.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    // the first level with at most kExactPoints points is solved exactly (dense inverses); the levels
+    // below it are never visited
+    w.le = -1;
+    for (int l = 0; l < nlev; ++l)
+        if (p->hl[l].N <= kExactPoints) { w.le = l; break; }
+    const int last = w.le >= 0 ? w.le : nlev - 1;
     // the smallest levels run together in one CTA with all their vectors in shared memory
     w.lc = -1;
     w.coarse_smem = 0;
-    for (int l = 0; l < nlev; ++l) {
+    for (int l = 0; l <= last; ++l) {
         size_t bytes = 0;
-        for (int m = l; m < nlev; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.Kp * sizeof(T) + 15) / 16 * 16);
-        if (bytes <= kCoarseSmem && nlev - l <= kMaxCoarseLevels) {
+        for (int m = l; m <= last; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.Kp * sizeof(T) + 15) / 16 * 16);
+        if (bytes <= kCoarseSmem && last - l + 1 <= kMaxCoarseLevels) {
             w.lc = l;
             w.coarse_smem = bytes;
             break;
         }
+    }
+    if (w.lc < 0) w.le = -1;  // the dense solve lives in the coarse CTA only
+    if (w.le >= 0) {
+        std::vector<double> inv;
+        dense_inverses(p->hl[w.le], p->dim, p->var, p->d, p->K, w.Kp, inv);
+        std::vector<T> tv(inv.begin(), inv.end());
+        CA(dalloc(p, &w.minv, tv.size() * sizeof(T)));
+        CK(cudaMemcpy(w.minv, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice));
     }
     w.gc.Kp = w.Kp;
     w.gc.C = w.C;
@@ -456,7 +537,9 @@ T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
     const int nlev = (int)p->hl.size();
     CoarseArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.nlev = nlev - w.lc;
+    a.nlev = (w.le >= 0 ? w.le : nlev - 1) - w.lc + 1;
+    a.exact = w.le >= 0 ? w.le - w.lc : -1;
+    a.minv = w.minv;
     a.Kp = w.Kp;
     a.dsh = w.dsh;
     a.b_in = b;
@@ -478,7 +561,8 @@ T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
         const int deg = w.deg[l];
         const unsigned int pre = ((deg - 1) % 2 == 0) ? c.xa : c.xb;
         const unsigned int other = pre == c.xa ? c.xb : c.xa;
-        c.result = (l == nlev - 1 || deg % 2 == 0) ? pre : other;
+        if (i == a.exact) c.result = c.xa;  // the dense solve writes xa
+        else c.result = (l == nlev - 1 || deg % 2 == 0) ? pre : other;
         c.c1 = w.c1[l];
         c.c2 = w.c2[l];
         c.deg = deg;
@@ -507,8 +591,8 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     const int deg = w.deg[l];
     const bool f32 = sizeof(T) == 4;
     const bool fine = (l == 0);
-    Red none{p->partial, w.scal, nullptr, RED_NONE, 0};
-    Red beta{p->partial, w.scal, nullptr, RED_BETA, 0};
+    Red none{p->partial, p->tickets, w.scal, nullptr, RED_NONE, 0};
+    Red beta{p->partial, p->tickets, w.scal, nullptr, RED_BETA, 0};
     if (l == w.lc) {  // the rest of the hierarchy in one CTA
         T* res = coarse_part(p, w, b, s);
         if (rz_fused)
@@ -569,8 +653,8 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
     const Launch& g = w.g[0];
     const Lev& L = w.L[0];
     const bool f32 = sizeof(T) == 4;
-    Red ralpha{p->partial, w.scal, nullptr, RED_ALPHA, 0};
-    Red rconv{p->partial, w.scal, nullptr, RED_CONV, cond};
+    Red ralpha{p->partial, p->tickets, w.scal, nullptr, RED_ALPHA, 0};
+    Red rconv{p->partial, p->tickets, w.scal, nullptr, RED_CONV, cond};
     T* z = vcycle<T>(p, w, 0, w.r, true, s);
     traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s,
            [&] { Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s); });
@@ -613,15 +697,29 @@ int build_graph(bura_plan* p, Work<T>& w) {
     return BURA_OK;
 }
 
+// Host function that holds the stream until the host thread has queued an iteration (bounded: ~10 s).
+void CUDART_CB wait_gate(void* arg) {
+    std::atomic<int>* g = reinterpret_cast<std::atomic<int>*>(arg);
+    for (long i = 0; i < 10000000L && g->load() == 0; ++i) std::this_thread::sleep_for(std::chrono::microseconds(1));
+}
+
 // Multi-shift PCG on the work set w: r holds the right-hand sides, x = 0, pa = 0 and the Scal
 // record is initialised by the caller.  Returns BURA_OK, BURA_ENOCONV or BURA_ENOTSPD.
 template <class T>
 int pcg(bura_plan* p, Work<T>& w, int* iters_out, cudaStream_t s) {
-    if (p->tr.on) {  // per-kernel timing: launch the same iteration directly, one sync per iteration
+    if (p->tr.on) {
+        // per-kernel timing: the iteration's launches (each between two events) are queued behind a
+        // host gate that opens only once all of them are queued, so the kernels run back to back and
+        // no host launch time falls between an event pair; one sync per iteration
         for (;;) {
-            CA(pcg_body<T>(p, w, 0, s));
+            std::atomic<int> gate(0);
+            CK(cudaLaunchHostFunc(s, wait_gate, &gate));
+            const int rc = pcg_body<T>(p, w, 0, s);
+            gate.store(1);
+            CA(rc);
             CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            collect_trace(p);
             const Scal& h = *p->hscal;
             if (h.breakdown || h.nactive == 0 || h.it >= h.max_it) break;
         }
@@ -685,7 +783,7 @@ int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     const long long N = p->hl[0].N;
     traced(p, K_BCAST, false, true, (double)N * 8 + vbytes<double>(p, 0, 3.0, false), s,
            [&] { Ops<double>::broadcast(w.g[0], f, N, p->K, w.r, w.x, w.pa, s); });
-    Red store{p->partial, p->scal_outer, p->red_out, RED_STORE, 0};
+    Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
     traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
     CKL();
     CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -714,7 +812,7 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     const Lev& L64 = p->w64.L[0];
     const long long N = p->hl[0].N;
     CK(cudaMemsetAsync(p->v64, 0, (size_t)N * g64.Kp * sizeof(double), s));
-    Red store{p->partial, p->scal_outer, p->red_out, RED_STORE, 0};
+    Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
     // the residual of the zero initial guess is f itself: only its norm is needed
     traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
     CKL();
@@ -725,6 +823,16 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     double rr[KMAXP] = {0};
     thresholds(p, tol, fnorm2, thr64);
     for (int j = 0; j < p->K; ++j) rr[j] = fnorm2;
+    // Plan the refinement: system j needs its residual reduced by need_j = sqrt(thr64_j) / ||f||; one
+    // FP32 inner solve is asked for at most a reduction of inner_rtol, so n_j = ceil(log need_j /
+    // log inner_rtol) steps are needed and each takes the even share need_j^(1/n_j).
+    double step_target[KMAXP] = {0};
+    for (int j = 0; j < p->K; ++j) {
+        const double need = fnorm2 > 0 ? std::sqrt(thr64[j] / fnorm2) : 1.0;
+        if (need >= 1.0) { step_target[j] = 1.0; continue; }
+        const int n = std::max(1, (int)std::ceil(std::log(need) / std::log(p->opt.inner_rtol) - 1e-9));
+        step_target[j] = std::pow(need, 1.0 / n);
+    }
     int total_it = 0, outer = 0;
     int rc = BURA_ENOCONV;
     int siters[KMAXP] = {0};
@@ -754,9 +862,10 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
             hs[j] = a ? std::sqrt(rr[j]) : 0.0;
             his[j] = a ? 1.0 / hs[j] : 0.0;
             if (a) {
-                // relative target of this inner solve (the scaled rhs has unit norm)
+                // relative target of this inner solve (the scaled rhs has unit norm): the planned
+                // share, or less if that already meets the FP64 threshold (with a margin of 2)
                 const double need = 0.5 * std::sqrt(thr64[j] / rr[j]);
-                const double t = std::max(p->opt.inner_rtol, need);
+                const double t = std::max(step_target[j] * 0.5, need);
                 thr[j] = t * t;
             }
         }
@@ -814,7 +923,7 @@ void bura_default_options(bura_options* opt) {
     opt->smoother_ratio = 4.0;
     opt->max_iters = 200;
     opt->max_outer = 12;
-    opt->inner_rtol = 1e-4;
+    opt->inner_rtol = 1e-5;
     opt->coarse_degree = 0;
 }
 
@@ -914,7 +1023,10 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if ((rc = dalloc(p, &p->v64, v64b)) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->r64, v64b)) != BURA_OK) return fail(rc);
     const size_t max_blocks = (size_t)nsm * std::max(8, o.blocks_per_sm);
-    if ((rc = dalloc(p, &p->partial, max_blocks * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    const size_t max_groups = (max_blocks + kRedGroup - 1) / kRedGroup;
+    if ((rc = dalloc(p, &p->partial, (max_blocks + max_groups) * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->tickets, (max_groups + 1) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
+    if (cudaMemset(p->tickets, 0, (max_groups + 1) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
     if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
