@@ -49,7 +49,9 @@ Readings where the paper leaves a choice (each also listed in the design doc)
   the spread floors near 1e-14 E).
 * Step 1 search: the paper refines on shrinking local meshes (remark (2)); here
   zeros are bracketed by bisection in log t and maxima found by golden-section
-  search in log t after a coarse scan.
+  search in log t after a coarse scan.  The end points t = 0 and t = 1 are extreme
+  points of the BURA error (Lemma BURA_caracter, item 3) and are never displaced by
+  the insertion of Step 1(iv).
 * Sign convention: i = 1 is s = -1 (t = 0), so f(0) - r(0) = -E and r(0) = +E,
   matching Lemma 2.2 ("BURA_caracter") item 3 and eq. (c0,beta).
 * Normalisation of the monomial form: q_k = 1, as in Tables ta:coeff1-3.
@@ -240,7 +242,9 @@ def remez_bura(alpha, k, pts0, dps=60, N=80, delta_rel=mp.mpf(10) ** -13):
             new = [_argmax_between(P, pbar, qbar, bnd[i], bnd[i + 1]) for i in range(l)]
             # Step 1 (iii)-(iv): global maximiser, inserted keeping the sign pattern.
             ts = _global_argmax(P, pbar, qbar, new)
-            if ts not in new:
+            # t = 0 and t = 1 are extreme points of the BURA error (Lemma BURA_caracter, item 3):
+            # they stay in the set, so a maximiser that would displace them is not inserted
+            if ts not in new and new[1] < ts < new[-2]:
                 j = max(i for i in range(l) if new[i] < ts) if ts > new[0] else 0
                 if j + 1 < l and mp.sign(P.e(pbar, qbar, ts)) != mp.sign(P.e(pbar, qbar, new[j])):
                     new[j + 1] = ts

@@ -239,3 +239,41 @@ def test_smallest_and_largest_tabulated_k(lib):
         u, st, rc, _ = _solve(lib, shape, 0.5, k, f, 1e-11, lib.BURA_PREC_FP64)
         ref = tables.entry(0.5, k)
         assert rc == lib.BURA_OK and _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"])) <= 1e-10
+
+
+def test_full_size_3d_variable_coefficients(lib):
+    """The 3D workload (255^3 interior, 7-point -div(a grad u) with a log-uniform in [1e-2, 1] on 8^3
+    blocks, alpha = 0.5, k = 9, f ~ N(0,1), mixed precision, tol 1e-6).  No closed form exists, so the
+    oracle's own sparse operator checks every system's residual r_j = f - (A - d_j I) v_j, and the
+    rigorous bound ||u - u_r|| <= sum_j c_j ||r_j|| / (lambda_lo - d_j) with lambda_lo = min(a) times the
+    closed-form smallest eigenvalue of the constant-coefficient operator (the quadratic form of A is
+    at least min(a) times that of the unit-coefficient operator, face by face) must be <= tol ||f||.
+    u itself must equal sum_j c_j v_j."""
+    shape, alpha, k, tol = (255, 255, 255), 0.5, 9, 1e-6
+    nps = _np_shape(shape)
+    faces = W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 2)
+    f = W.rhs_normal(nps, 3)
+    plan = lib.bura_setup(shape, alpha, k, faces=faces, options=_opts(lib, lib.BURA_PREC_MIXED))
+    try:
+        fd = torch.from_numpy(f).cuda()
+        V = torch.zeros((k + 1, f.size), dtype=torch.float64, device="cuda")
+        assert lib.bura_solve_systems(plan, fd, V, tol) == lib.BURA_OK
+        ud = torch.zeros_like(fd)
+        assert lib.bura_solve(plan, fd, ud, tol) == lib.BURA_OK
+        torch.cuda.synchronize()
+        c, d, E = lib.bura_get_rational(plan, k)
+        V = V.cpu().numpy()
+        u = ud.cpu().numpy()
+    finally:
+        lib.bura_destroy(plan)
+    A, _ = operators.scaled_matrix(nps, faces)
+    amin = min(float(a.min()) for a in faces)
+    lam_lo = amin * float(exact.eigenvalues(nps).min())
+    fn = np.linalg.norm(f)
+    bound = 0.0
+    for j in range(k + 1):
+        rj = f - (A @ V[j] - d[j] * V[j])
+        bound += c[j] * np.linalg.norm(rj) / (lam_lo - d[j])
+    assert bound <= tol * fn, bound / fn
+    usum = sum(c[j] * V[j] for j in range(k + 1))
+    assert _rel(u, usum) <= 1e-12
