@@ -2,14 +2,11 @@
 // device workspaces) and the solve drivers (FP64 multi-shift PCG, and FP32 PCG inside FP64
 // iterative refinement), followed by the FP64 weighted sum u = sum_j c_j v_j (eq. (Rgeneral)).
 #include <algorithm>
-#include <atomic>
-#include <chrono>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "../../include/bura.h"
@@ -697,26 +694,13 @@ int build_graph(bura_plan* p, Work<T>& w) {
     return BURA_OK;
 }
 
-// Host function that holds the stream until the host thread has queued an iteration (bounded: ~10 s).
-void CUDART_CB wait_gate(void* arg) {
-    std::atomic<int>* g = reinterpret_cast<std::atomic<int>*>(arg);
-    for (long i = 0; i < 10000000L && g->load() == 0; ++i) std::this_thread::sleep_for(std::chrono::microseconds(1));
-}
-
 // Multi-shift PCG on the work set w: r holds the right-hand sides, x = 0, pa = 0 and the Scal
 // record is initialised by the caller.  Returns BURA_OK, BURA_ENOCONV or BURA_ENOTSPD.
 template <class T>
 int pcg(bura_plan* p, Work<T>& w, int* iters_out, cudaStream_t s) {
-    if (p->tr.on) {
-        // per-kernel timing: the iteration's launches (each between two events) are queued behind a
-        // host gate that opens only once all of them are queued, so the kernels run back to back and
-        // no host launch time falls between an event pair; one sync per iteration
+    if (p->tr.on) {  // per-kernel timing: the same iteration launched directly, one sync per iteration
         for (;;) {
-            std::atomic<int> gate(0);
-            CK(cudaLaunchHostFunc(s, wait_gate, &gate));
-            const int rc = pcg_body<T>(p, w, 0, s);
-            gate.store(1);
-            CA(rc);
+            CA(pcg_body<T>(p, w, 0, s));
             CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             collect_trace(p);
