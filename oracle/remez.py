@@ -188,15 +188,21 @@ def _golden_max(P, pbar, qbar, a, b):
 
 
 def _argmax_between(P, pbar, qbar, a, b, nscan=12):
-    """Step 1(ii): argmax of |f - r| on [a, b] (a may be 0, b may be 1)."""
-    lo = b * mp.mpf(10) ** (-(mp.mp.dps - 15)) if a == 0 else a
-    cands = ([mp.mpf(0)] if a == 0 else []) + [lo * (b / lo) ** (mp.mpf(i) / nscan) for i in range(nscan + 1)]
+    """Step 1(ii): argmax of |f - r| on [a, b] (a may be 0, b may be 1).
+
+    t = 0 and t = 1 are extreme points of the BURA error (Lemma BURA_caracter, item 3), so on the
+    first and the last interval the point is the end point itself: a scan would otherwise pick a
+    neighbour whose |f - r| equals the end value up to rounding (t = 1e-58, or 1 - 4e-16)."""
+    if a == 0:
+        return mp.mpf(0)
+    if b == 1:
+        return mp.mpf(1)
+    lo = a
+    cands = [lo * (b / lo) ** (mp.mpf(i) / nscan) for i in range(nscan)] + [b]
     vals = [abs(P.e(pbar, qbar, t)) for t in cands]
     i = max(range(len(cands)), key=vals.__getitem__)
     t = cands[i]
-    if t == 0 or t == 1:
-        return t
-    left = cands[i - 1] if i > 0 and cands[i - 1] > 0 else t / 10
+    left = cands[i - 1] if i > 0 else a
     right = cands[i + 1] if i + 1 < len(cands) else b
     return _golden_max(P, pbar, qbar, max(left, lo), min(right, b))
 
@@ -354,15 +360,36 @@ def bura(alpha, k, dps=60):
                 pts = _extend_points(bura(0.5, k - 1, dps).eta)
         else:
             nxt = 0.5 if abs(alpha - 0.5) <= 0.05 + 1e-12 else round(alpha - (0.05 if alpha > 0.5 else -0.05), 6)
-            pts = list(bura(nxt, k, dps).eta)
-        # The Step 3 matrix loses about 4 digits per decade that eta_2 sits below 1 (its rows at
-        # the clustered points near s = -1 become nearly equal), so the working precision grows
-        # with -log10(eta_2) of the starting points.
-        work = max(dps, int(mp.ceil(40 + 4 * (-mp.log10(pts[1])))))
-        with mp.workdps(work):
-            pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=work)
+            pbar, qbar, E, pts = _continue_alpha(alpha, k, nxt, list(bura(nxt, k, dps).eta), dps)
+            with mp.workdps(_work_dps(pts, dps)):
+                p, q, d, c, zeta = partial_fractions(pbar, qbar)
+                return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
+        with mp.workdps(_work_dps(pts, dps)):
+            pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=mp.mp.dps)
             p, q, d, c, zeta = partial_fractions(pbar, qbar)
             return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
+
+
+def _work_dps(pts, dps):
+    """The Step 3 matrix loses about 4 digits per decade that eta_2 sits below 1 (its rows at the
+    clustered points near s = -1 become nearly equal), so the working precision grows with
+    -log10(eta_2) of the starting points."""
+    return max(dps, int(mp.ceil(40 + 4 * (-mp.log10(pts[1])))))
+
+
+def _continue_alpha(alpha, k, alpha0, pts0, dps, depth=0):
+    """Algorithm 1 at alpha from the extreme points pts0 of the BURA at alpha0.  When the iteration
+    from there does not converge (it can slide onto the degree-(k-1) best approximation, whose error
+    cannot equioscillate on 2k+2 points), the step alpha0 -> alpha is halved, up to four times."""
+    with mp.workdps(_work_dps(pts0, dps)):
+        try:
+            return remez_bura(alpha, k, pts0, dps=mp.mp.dps)
+        except RuntimeError:
+            if depth >= 4:
+                raise
+    mid = round((alpha + alpha0) / 2, 8)
+    _, _, _, pmid = _continue_alpha(mid, k, alpha0, pts0, dps, depth + 1)
+    return _continue_alpha(alpha, k, mid, list(pmid), dps, depth + 1)
 
 
 def error_at(res, t):

@@ -4,7 +4,8 @@ Every value in the table comes from ``oracle.remez.bura`` and nothing else.
 Tests, smoke() and bench.py read the table instead of re-running the
 multi-precision Remez (mpmath is not installed on every machine that runs them).
 
-Usage:  python tests/golden/make_bura_table.py [alpha ...]   (merges into the file)
+Usage:  python tests/golden/make_bura_table.py [--k K1-K2] [alpha ...]   (merges into the file;
+        default k = 1..10)
 """
 import json
 import os
@@ -32,13 +33,13 @@ def entry(res):
             "eta": [s(v) for v in res.eta]}
 
 
-def main(alphas, kmax):
+def main(alphas, kmin, kmax):
     table = {}
     if os.path.exists(OUT):
         with open(OUT) as fh:
             table = json.load(fh)
     for a in alphas:
-        for k in range(1, kmax + 1):
+        for k in range(kmin, kmax + 1):
             t0 = time.time()
             res = bura(a, k)
             table["%.4f/%d" % (a, k)] = entry(res)
@@ -55,5 +56,11 @@ def main(alphas, kmax):
 
 
 if __name__ == "__main__":
-    al = [float(x) for x in sys.argv[1:]] or ALPHAS
-    main(al, KMAX)
+    args = sys.argv[1:]
+    kmin, kmax = 1, KMAX
+    if args and args[0] == "--k":
+        lo, hi = args[1].split("-")
+        kmin, kmax = int(lo), int(hi)
+        args = args[2:]
+    al = [float(x) for x in args] or ALPHAS
+    main(al, kmin, kmax)
