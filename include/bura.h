@@ -62,6 +62,21 @@ typedef struct {
     int coef_kind; /* bura_coef_kind */
 } bura_grid;
 
+/* How the small levels of the multigrid V-cycle are run. */
+typedef enum {
+    BURA_COARSE_AUTO = 0,    /* CLUSTER where the device launches thread-block clusters, else CTA */
+    BURA_COARSE_CLUSTER = 1, /* levels with <= 16384 points in one thread-block cluster (vectors in L2);
+                                bura_setup returns BURA_EINVAL on a device without cluster launch */
+    BURA_COARSE_CTA = 2,     /* the levels that fit 200 KB of shared memory in a single CTA */
+    BURA_COARSE_NONE = 3     /* every level as grid-wide kernels; the coarsest level is smoothed only */
+} bura_coarse_kernel;
+
+/* How the level sweeps of the large levels are run. */
+typedef enum {
+    BURA_SWEEP_AUTO = 0, /* TMA-staged tiles (FP32, 2-D, constant coefficients, >= 1 tile per SM), else GRID */
+    BURA_SWEEP_GRID = 1  /* grid-stride kernels with direct global loads everywhere */
+} bura_sweep_kind;
+
 /* Solver options; bura_default_options() fills the defaults. */
 typedef struct {
     int precision;        /* bura_precision; default BURA_PREC_MIXED */
@@ -75,7 +90,11 @@ typedef struct {
     int coarse_degree;    /* Chebyshev degree on the coarsest level when it has > 1 point; 0 = auto */
     int block_points;     /* grid points per CTA of the level sweeps (CTA = points x 16-byte chunks); 0 = auto */
     int blocks_per_sm;    /* CTAs per SM of the grid-stride sweeps; 0 = auto */
-    int reserved[6];
+    int coarse_kernel;    /* bura_coarse_kernel; default BURA_COARSE_AUTO */
+    int cluster_size;     /* largest cluster tried for BURA_COARSE_CLUSTER: 2, 4, 8 or 16; 0 = 16.  The
+                             size used is the largest power of two <= this that the device co-schedules */
+    int sweeps;           /* bura_sweep_kind; default BURA_SWEEP_AUTO */
+    int reserved[3];
 } bura_options;
 
 /* Statistics of the last bura_solve*/

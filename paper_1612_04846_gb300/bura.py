@@ -21,6 +21,8 @@ BURA_OK, BURA_EINVAL, BURA_ENOMEM, BURA_EREMEZ = 0, -1, -2, -3
 BURA_ENOTSPD, BURA_ENOCONV, BURA_ETIMEOUT, BURA_ECUDA, BURA_ERANGE = -4, -5, -6, -7, -8
 BURA_COEF_CONSTANT, BURA_COEF_FACES = 0, 1
 BURA_PREC_FP64, BURA_PREC_MIXED = 0, 1
+BURA_COARSE_AUTO, BURA_COARSE_CLUSTER, BURA_COARSE_CTA, BURA_COARSE_NONE = 0, 1, 2, 3
+BURA_SWEEP_AUTO, BURA_SWEEP_GRID = 0, 1
 
 
 class bura_grid(C.Structure):
@@ -31,7 +33,8 @@ class bura_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("smoother_degree", C.c_int), ("smoother_ratio", C.c_double),
                 ("max_iters", C.c_int), ("max_outer", C.c_int), ("inner_rtol", C.c_double),
                 ("coarse_degree", C.c_int), ("block_points", C.c_int), ("blocks_per_sm", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("coarse_kernel", C.c_int), ("cluster_size", C.c_int), ("sweeps", C.c_int),
+                ("reserved", C.c_int * 3)]
 
 
 class bura_stats(C.Structure):

@@ -54,6 +54,7 @@ struct Scal {
     int it;               // PCG iterations done in the current inner solve
     int max_it;           // cap on it (device-side loop control)
     int parity;           // which of the two direction buffers holds the current p
+    int fault;            // set by a kernel whose bounded wait on its own copies gave up
 };
 
 // Chebyshev step coefficients of one level: d_m = c1 d_{m-1} + c2 Dinv res (c2 includes 1/(diag - d)
@@ -88,6 +89,30 @@ struct CoarseLevel {
     unsigned int cofs;  // shared-memory byte offset of a copy of c1 then c2 (kNoCopy: read them from global)
     int deg;
 };
+
+// One level of the clustered coarse V-cycle (vectors in global memory, L2 resident).
+struct ClusterLevel {
+    Lev L;
+    void* b;
+    void* xa;
+    void* xb;
+    void* dd;
+    const void* result;  // buffer holding this level's V-cycle result
+    const double* c1;
+    const double* c2;
+    int deg;
+};
+
+struct ClusterArgs {
+    int nlev;
+    int Kp;
+    int exact;           // level solved with dense inverses (index in lev[]), -1: none
+    const void* minv;
+    const double* dsh;
+    ClusterLevel lev[16];
+};
+constexpr int kClusterThreads = 512;        // threads per CTA of the clustered coarse V-cycle
+constexpr long long kClusterPoints = 16384; // levels with at most this many points run in the cluster
 
 constexpr unsigned int kNoCopy = 0xffffffffu;
 constexpr long long kExactPoints = 64;  // a coarse-CTA level this small is solved with dense inverses
@@ -138,6 +163,10 @@ struct Ops {
     static void prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x,
                             cudaStream_t s);
     static void coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s);
+    static cudaError_t coarse_cluster(const Launch& g1, int csize, int dim, bool var, const ClusterArgs& a,
+                                      cudaStream_t s);
+    // Largest cluster size (16, 8, 4, 2 or 1) that the device can co-schedule for this kernel.
+    static cudaError_t cluster_prepare(int dim, bool var, int threads, int want, int* csize);
     static cudaError_t prepare_coarse(int dim, bool var, size_t smem_bytes);
     static void apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const double* dsh,
                               cudaStream_t s);

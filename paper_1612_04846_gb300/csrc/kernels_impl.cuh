@@ -6,7 +6,11 @@
 // coarse kernel runs the whole small-level part of the V-cycle with (0, 1) and __syncthreads()
 // between dependent sweeps.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace bura {
 
@@ -374,7 +378,7 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
             S->parity ^= 1;
             // device-side loop control of a captured PCG loop (conditional WHILE node)
             if (red.cond) {
-                const bool go = na > 0 && !S->breakdown && S->it < S->max_it;
+                const bool go = na > 0 && !S->breakdown && !S->fault && S->it < S->max_it;
                 cudaGraphSetConditional(red.cond, go ? 1u : 0u);
             }
         }
@@ -820,6 +824,86 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ clustered coarse V-cycle
+// The small levels (levels 0..nlev-1 of the argument, all L2 resident) run in one thread-block
+// cluster: every sweep is spread over the cluster's CTAs (tile stride = cluster size) and the
+// hardware cluster barrier (release/acquire) separates dependent sweeps.  The first level's right-hand
+// side is its b buffer; each level's result ends in the buffer the host predicts (lev[].result).
+template <class T, int DIM, bool VAR>
+__global__ void __launch_bounds__(kClusterThreads, 1) k_coarse_cluster(ClusterArgs a) {
+    pdl_wait();
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int ncta = (int)cl.num_blocks();
+    for (int l = 0; l < a.nlev; ++l) {
+        const ClusterLevel& c = a.lev[l];
+        const int deg = c.deg;
+        T* A = reinterpret_cast<T*>(c.xa);
+        T* B = reinterpret_cast<T*>(c.xb);
+        T* D = reinterpret_cast<T*>(c.dd);
+        const T* b = reinterpret_cast<const T*>(c.b);
+        if (l == a.exact) {  // dense exact solve of every shifted system: A = M_j b
+            constexpr int W = VecT<T>::W;
+            const int n = (int)c.L.N;
+            const int off = threadIdx.x * W;
+            const T* M = reinterpret_cast<const T*>(a.minv);
+            for (int i = rank * blockDim.y + threadIdx.y; i < n; i += ncta * blockDim.y) {
+                T acc[W];
+                for (int v = 0; v < W; ++v) acc[v] = T(0);
+                const T* row = M + (size_t)i * n * a.Kp + off;
+#pragma unroll 4
+                for (int jj = 0; jj < n; ++jj) {
+                    T m[W], bv[W];
+                    vld(row + (size_t)jj * a.Kp, m);
+                    vld(b + (size_t)jj * a.Kp + off, bv);
+                    for (int v = 0; v < W; ++v) acc[v] = fma(m[v], bv[v], acc[v]);
+                }
+                vst(A + (size_t)i * a.Kp + off, acc);
+            }
+            cl.sync();
+            break;
+        }
+        sw_cheb_zero<T, DIM, VAR>(c.L, a.Kp, b, A, ChebStep{c.c1, c.c2}, a.dsh, rank, ncta);
+        cl.sync();
+        T* cur = A;
+        T* oth = B;
+        for (int m = 1; m < deg; ++m) {
+            LoadPlain<T> ld{cur};
+            // after the step from zero the previous Chebyshev direction is the iterate itself
+            sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 1 ? nullptr : D, m == 1, b, oth, m < deg - 1 ? D : nullptr,
+                                      ChebStep{c.c1 + m * a.Kp, c.c2 + m * a.Kp}, a.dsh, nullptr, rank, ncta);
+            cl.sync();
+            T* t = cur; cur = oth; oth = t;
+        }
+        if (l + 1 < a.nlev) {
+            sw_restrict<T, DIM, VAR>(c.L, a.lev[l + 1].L, a.Kp, cur, b, reinterpret_cast<T*>(a.lev[l + 1].b), a.dsh,
+                                     rank, ncta);
+            cl.sync();
+        }
+    }
+    for (int l = a.nlev - 2; l >= 0; --l) {
+        const ClusterLevel& c = a.lev[l];
+        const int deg = c.deg;
+        T* A = reinterpret_cast<T*>(c.xa);
+        T* B = reinterpret_cast<T*>(c.xb);
+        T* D = reinterpret_cast<T*>(c.dd);
+        const T* b = reinterpret_cast<const T*>(c.b);
+        T* cur = ((deg - 1) % 2 == 0) ? A : B;  // where the pre-smoothing ended
+        T* oth = cur == A ? B : A;
+        sw_prolong_add<T, DIM>(c.L, a.lev[l + 1].L, a.Kp, reinterpret_cast<const T*>(a.lev[l + 1].result), cur, rank,
+                               ncta);
+        cl.sync();
+        for (int m = 0; m < deg; ++m) {
+            LoadPlain<T> ld{cur};
+            sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 0 ? nullptr : D, false, b, oth, m < deg - 1 ? D : nullptr,
+                                      ChebStep{m == 0 ? nullptr : c.c1 + m * a.Kp, c.c2 + m * a.Kp}, a.dsh, nullptr,
+                                      rank, ncta);
+            cl.sync();
+            T* t = cur; cur = oth; oth = t;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host launchers
 inline dim3 blk(const Launch& g) { return dim3(g.C, g.PPB); }
 inline size_t shm(const Launch& g, int W) { return (size_t)g.C * g.PPB * W * sizeof(double); }
@@ -910,6 +994,61 @@ cudaError_t Ops<T>::prepare_coarse(int dim, bool var, size_t smem_bytes) {
 template <class T>
 void Ops<T>::coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s) {
     BURA_DISPATCH_PDL(dim, var, k_coarse_cycle, dim3(1), blk(g1), (size_t)a.smem_bytes, s, a);
+}
+
+template <class T>
+cudaError_t Ops<T>::coarse_cluster(const Launch& g1, int csize, int dim, bool var, const ClusterArgs& a,
+                                   cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = blk(g1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (dim == 2 && !var) return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 2, false>, a);
+    if (dim == 2 && var) return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 2, true>, a);
+    if (dim == 3 && !var) return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 3, false>, a);
+    return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 3, true>, a);
+}
+
+template <class T, int DIM, bool VAR>
+cudaError_t cluster_prepare_t(int threads, int want, int* csize) {
+    auto fn = k_coarse_cluster<T, DIM, VAR>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    *csize = 1;
+    for (int c = 16; c >= 2; c /= 2) {
+        if (c > want) continue;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(threads);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+        if (e != cudaSuccess) { cudaGetLastError(); continue; }
+        if (n >= 1) { *csize = c; return cudaSuccess; }
+    }
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t Ops<T>::cluster_prepare(int dim, bool var, int threads, int want, int* csize) {
+    if (dim == 2 && !var) return cluster_prepare_t<T, 2, false>(threads, want, csize);
+    if (dim == 2 && var) return cluster_prepare_t<T, 2, true>(threads, want, csize);
+    if (dim == 3 && !var) return cluster_prepare_t<T, 3, false>(threads, want, csize);
+    return cluster_prepare_t<T, 3, true>(threads, want, csize);
 }
 
 template <class T>

@@ -11,6 +11,7 @@
 
 #include "../../include/bura.h"
 #include "kernels.cuh"
+#include "tma.cuh"
 
 using namespace bura;
 
@@ -28,7 +29,7 @@ struct HostLevel {
 
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
-           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_NK };
+           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -46,7 +47,10 @@ const char* const kNames[K_NK][2][2] = {
     {{"cast_scaled", "cast_scaled"}, {"cast_scaled", "cast_scaled"}},
     {{"correct64", "correct64"}, {"correct64", "correct64"}},
     {{"weighted_sum", "weighted_sum"}, {"weighted_sum", "weighted_sum"}},
-    {{"gather_systems", "gather_systems"}, {"gather_systems", "gather_systems"}}};
+    {{"gather_systems", "gather_systems"}, {"gather_systems", "gather_systems"}},
+    {{"coarse_cluster_f64", "coarse_cluster_f64@coarse"}, {"coarse_cluster_f32", "coarse_cluster_f32@coarse"}},
+    {{"pre2_restrict_f64", "pre2_restrict_f64@coarse"}, {"pre2_restrict_f32", "pre2_restrict_f32@coarse"}},
+    {{"prolong_cheb_f64", "prolong_cheb_f64@coarse"}, {"prolong_cheb_f32", "prolong_cheb_f32@coarse"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -70,13 +74,29 @@ struct Work {
     std::vector<T*> b, xa, xb, dd;
     std::vector<double*> c1, c2;  // [level] -> deg rows of Kp coefficients
     std::vector<int> deg;
-    int lc = -1;                  // first level run by the single-CTA coarse kernel (-1: none)
-    int le = -1;                  // level solved exactly with dense inverses inside that CTA (-1: none)
+    int lc = -1;                  // first level run by the coarse kernel (-1: none, grid kernels to the end)
+    int coarse_kind = 0;          // BURA_COARSE_CLUSTER or BURA_COARSE_CTA
+    int csize = 0;                // CTAs of the cluster (cluster kind)
+    int le = -1;                  // level solved exactly with dense inverses inside that kernel (-1: none)
     T* minv = nullptr;            // the inverses, [row][col][Kp]
-    size_t coarse_smem = 0;       // its shared-memory bytes
-    Launch gc{};                  // launch shape of that kernel
+    size_t coarse_smem = 0;       // shared-memory bytes of the single-CTA kind
+    Launch gc{};                  // launch shape of the coarse kernel (one CTA)
     double* dsh = nullptr;
     Scal* scal = nullptr;
+    // TMA-staged sweeps (FP32, 2-D, constant coefficients) of the levels with at least one tile per SM:
+    // tensor maps of the level's vectors, with a halo box (stencil inputs) and a plain box
+    struct TmaLev {
+        bool on = false;
+        TmaGeo geo{};
+        struct Ent { int box; const void* buf; CUtensorMap map; };
+        std::vector<Ent> maps;
+        const CUtensorMap* find(int box, const void* buf) const {
+            for (const auto& e : maps)
+                if (e.box == box && e.buf == buf) return &e.map;
+            return nullptr;
+        }
+    };
+    std::vector<TmaLev> tma;
     bool ready = false;
     // the PCG loop captured once as a graph with a device-side conditional WHILE node
     cudaGraph_t graph = nullptr;
@@ -92,6 +112,7 @@ int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
 
 struct bura_plan {
     int dev = 0, nsm = 152;
+    bool cluster_ok = false;  // the device launches thread-block clusters
     int dim = 2;
     bool var = false;
     int k = 0, K = 0;
@@ -398,6 +419,49 @@ int coarse_degree_auto(const HostLevel& h, double d0) {
     return std::max(2, std::min(m, 400));
 }
 
+// Tensor maps for the TMA-staged sweeps: FP32, 2-D, constant coefficients, levels that the grid
+// kernels would run (not the coarse kernel's) with at least one tile per SM.
+template <class T>
+int build_tma(bura_plan* p, Work<T>& w) {
+    const int nlev = (int)p->hl.size();
+    w.tma.assign(nlev, typename Work<T>::TmaLev());
+    if (sizeof(T) != 4 || p->dim != 2 || p->var || p->opt.sweeps == BURA_SWEEP_GRID || !tma_supported(w.Kp))
+        return BURA_OK;
+    bool any = false;
+    for (int l = 0; l < nlev; ++l) {
+        if (w.lc >= 0 && l >= w.lc) break;
+        const bool has_coarse = l + 1 < nlev;
+        const TmaGeo g = tma_geo(w.L[l], has_coarse ? &w.L[l + 1] : nullptr, w.Kp);
+        if (g.ntiles < p->nsm) break;
+        auto& t = w.tma[l];
+        t.geo = g;
+        const void* bl = l == 0 ? (const void*)w.r : (const void*)w.b[l];
+        struct Want { int box; const void* buf; int lev; };
+        std::vector<Want> want = {{TB_HALO, bl, l}, {TB_HALO, w.xa[l], l}, {TB_HALO, w.xb[l], l},
+                                  {TB_PLAIN, bl, l}, {TB_PLAIN, w.dd[l], l}};
+        if (l == 0) {
+            want.push_back({TB_HALO, w.pa, 0});
+            want.push_back({TB_HALO, w.pb, 0});
+        }
+        if (has_coarse) {  // the fused transfers: b with a two-point halo, coarse results for prolongation
+            want.push_back({TB_RSRC, bl, l});
+            want.push_back({TB_CPRO, w.xa[l + 1], l + 1});
+            want.push_back({TB_CPRO, w.xb[l + 1], l + 1});
+        }
+        for (const Want& e : want) {
+            typename Work<T>::TmaLev::Ent ent;
+            ent.box = e.box;
+            ent.buf = e.buf;
+            CK(tma_encode(&ent.map, reinterpret_cast<const float*>(e.buf), w.Kp, w.L[e.lev].nx, w.L[e.lev].ny, e.box));
+            t.maps.push_back(ent);
+        }
+        t.on = true;
+        any = true;
+    }
+    if (any) CK(tma_prepare(w.Kp));
+    return BURA_OK;
+}
+
 template <class T>
 int build_work(bura_plan* p, Work<T>& w) {
     const int nlev = (int)p->hl.size();
@@ -469,19 +533,32 @@ int build_work(bura_plan* p, Work<T>& w) {
     for (int l = 0; l < nlev; ++l)
         if (p->hl[l].N <= kExactPoints) { w.le = l; break; }
     const int last = w.le >= 0 ? w.le : nlev - 1;
-    // the smallest levels run together in one CTA with all their vectors in shared memory
     w.lc = -1;
     w.coarse_smem = 0;
-    for (int l = 0; l <= last; ++l) {
-        size_t bytes = 0;
-        for (int m = l; m <= last; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.Kp * sizeof(T) + 15) / 16 * 16);
-        if (bytes <= kCoarseSmem && last - l + 1 <= kMaxCoarseLevels) {
-            w.lc = l;
-            w.coarse_smem = bytes;
-            break;
+    w.coarse_kind = p->opt.coarse_kernel;
+    if (w.coarse_kind == BURA_COARSE_AUTO) w.coarse_kind = p->cluster_ok ? BURA_COARSE_CLUSTER : BURA_COARSE_CTA;
+    if (w.coarse_kind == BURA_COARSE_CLUSTER) {
+        // the small levels (at most kClusterPoints points each, L2 resident) run in one thread-block cluster
+        for (int l = 0; l <= last; ++l)
+            if (p->hl[l].N <= kClusterPoints && last - l + 1 <= kMaxCoarseLevels) { w.lc = l; break; }
+        if (w.lc >= 0) {
+            const int want = p->opt.cluster_size > 0 ? p->opt.cluster_size : 16;
+            CK(Ops<T>::cluster_prepare(p->dim, p->var, kClusterThreads, want, &w.csize));
+            if (w.csize < 2) w.lc = -1;
+        }
+    } else if (w.coarse_kind == BURA_COARSE_CTA) {
+        // the smallest levels run together in one CTA with all their vectors in shared memory
+        for (int l = 0; l <= last; ++l) {
+            size_t bytes = 0;
+            for (int m = l; m <= last; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.Kp * sizeof(T) + 15) / 16 * 16);
+            if (bytes <= kCoarseSmem && last - l + 1 <= kMaxCoarseLevels) {
+                w.lc = l;
+                w.coarse_smem = bytes;
+                break;
+            }
         }
     }
-    if (w.lc < 0) w.le = -1;  // the dense solve lives in the coarse CTA only
+    if (w.lc < 0) w.le = -1;  // the dense solve lives in the coarse kernel only
     if (w.le >= 0) {
         std::vector<double> inv;
         dense_inverses(p->hl[w.le], p->dim, p->var, p->d, p->K, w.Kp, inv);
@@ -491,9 +568,10 @@ int build_work(bura_plan* p, Work<T>& w) {
     }
     w.gc.Kp = w.Kp;
     w.gc.C = w.C;
-    w.gc.PPB = kCoarseThreads / w.C;
+    w.gc.PPB = (w.coarse_kind == BURA_COARSE_CLUSTER ? kClusterThreads : kCoarseThreads) / w.C;
     w.gc.blocks = 1;
-    if (w.lc >= 0) CK(Ops<T>::prepare_coarse(p->dim, p->var, w.coarse_smem + kCoarseTables + KMAXP * sizeof(double)));
+    if (w.lc >= 0 && w.coarse_kind == BURA_COARSE_CTA)
+        CK(Ops<T>::prepare_coarse(p->dim, p->var, w.coarse_smem + kCoarseTables + KMAXP * sizeof(double)));
     const size_t vb0 = (size_t)p->hl[0].N * w.Kp * sizeof(T);
     CA(dalloc(p, &w.x, vb0));
     CA(dalloc(p, &w.r, vb0));
@@ -506,6 +584,7 @@ int build_work(bura_plan* p, Work<T>& w) {
     CK(cudaMemcpy(w.dsh, dsh.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice));
     CA(dalloc(p, &w.scal, sizeof(Scal)));
     CK(cudaMemset(w.scal, 0, sizeof(Scal)));
+    CA(build_tma(p, w));
     w.ready = true;
     return BURA_OK;
 }
@@ -577,6 +656,43 @@ T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
     return w.xa[w.lc];
 }
 
+// Launch the clustered V-cycle over levels w.lc..(w.le or nlev-1) for the right-hand side b; every
+// level keeps its vectors in its own global buffers (L2 resident).  Returns the buffer holding the
+// result of level lc (predicted exactly as the kernel leaves it: a level's pre-smoothing ends in xa
+// when deg-1 is even, its post-smoothing toggles deg more times, the coarsest level has no
+// post-smoothing and the dense solve writes xa).
+template <class T>
+T* cluster_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
+    const int nlev = (int)p->hl.size();
+    ClusterArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nlev = (w.le >= 0 ? w.le : nlev - 1) - w.lc + 1;
+    a.exact = w.le >= 0 ? w.le - w.lc : -1;
+    a.minv = w.minv;
+    a.Kp = w.Kp;
+    a.dsh = w.dsh;
+    for (int i = 0; i < a.nlev; ++i) {
+        const int l = w.lc + i;
+        ClusterLevel& c = a.lev[i];
+        c.L = w.L[l];
+        c.b = i == 0 ? const_cast<T*>(b) : w.b[l];
+        c.xa = w.xa[l];
+        c.xb = w.xb[l];
+        c.dd = w.dd[l];
+        const int deg = w.deg[l];
+        T* pre = ((deg - 1) % 2 == 0) ? w.xa[l] : w.xb[l];
+        T* other = pre == w.xa[l] ? w.xb[l] : w.xa[l];
+        if (i == a.exact) c.result = w.xa[l];
+        else c.result = (l == nlev - 1 || deg % 2 == 0) ? pre : other;
+        c.c1 = w.c1[l];
+        c.c2 = w.c2[l];
+        c.deg = deg;
+    }
+    traced(p, K_CLUSTER, sizeof(T) == 4, w.lc == 0, 0.0, s,
+           [&] { (void)Ops<T>::coarse_cluster(w.gc, w.csize, p->dim, p->var, a, s); });  // errors: cudaGetLastError
+    return reinterpret_cast<T*>(const_cast<void*>(a.lev[0].result));
+}
+
 // Symmetric V-cycle on level l for rhs b; returns the buffer holding the result.  With rz_fused
 // (level 0 only) the last smoothing step also forms r^T z and the CG beta of every system.
 template <class T>
@@ -590,8 +706,8 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     const bool fine = (l == 0);
     Red none{p->partial, p->tickets, w.scal, nullptr, RED_NONE, 0};
     Red beta{p->partial, p->tickets, w.scal, nullptr, RED_BETA, 0};
-    if (l == w.lc) {  // the rest of the hierarchy in one CTA
-        T* res = coarse_part(p, w, b, s);
+    if (l == w.lc) {  // the rest of the hierarchy in one kernel
+        T* res = w.coarse_kind == BURA_COARSE_CLUSTER ? cluster_part(p, w, b, s) : coarse_part(p, w, b, s);
         if (rz_fused)
             traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, res, beta, s); });
         return res;
@@ -601,19 +717,69 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     T* D = w.dd[l];
     T* cur = A;
     T* oth = B;
+    const auto& tl = w.tma[l];
+    // one Chebyshev step, TMA-staged where the level has tensor maps
+    auto cheb = [&](const T* xin, const T* din, T* xout, T* dout, ChebStep cs, const Red& red) {
+        const CUtensorMap* mx = tl.on ? tl.find(TB_HALO, xin) : nullptr;
+        const CUtensorMap* md = tl.on && din ? tl.find(TB_PLAIN, din) : nullptr;
+        const CUtensorMap* mb = tl.on ? tl.find(TB_PLAIN, b) : nullptr;
+        if (mx && mb && (md || !din))
+            (void)tma_cheb_step(tl.geo, p->nsm, *mx, md, *mb, reinterpret_cast<float*>(xout),
+                                reinterpret_cast<float*>(dout), cs, w.dsh, red, s);
+        else
+            Ops<T>::cheb_step(g, L, dim, var, xin, din, b, xout, dout, cs, w.dsh, red, s);
+    };
+    // TMA-staged level with degree-2 smoothing: pre-smoothing fused with the restriction of its
+    // residual, the coarse levels, the first post-smoothing step fused with the prolongation, the last
+    // post-smoothing step (with r.z and beta at the finest level)
+    const CUtensorMap* m_rsrc = tl.on && deg == 2 ? tl.find(TB_RSRC, b) : nullptr;
+    const CUtensorMap* m_ca = tl.on ? tl.find(TB_CPRO, w.xa[l + 1 < (int)p->hl.size() ? l + 1 : l]) : nullptr;
+    const CUtensorMap* m_cb = tl.on ? tl.find(TB_CPRO, w.xb[l + 1 < (int)p->hl.size() ? l + 1 : l]) : nullptr;
+    const CUtensorMap* m_xa = tl.on ? tl.find(TB_HALO, A) : nullptr;
+    const CUtensorMap* m_bp = tl.on ? tl.find(TB_PLAIN, b) : nullptr;
+    if (m_rsrc && m_ca && m_cb && m_xa && m_bp) {
+        traced(p, K_PRE2R, f32, fine, vbytes<T>(p, l, 2.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
+            (void)tma_pre2_restrict(tl.geo, p->nsm, *m_rsrc, reinterpret_cast<float*>(A),
+                                    reinterpret_cast<float*>(w.b[l + 1]), step_of(w, l, 0), step_of(w, l, 1), w.dsh,
+                                    none, s);
+        });
+        T* ec = vcycle<T>(p, w, l + 1, w.b[l + 1], false, s);
+        const CUtensorMap* mec = ec == w.xa[l + 1] ? m_ca : ec == w.xb[l + 1] ? m_cb : nullptr;
+        if (mec) {
+            traced(p, K_PROCHEB, f32, fine, vbytes<T>(p, l, 4.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
+                (void)tma_prolong_cheb(tl.geo, p->nsm, *m_xa, *mec, *m_bp, reinterpret_cast<float*>(B),
+                                       reinterpret_cast<float*>(D), step_of(w, l, 0, false), w.dsh, none, s);
+            });
+        } else {  // a coarse result outside the level's two buffers: unfused correction and first step
+            traced(p, K_PROLONG, f32, fine, vbytes<T>(p, l, 2.0, false) + vbytes<T>(p, l + 1, 1.0, false), s,
+                   [&] { Ops<T>::prolong_add(g, L, w.L[l + 1], dim, ec, A, s); });
+            traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0, true), s,
+                   [&] { cheb(A, nullptr, B, D, step_of(w, l, 0, false), none); });
+        }
+        const Red& red = rz_fused ? beta : none;
+        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0, true), s,
+               [&] { cheb(B, D, A, nullptr, step_of(w, l, 1), red); });
+        return A;
+    }
     // pre-smoothing from a zero initial guess; the first two Chebyshev steps share one sweep
     if (deg == 1) {
         traced(p, K_CHEB0, f32, fine, vbytes<T>(p, l, 2.0, var), s,
                [&] { Ops<T>::cheb_zero(g, L, dim, var, b, A, step_of(w, l, 0), w.dsh, s); });
     } else {
         traced(p, K_PRE2, f32, fine, vbytes<T>(p, l, deg > 2 ? 3.0 : 2.0, true), s, [&] {
-            Ops<T>::cheb_pre2(g, L, dim, var, b, A, deg > 2 ? D : nullptr, step_of(w, l, 0), step_of(w, l, 1), w.dsh, s);
+            const CUtensorMap* mb = tl.on ? tl.find(TB_HALO, b) : nullptr;
+            if (mb)
+                (void)tma_pre2(tl.geo, p->nsm, *mb, reinterpret_cast<float*>(A),
+                               reinterpret_cast<float*>(deg > 2 ? D : nullptr), step_of(w, l, 0), step_of(w, l, 1),
+                               w.dsh, none, s);
+            else
+                Ops<T>::cheb_pre2(g, L, dim, var, b, A, deg > 2 ? D : nullptr, step_of(w, l, 0), step_of(w, l, 1),
+                                  w.dsh, s);
         });
         for (int m = 2; m < deg; ++m) {
             T* dout = m < deg - 1 ? D : nullptr;
-            traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0 + (dout ? 1.0 : 0.0), true), s, [&] {
-                Ops<T>::cheb_step(g, L, dim, var, cur, D, b, oth, dout, step_of(w, l, m), w.dsh, none, s);
-            });
+            traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0 + (dout ? 1.0 : 0.0), true), s,
+                   [&] { cheb(cur, D, oth, dout, step_of(w, l, m), none); });
             std::swap(cur, oth);
         }
     }
@@ -635,9 +801,8 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
         T* din = m == 0 ? nullptr : D;
         T* dout = last ? nullptr : D;
         const Red& red = (rz_fused && last) ? beta : none;
-        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 3.0 + (din ? 1.0 : 0.0) + (dout ? 1.0 : 0.0), true), s, [&] {
-            Ops<T>::cheb_step(g, L, dim, var, cur, din, b, oth, dout, step_of(w, l, m, m != 0), w.dsh, red, s);
-        });
+        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 3.0 + (din ? 1.0 : 0.0) + (dout ? 1.0 : 0.0), true), s,
+               [&] { cheb(cur, din, oth, dout, step_of(w, l, m, m != 0), red); });
         std::swap(cur, oth);
     }
     return cur;
@@ -653,8 +818,17 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
     Red ralpha{p->partial, p->tickets, w.scal, nullptr, RED_ALPHA, 0};
     Red rconv{p->partial, p->tickets, w.scal, nullptr, RED_CONV, cond};
     T* z = vcycle<T>(p, w, 0, w.r, true, s);
-    traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s,
-           [&] { Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s); });
+    const auto& tl = w.tma[0];
+    traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s, [&] {
+        const CUtensorMap* mz = tl.on ? tl.find(TB_HALO, z) : nullptr;
+        const CUtensorMap* ma = tl.on ? tl.find(TB_HALO, w.pa) : nullptr;
+        const CUtensorMap* mbb = tl.on ? tl.find(TB_HALO, w.pb) : nullptr;
+        if (mz && ma && mbb)
+            (void)tma_spmv_p(tl.geo, p->nsm, *mz, *ma, *mbb, reinterpret_cast<float*>(w.pa),
+                             reinterpret_cast<float*>(w.pb), reinterpret_cast<float*>(w.q), ralpha, s);
+        else
+            Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s);
+    });
     traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s,
            [&] { Ops<T>::cg_update(g, L.N, w.x, w.r, w.pa, w.pb, w.q, rconv, s); });
     CKL();
@@ -705,7 +879,7 @@ int pcg(bura_plan* p, Work<T>& w, int* iters_out, cudaStream_t s) {
             CK(cudaStreamSynchronize(s));
             collect_trace(p);
             const Scal& h = *p->hscal;
-            if (h.breakdown || h.nactive == 0 || h.it >= h.max_it) break;
+            if (h.breakdown || h.fault || h.nactive == 0 || h.it >= h.max_it) break;
         }
     } else {
         CA(build_graph<T>(p, w));
@@ -716,6 +890,7 @@ int pcg(bura_plan* p, Work<T>& w, int* iters_out, cudaStream_t s) {
     }
     const Scal& h = *p->hscal;
     *iters_out = h.it;
+    if (h.fault) return BURA_ETIMEOUT;
     if (h.breakdown) return BURA_ENOTSPD;
     return h.nactive == 0 ? BURA_OK : BURA_ENOCONV;
 }
@@ -933,7 +1108,11 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if (o.precision != BURA_PREC_FP64 && o.precision != BURA_PREC_MIXED) return BURA_EINVAL;
     if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio > 1) || o.max_iters < 1 ||
         o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000 ||
-        o.block_points < 0 || o.block_points > 1024 || o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
+        o.block_points < 0 || o.block_points > 1024 || o.blocks_per_sm < 0 || o.blocks_per_sm > 64 ||
+        o.coarse_kernel < BURA_COARSE_AUTO || o.coarse_kernel > BURA_COARSE_NONE ||
+        !(o.cluster_size == 0 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8 ||
+          o.cluster_size == 16) ||
+        o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID)
         return BURA_EINVAL;
 
     bura_plan* p = new (std::nothrow) bura_plan();
@@ -996,6 +1175,9 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess || nsm <= 0)
         return fail(BURA_ECUDA);
     p->nsm = nsm;
+    int cl = 0;
+    p->cluster_ok = cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, p->dev) == cudaSuccess && cl != 0;
+    if (o.coarse_kernel == BURA_COARSE_CLUSTER && !p->cluster_ok) return fail(BURA_EINVAL);
 
     rc = build_work<double>(p, p->w64);
     if (rc != BURA_OK) return fail(rc);

@@ -138,14 +138,54 @@ def test_fp64_each_system_matches(lib):
         lib.bura_destroy(plan)
 
 
+@pytest.mark.parametrize("kind,csize", [("CLUSTER", 0), ("CLUSTER", 2), ("CLUSTER", 8), ("CTA", 0), ("NONE", 0)])
+@pytest.mark.parametrize("shape,var", [((255, 255), False), ((31, 31, 31), True), ((127, 63), False)])
+def test_fp64_solve_each_coarse_kernel(lib, kind, csize, shape, var):
+    """The three ways of running the small levels (one thread-block cluster over L2-resident vectors,
+    one CTA over shared memory, grid kernels down to the coarsest level) all converge to the BURA
+    value; the profile names the coarse kernel that ran."""
+    nps = _np_shape(shape)
+    alpha, k = 0.5, 7
+    faces = W.block_lognormal_faces(nps, 4, 1e-2, 1.0, 5) if var else None
+    f = W.rhs_normal(nps, 6)
+    o = _opts(lib, lib.BURA_PREC_FP64, coarse_kernel=getattr(lib, "BURA_COARSE_" + kind), cluster_size=csize)
+    plan = lib.bura_setup(shape, alpha, k, faces=faces, options=o)
+    try:
+        lib.bura_set_profiling(plan, True)
+        fd = torch.from_numpy(f).cuda()
+        ud = torch.zeros_like(fd)
+        assert lib.bura_solve(plan, fd, ud, 1e-11) == lib.BURA_OK
+        torch.cuda.synchronize()
+        names = {e["name"] for e in lib.bura_get_profile(plan)}
+        u = ud.cpu().numpy()
+    finally:
+        lib.bura_destroy(plan)
+    ref = tables.entry(alpha, k)
+    if var:
+        A, _ = operators.scaled_matrix(nps, faces)
+        ur = direct.bura_sparse(A, f, ref["c"], ref["d"])
+    else:
+        ur = exact.bura_value(nps, f, ref["c"], ref["d"])
+    assert _rel(u, ur) <= 1e-10
+    has_cluster = any(n.startswith("coarse_cluster") for n in names)
+    has_cta = any(n.startswith("coarse_cycle") for n in names)
+    assert (has_cluster, has_cta) == (kind == "CLUSTER", kind == "CTA"), names
+
+
 # ------------------------------------------------------------------ mixed path
+@pytest.mark.parametrize("sweeps", ["AUTO", "GRID"])
 @pytest.mark.parametrize("shape,alpha,k,tol", [((64, 64), 0.5, 5, 1e-6), ((127, 127), 0.25, 7, 1e-6),
                                                ((255, 255), 0.75, 7, 1e-6), ((127, 127), 0.5, 7, 1e-8),
-                                               ((31, 31, 31), 0.5, 9, 1e-6)])
-def test_mixed_solve_within_tolerance(lib, shape, alpha, k, tol):
+                                               ((31, 31, 31), 0.5, 9, 1e-6), ((1023, 255), 0.5, 3, 1e-7),
+                                               ((257, 1023), 0.25, 10, 1e-6), ((1023, 511), 0.5, 12, 1e-6)])
+def test_mixed_solve_within_tolerance(lib, shape, alpha, k, tol, sweeps):
+    """Mixed path with the TMA-staged tile sweeps (AUTO: FP32 2-D constant-coefficient levels with at
+    least one 32x16 tile per SM; ragged last tiles on every shape here) and with grid-stride sweeps
+    only.  k = 3, 7, 10, 12 give 4, 8, 12 and 16 FP32 values per point (1 to 4 chunks of 16 bytes)."""
     nps = _np_shape(shape)
     f = W.rhs_uniform(nps, 1)
-    u, st, rc, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED)
+    u, st, rc, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED,
+                          sweeps=getattr(lib, "BURA_SWEEP_" + sweeps))
     assert rc == lib.BURA_OK
     ref = tables.entry(alpha, k)
     err = _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"]))

@@ -54,6 +54,17 @@ def test_setup_rejects_bad_arguments_on_the_host(lib, shape, alpha, k):
     assert ei.value.code == lib.BURA_EINVAL
 
 
+@pytest.mark.parametrize("field,value", [("coarse_kernel", -1), ("coarse_kernel", 4), ("cluster_size", 3),
+                                         ("cluster_size", 32), ("smoother_degree", 0), ("inner_rtol", 1.0)])
+def test_setup_rejects_bad_options_on_the_host(lib, field, value):
+    o = lib.bura_default_options()
+    assert o.coarse_kernel == lib.BURA_COARSE_AUTO and o.cluster_size == 0
+    setattr(o, field, value)
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup((31, 31), 0.5, 5, options=o)
+    assert ei.value.code == lib.BURA_EINVAL
+
+
 def test_setup_rejects_nonpositive_coefficients(lib):
     from paper_1612_04846_gb300 import workloads as W
     faces = list(W.constant_faces((4, 5)))
