@@ -64,7 +64,7 @@ typedef struct {
 
 /* How the small levels of the multigrid V-cycle are run. */
 typedef enum {
-    BURA_COARSE_AUTO = 0,    /* CLUSTER where the device launches thread-block clusters, else CTA */
+    BURA_COARSE_AUTO = 0,    /* currently CTA (the faster of the two on GB300) */
     BURA_COARSE_CLUSTER = 1, /* levels with <= 16384 points in one thread-block cluster (vectors in L2);
                                 bura_setup returns BURA_EINVAL on a device without cluster launch */
     BURA_COARSE_CTA = 2,     /* the levels that fit 200 KB of shared memory in a single CTA */

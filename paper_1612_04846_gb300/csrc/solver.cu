@@ -536,7 +536,9 @@ int build_work(bura_plan* p, Work<T>& w) {
     w.lc = -1;
     w.coarse_smem = 0;
     w.coarse_kind = p->opt.coarse_kernel;
-    if (w.coarse_kind == BURA_COARSE_AUTO) w.coarse_kind = p->cluster_ok ? BURA_COARSE_CLUSTER : BURA_COARSE_CTA;
+    // measured on GB300 (2-D 1023^2, k = 7): the single CTA over shared memory beats the cluster, whose
+    // sweeps each pay an L2 round trip and a cluster barrier (about 3 us of fixed cost per sweep)
+    if (w.coarse_kind == BURA_COARSE_AUTO) w.coarse_kind = BURA_COARSE_CTA;
     if (w.coarse_kind == BURA_COARSE_CLUSTER) {
         // the small levels (at most kClusterPoints points each, L2 resident) run in one thread-block cluster
         for (int l = 0; l <= last; ++l)
