@@ -169,13 +169,13 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             int x0, y0;
             tile_origin(g, t, x0, y0);
             mbar_expect_tx(bar, tx_bytes);
-            tma_load_3d(st, &mp.m[0], 0, x0 - 1, y0 - 1, bar);
+            tma_load_pt(st, &mp.m[0], g, x0 - 1, y0 - 1, bar);
             unsigned char* q = st + halo_bytes(Kp);
             if (HAS_DIN) {
-                tma_load_3d(q, &mp.m[1], 0, x0, y0, bar);
+                tma_load_pt(q, &mp.m[1], g, x0, y0, bar);
                 q += plain_bytes(Kp);
             }
-            tma_load_3d(q, &mp.m[2], 0, x0, y0, bar);
+            tma_load_pt(q, &mp.m[2], g, x0, y0, bar);
         },
         [&](unsigned char* st, int t) {
             int x0, y0;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             int x0, y0;
             tile_origin(g, t, x0, y0);
             mbar_expect_tx(bar, tx_bytes);
-            tma_load_3d(st, &mp.m[0], 0, x0 - 1, y0 - 1, bar);
+            tma_load_pt(st, &mp.m[0], g, x0 - 1, y0 - 1, bar);
         },
         [&](unsigned char* st, int t) {
             int x0, y0;
@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             int x0, y0;
             tile_origin(g, t, x0, y0);
             mbar_expect_tx(bar, tx_bytes);
-            tma_load_3d(st, &mp.m[0], 0, x0 - 1, y0 - 1, bar);
-            tma_load_3d(st + halo_bytes(Kp), mold, 0, x0 - 1, y0 - 1, bar);
+            tma_load_pt(st, &mp.m[0], g, x0 - 1, y0 - 1, bar);
+            tma_load_pt(st + halo_bytes(Kp), mold, g, x0 - 1, y0 - 1, bar);
         },
         [&](unsigned char* st, int t) {
             int x0, y0;
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
         [&](unsigned char* st, int t, uint64_t* bar) {
             const int cy = t / g.ncx, cx = t - cy * g.ncx;
             mbar_expect_tx(bar, tx_bytes);
-            tma_load_3d(st, &mp.m[0], 0, 2 * cx * kTXc - 2, 2 * cy * kTYc - 2, bar);
+            tma_load_pt(st, &mp.m[0], g, 2 * cx * kTXc - 2, 2 * cy * kTYc - 2, bar);
         },
         [&](unsigned char* st, int t) {
             const int cy = t / g.ncx, cx = t - cy * g.ncx;
@@ -476,9 +476,9 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
             int x0, y0;
             tile_origin(g, t, x0, y0);
             mbar_expect_tx(bar, tx_bytes);
-            tma_load_3d(st, &mp.m[0], 0, x0 - 1, y0 - 1, bar);
-            tma_load_3d(st + halo_bytes(Kp), &mp.m[1], 0, x0 / 2 - 1, y0 / 2 - 1, bar);
-            tma_load_3d(st + halo_bytes(Kp) + vec_bytes(kCpX * kCpY, Kp), &mp.m[2], 0, x0, y0, bar);
+            tma_load_pt(st, &mp.m[0], g, x0 - 1, y0 - 1, bar);
+            tma_load_pt(st + halo_bytes(Kp), &mp.m[1], g, x0 / 2 - 1, y0 / 2 - 1, bar);
+            tma_load_pt(st + halo_bytes(Kp) + vec_bytes(kCpX * kCpY, Kp), &mp.m[2], g, x0, y0, bar);
         },
         [&](unsigned char* st, int t) {
             int x0, y0;
@@ -580,6 +580,9 @@ cudaError_t launch_tile(K kernel, int blocks, int C, size_t smem, cudaStream_t s
 
 bool tma_supported(int Kp) { return Kp == 4 || Kp == 8 || Kp == 12 || Kp == 16; }
 
+// The widest box row is the fused restriction's, (2 kTXc + 5) points of Kp / 2 eight-byte elements.
+bool tma_flat(int Kp) { return (2 * kTXc + 5) * (Kp / 2) <= 256; }
+
 TmaGeo tma_geo(const Lev& L, const Lev* Lc, int Kp) {
     TmaGeo g;
     g.nxc = Lc ? Lc->nx : 0;
@@ -595,6 +598,7 @@ TmaGeo tma_geo(const Lev& L, const Lev* Lc, int Kp) {
     g.Kp = Kp;
     g.wx = (float)L.wx;
     g.wy = (float)L.wy;
+    g.flat = tma_flat(Kp) ? 1 : 0;
     return g;
 }
 
@@ -608,15 +612,27 @@ cudaError_t tma_encode(CUtensorMap* m, const float* base, int Kp, int nx, int ny
         if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)nx, (cuuint64_t)ny};
-    const cuuint64_t strides[2] = {(cuuint64_t)Kp * sizeof(float), (cuuint64_t)nx * Kp * sizeof(float)};
     int bx = 0, by = 0;
     tma_box_dims(boxkind, &bx, &by);
-    const cuuint32_t box[3] = {(cuuint32_t)Kp, (cuuint32_t)bx, (cuuint32_t)by};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r;
+    if (tma_flat(Kp)) {
+        // rows of nx * Kp / 2 eight-byte elements: a box row is (bx points) contiguous bytes; zero fill
+        // outside the row is the Dirichlet boundary exactly as in the 3-D form (all-zero bits = 0.0f)
+        const cuuint64_t dims[2] = {(cuuint64_t)nx * (Kp / 2), (cuuint64_t)ny};
+        const cuuint64_t strides[1] = {(cuuint64_t)nx * Kp * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)(bx * (Kp / 2)), (cuuint32_t)by};
+        r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)nx, (cuuint64_t)ny};
+        const cuuint64_t strides[2] = {(cuuint64_t)Kp * sizeof(float), (cuuint64_t)nx * Kp * sizeof(float)};
+        const cuuint32_t box[3] = {(cuuint32_t)Kp, (cuuint32_t)bx, (cuuint32_t)by};
+        r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

@@ -82,6 +82,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     return true;
 }
 
+// 2-D tiled TMA load of the box at coordinates (c0, c1) (innermost first) into shared memory;
+// completion is signalled on `bar` (transaction bytes).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 3-D tiled TMA load of the box at coordinates (c0, c1, c2) (innermost first) into shared memory;
 // completion is signalled on `bar` (transaction bytes).  c0 is always 0 here (16-byte aligned).
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
@@ -104,7 +114,19 @@ struct TmaGeo {
     int nxc, nyc;      // the next coarser level (0 if none)
     int ncx, ncy;      // coarse tiles (kTXc x kTYc) of the fused smoothing + restriction
     int nctiles;
+    int flat;          // 1: 2-D maps over 8-byte elements (a tile row is one contiguous box row),
+                       // 0: 3-D maps (Kp floats innermost), used when a box row would exceed 256 elements
 };
+
+#ifdef __CUDACC__
+// Load the box whose first grid point is (x, y) (may be negative: zero fill); the shared-memory layout
+// is [rows][points][Kp floats] for both map kinds.
+__device__ __forceinline__ void tma_load_pt(void* dst, const CUtensorMap* map, const TmaGeo& g, int x, int y,
+                                            uint64_t* bar) {
+    if (g.flat) tma_load_2d(dst, map, x * (g.Kp / 2), y, bar);
+    else tma_load_3d(dst, map, 0, x, y, bar);
+}
+#endif
 
 struct TmaMaps3 {
     CUtensorMap m[3];
@@ -113,6 +135,8 @@ struct TmaMaps3 {
 // Host side.  Every launcher returns the launch status; the kernels take the fault flag from red.scal.
 bool tma_supported(int Kp);
 TmaGeo tma_geo(const Lev& L, const Lev* Lc, int Kp);
+// Whether the maps of a level with Kp floats per point are flat (2-D over 8-byte elements).
+bool tma_flat(int Kp);
 // Tensor map of an [ny][nx][Kp] float vector with a box of kind TmaBox.
 cudaError_t tma_encode(CUtensorMap* m, const float* base, int Kp, int nx, int ny, int box);
 cudaError_t tma_prepare(int Kp);
