@@ -716,39 +716,55 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_dot(int N, i
 }
 
 // ------------------------------------------------------------------ single-CTA coarse V-cycle
-// Runs levels l0..nlev-1 of the V-cycle (all with few points) in one CTA with every vector in shared
-// memory: the same sweeps as the grid kernels with (first tile, stride) = (0, 1) and __syncthreads()
-// between dependent sweeps.  b of level l0 is read from and its result written to global memory.
+// Runs levels l0..nlev-1 of the V-cycle (all with few points) with every vector in shared memory: the
+// same sweeps as the grid kernels with (first tile, stride) = (0, 1) and __syncthreads() between
+// dependent sweeps.  The V-cycle of one shifted system never touches another system's values, so CTA
+// `blockIdx.x` runs the systems of one 16-byte chunk (W of them) on its own SM: the chunk's values are
+// stored compactly (stride W) in shared memory and the global arrays are addressed at chunk offset
+// blockIdx.x * W with their own stride Kp.  b of level l0 is read from and its result written to global.
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
     pdl_wait();
+    constexpr int W = VecT<T>::W;
     extern __shared__ __align__(16) unsigned char csm[];
     auto at = [&](unsigned int off) { return reinterpret_cast<T*>(csm + off); };
     const int nthr = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.x * W;  // first system of this CTA's chunk
+    const int Kp = a.Kp;            // stride of the global arrays
+    constexpr int Ks = W;           // stride of the shared-memory vectors
     {
-        const int n = (int)(a.lev[0].L.N * a.Kp);
-        const T* src = reinterpret_cast<const T*>(a.b_in);
+        const int n = (int)a.lev[0].L.N;
+        const T* src = reinterpret_cast<const T*>(a.b_in) + ch;
         T* dst = at(a.lev[0].b);
-        for (int i = tid; i < n; i += nthr) dst[i] = src[i];
+        for (int i = tid; i < n; i += nthr) {
+            T v[W];
+            vld(src + (size_t)i * Kp, v);
+            vst(dst + (size_t)i * Ks, v);
+        }
         // the shifts and the small Chebyshev tables are read by every sweep: keep them on chip
         double* ds = reinterpret_cast<double*>(csm + a.dsh_ofs);
-        for (int i = tid; i < KMAXP; i += nthr) ds[i] = a.dsh[i];
+        for (int i = tid; i < W; i += nthr) ds[i] = a.dsh[ch + i];
         for (int l = 0; l < a.nlev; ++l) {
             const CoarseLevel& c = a.lev[l];
             if (c.cofs == kNoCopy) continue;
             double* t = reinterpret_cast<double*>(csm + c.cofs);
-            const int m = c.deg * a.Kp;
-            for (int i = tid; i < m; i += nthr) { t[i] = c.c1[i]; t[m + i] = c.c2[i]; }
+            const int m = c.deg * W;
+            for (int i = tid; i < m; i += nthr) {
+                const int row = i / W, v = i - row * W;
+                t[i] = c.c1[row * Kp + ch + v];
+                t[m + i] = c.c2[row * Kp + ch + v];
+            }
         }
     }
     __syncthreads();
     const double* dsh = reinterpret_cast<const double*>(csm + a.dsh_ofs);
-    auto tab1 = [&](const CoarseLevel& c) {
-        return c.cofs == kNoCopy ? c.c1 : reinterpret_cast<const double*>(csm + c.cofs);
-    };
-    auto tab2 = [&](const CoarseLevel& c) {
-        return c.cofs == kNoCopy ? c.c2 : reinterpret_cast<const double*>(csm + c.cofs) + c.deg * a.Kp;
+    // step m of level c's Chebyshev tables: compact copies in shared memory or the global rows
+    auto step = [&](const CoarseLevel& c, int m, bool with_c1) {
+        if (c.cofs == kNoCopy)
+            return ChebStep{with_c1 ? c.c1 + (size_t)m * Kp + ch : nullptr, c.c2 + (size_t)m * Kp + ch};
+        const double* t = reinterpret_cast<const double*>(csm + c.cofs);
+        return ChebStep{with_c1 ? t + m * W : nullptr, t + (c.deg + m) * W};
     };
     // down: pre-smoothing and restriction
     for (int l = 0; l < a.nlev; ++l) {
@@ -759,39 +775,38 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
         T* D = at(c.dd);
         const T* b = at(c.b);
         if (l == a.exact) {  // dense exact solve of every shifted system: A = M_j b
-            constexpr int W = VecT<T>::W;
             const int n = (int)c.L.N;
-            const int off = threadIdx.x * W;
-            const T* M = reinterpret_cast<const T*>(a.minv);
+            const T* M = reinterpret_cast<const T*>(a.minv) + ch;
             for (int i = threadIdx.y; i < n; i += blockDim.y) {
                 T acc[W];
                 for (int v = 0; v < W; ++v) acc[v] = T(0);
-                const T* row = M + (size_t)i * n * a.Kp + off;
+                const T* row = M + (size_t)i * n * Kp;
 #pragma unroll 4
                 for (int jj = 0; jj < n; ++jj) {
                     T m[W], bv[W];
-                    vld(row + (size_t)jj * a.Kp, m);
-                    vld(b + (size_t)jj * a.Kp + off, bv);
+                    vld(row + (size_t)jj * Kp, m);
+                    vld(b + (size_t)jj * Ks, bv);
                     for (int v = 0; v < W; ++v) acc[v] = fma(m[v], bv[v], acc[v]);
                 }
-                vst(A + (size_t)i * a.Kp + off, acc);
+                vst(A + (size_t)i * Ks, acc);
             }
             __syncthreads();
             break;
         }
-        sw_cheb_zero<T, DIM, VAR>(c.L, a.Kp, b, A, ChebStep{tab1(c), tab2(c)}, dsh, 0, 1);
+        sw_cheb_zero<T, DIM, VAR>(c.L, Ks, b, A, step(c, 0, true), dsh, 0, 1);
         __syncthreads();
         T* cur = A;
         T* oth = B;
         for (int m = 1; m < deg; ++m) {
             LoadPlain<T> ld{cur};
-            sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 1 ? cur : D, false, b, oth, m < deg - 1 ? D : nullptr,
-                                      ChebStep{tab1(c) + m * a.Kp, tab2(c) + m * a.Kp}, dsh, nullptr, 0, 1);
+            // after the step from zero the previous Chebyshev direction is the iterate itself
+            sw_cheb_step<T, DIM, VAR>(c.L, Ks, ld, m == 1 ? nullptr : D, m == 1, b, oth, m < deg - 1 ? D : nullptr,
+                                      step(c, m, true), dsh, nullptr, 0, 1);
             __syncthreads();
             T* t = cur; cur = oth; oth = t;
         }
         if (l + 1 < a.nlev) {
-            sw_restrict<T, DIM, VAR>(c.L, a.lev[l + 1].L, a.Kp, cur, b, at(a.lev[l + 1].b), dsh, 0, 1);
+            sw_restrict<T, DIM, VAR>(c.L, a.lev[l + 1].L, Ks, cur, b, at(a.lev[l + 1].b), dsh, 0, 1);
             __syncthreads();
         }
     }
@@ -805,22 +820,25 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
         const T* b = at(c.b);
         T* cur = ((deg - 1) % 2 == 0) ? A : B;  // where the pre-smoothing ended
         T* oth = cur == A ? B : A;
-        sw_prolong_add<T, DIM>(c.L, a.lev[l + 1].L, a.Kp, at(a.lev[l + 1].result), cur, 0, 1);
+        sw_prolong_add<T, DIM>(c.L, a.lev[l + 1].L, Ks, at(a.lev[l + 1].result), cur, 0, 1);
         __syncthreads();
         for (int m = 0; m < deg; ++m) {
             LoadPlain<T> ld{cur};
-            sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 0 ? nullptr : D, false, b, oth, m < deg - 1 ? D : nullptr,
-                                      ChebStep{m == 0 ? nullptr : tab1(c) + m * a.Kp, tab2(c) + m * a.Kp}, dsh, nullptr,
-                                      0, 1);
+            sw_cheb_step<T, DIM, VAR>(c.L, Ks, ld, m == 0 ? nullptr : D, false, b, oth, m < deg - 1 ? D : nullptr,
+                                      step(c, m, m != 0), dsh, nullptr, 0, 1);
             __syncthreads();
             T* t = cur; cur = oth; oth = t;
         }
     }
     {
-        const int n = (int)(a.lev[0].L.N * a.Kp);
+        const int n = (int)a.lev[0].L.N;
         const T* src = at(a.lev[0].result);
-        T* dst = reinterpret_cast<T*>(a.x_out);
-        for (int i = tid; i < n; i += nthr) dst[i] = src[i];
+        T* dst = reinterpret_cast<T*>(a.x_out) + ch;
+        for (int i = tid; i < n; i += nthr) {
+            T v[W];
+            vld(src + (size_t)i * Ks, v);
+            vst(dst + (size_t)i * Kp, v);
+        }
     }
 }
 
@@ -993,7 +1011,8 @@ cudaError_t Ops<T>::prepare_coarse(int dim, bool var, size_t smem_bytes) {
 
 template <class T>
 void Ops<T>::coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s) {
-    BURA_DISPATCH_PDL(dim, var, k_coarse_cycle, dim3(1), blk(g1), (size_t)a.smem_bytes, s, a);
+    // one CTA per 16-byte chunk of systems, each with its whole thread block on that chunk
+    BURA_DISPATCH_PDL(dim, var, k_coarse_cycle, dim3(g1.C), dim3(1, kCoarseThreads), (size_t)a.smem_bytes, s, a);
 }
 
 template <class T>

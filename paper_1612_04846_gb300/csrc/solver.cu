@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -432,7 +433,8 @@ int build_tma(bura_plan* p, Work<T>& w) {
         if (w.lc >= 0 && l >= w.lc) break;
         const bool has_coarse = l + 1 < nlev;
         const TmaGeo g = tma_geo(w.L[l], has_coarse ? &w.L[l + 1] : nullptr, w.Kp);
-        if (g.ntiles < p->nsm) break;
+        // every grid level: even with fewer tiles than SMs the fused 3-launch V-cycle step beats the
+        // 5 grid launches of a small level (measured on GB300: 255^2 ... 63^2 levels of a 1023^2 solve)
         auto& t = w.tma[l];
         t.geo = g;
         const void* bl = l == 0 ? (const void*)w.r : (const void*)w.b[l];
@@ -448,12 +450,21 @@ int build_tma(bura_plan* p, Work<T>& w) {
             want.push_back({TB_CPRO, w.xa[l + 1], l + 1});
             want.push_back({TB_CPRO, w.xb[l + 1], l + 1});
         }
+        bool ok = true;
         for (const Want& e : want) {
             typename Work<T>::TmaLev::Ent ent;
             ent.box = e.box;
             ent.buf = e.buf;
-            CK(tma_encode(&ent.map, reinterpret_cast<const float*>(e.buf), w.Kp, w.L[e.lev].nx, w.L[e.lev].ny, e.box));
+            if (tma_encode(&ent.map, reinterpret_cast<const float*>(e.buf), w.Kp, w.L[e.lev].nx, w.L[e.lev].ny,
+                           e.box) != cudaSuccess) {
+                ok = false;  // a map the driver does not accept: this level and the coarser ones stay on grid kernels
+                break;
+            }
             t.maps.push_back(ent);
+        }
+        if (!ok) {
+            t = typename Work<T>::TmaLev();
+            break;
         }
         t.on = true;
         any = true;
@@ -552,7 +563,8 @@ int build_work(bura_plan* p, Work<T>& w) {
         // the smallest levels run together in one CTA with all their vectors in shared memory
         for (int l = 0; l <= last; ++l) {
             size_t bytes = 0;
-            for (int m = l; m <= last; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.Kp * sizeof(T) + 15) / 16 * 16);
+            // one CTA per 16-byte chunk: each holds its chunk's W values per point
+            for (int m = l; m <= last; ++m) bytes += 4 * (((size_t)p->hl[m].N * w.W * sizeof(T) + 15) / 16 * 16);
             if (bytes <= kCoarseSmem && last - l + 1 <= kMaxCoarseLevels) {
                 w.lc = l;
                 w.coarse_smem = bytes;
@@ -606,10 +618,11 @@ ChebStep step_of(const Work<T>& w, int l, int m, bool with_c1 = true) {
     return ChebStep{with_c1 ? w.c1[l] + (size_t)m * w.Kp : nullptr, w.c2[l] + (size_t)m * w.Kp};
 }
 
-// Launch the single-CTA V-cycle over levels w.lc..nlev-1 for the right-hand side b (global); the
-// result of level lc is written to w.xa[lc].  Inside the CTA every level has b, xa, xb, dd in shared
-// memory; a level's pre-smoothing (zero step + deg-1 steps) ends in xa when deg-1 is even and its
-// post-smoothing toggles deg more times (the coarsest level has no post-smoothing).
+// Launch the shared-memory V-cycle over levels w.lc..nlev-1 for the right-hand side b (global), one
+// CTA per 16-byte chunk of systems; the result of level lc is written to w.xa[lc].  Inside a CTA every
+// level has b, xa, xb, dd of its chunk in shared memory; a level's pre-smoothing (zero step + deg-1
+// steps) ends in xa when deg-1 is even and its post-smoothing toggles deg more times (the coarsest
+// level has no post-smoothing).
 template <class T>
 T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
     const int nlev = (int)p->hl.size();
@@ -628,7 +641,7 @@ T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
     cof += KMAXP * sizeof(double);
     for (int i = 0; i < a.nlev; ++i) {
         const int l = w.lc + i;
-        const unsigned int vb = (unsigned int)((((size_t)p->hl[l].N * w.Kp * sizeof(T)) + 15) / 16 * 16);
+        const unsigned int vb = (unsigned int)((((size_t)p->hl[l].N * w.W * sizeof(T)) + 15) / 16 * 16);
         CoarseLevel& c = a.lev[i];
         c.L = w.L[l];
         c.b = off;
@@ -644,7 +657,7 @@ T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
         c.c1 = w.c1[l];
         c.c2 = w.c2[l];
         c.deg = deg;
-        const unsigned int tb = (unsigned int)(2 * deg * w.Kp * sizeof(double));
+        const unsigned int tb = (unsigned int)(2 * deg * w.W * sizeof(double));
         if (tb <= 4096 && cof + tb <= w.coarse_smem + KMAXP * sizeof(double) + kCoarseTables) {
             c.cofs = cof;
             cof += tb;
