@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbura.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "solver.cu",
+           "noalloc.cu"]
 HEADERS = ["kernels.cuh", "kernels_impl.cuh", "tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

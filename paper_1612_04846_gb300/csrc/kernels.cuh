@@ -194,19 +194,31 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// FP64 refinement and output kernels.
-void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
-                       double* r, const Red& red, cudaStream_t s);
-void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K, const double* r64,
-                        const double* scale, float* r32, float* x32, float* p32, cudaStream_t s);
-void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
-                      const double* scale, cudaStream_t s);
+// FP64 output kernels.
 void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s);
 void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s);
-void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const double* invscale, float* r32,
-                   float* x32, float* p32, cudaStream_t s);
 void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s);
 void launch_scatter_systems(long long N, int Kp, int K, const double* X, double* x, cudaStream_t s);
 void launch_gather_systems_f(long long N, int Kp, int K, const float* v, double* V, cudaStream_t s);
+
+// Double-float refinement of the mixed path (kernels_df.cu).  DfOpHost holds device pointers and the
+// hi/lo FP32 parts of the level-0 operator's coefficients.
+struct DfOpHost {
+    float w[3][2];                       // constant face weights (hi, lo)
+    const float* ch = nullptr;           // diag - d_j (constant coefficients), Kp entries each
+    const float* cl = nullptr;
+    const float* dh = nullptr;           // d_j (variable coefficients)
+    const float* dl = nullptr;
+    const float* fh[3] = {nullptr, nullptr, nullptr};  // scaled face coefficients (variable coefficients)
+    const float* fl[3] = {nullptr, nullptr, nullptr};
+};
+void launch_update_residual_df(const Launch& g, const Lev& L, int dim, bool var, const DfOpHost& h, const float* fh,
+                               const float* fl, const float* vhin, const float* vlin, const float* x, float* vhout,
+                               float* vlout, float* r32, float sf, const Red& red, cudaStream_t s);
+void launch_cast_f_df(const Launch& g32, long long N, int K, const double* f, double sf, float* r32, float* x32,
+                      float* p32, float* fh, float* fl, cudaStream_t s);
+void launch_weighted_sum_df(long long N, int Kp, int K, const float* vh, const float* vl, const float* ch,
+                            const float* cl, double* u, cudaStream_t s);
+void launch_gather_df(long long N, int Kp, int K, const float* vh, const float* vl, double* V, cudaStream_t s);
 
 }  // namespace bura

@@ -44,9 +44,9 @@ const char* const kNames[K_NK][2][2] = {
     {{"dot_f64", "dot_f64@coarse"}, {"dot_f32", "dot_f32@coarse"}},
     {{"broadcast_f64", "broadcast_f64"}, {"broadcast_f32", "broadcast_f32"}},
     {{"norm2", "norm2"}, {"norm2", "norm2"}},
-    {{"residual64", "residual64"}, {"residual64", "residual64"}},
-    {{"cast_scaled", "cast_scaled"}, {"cast_scaled", "cast_scaled"}},
-    {{"correct64", "correct64"}, {"correct64", "correct64"}},
+    {{"update_residual_df", "update_residual_df"}, {"update_residual_df", "update_residual_df"}},
+    {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}},
+    {{"unused", "unused"}, {"unused", "unused"}},
     {{"weighted_sum", "weighted_sum"}, {"weighted_sum", "weighted_sum"}},
     {{"gather_systems", "gather_systems"}, {"gather_systems", "gather_systems"}},
     {{"coarse_cluster_f64", "coarse_cluster_f64@coarse"}, {"coarse_cluster_f32", "coarse_cluster_f32@coarse"}},
@@ -129,8 +129,16 @@ struct bura_plan {
     double* partial = nullptr;
     unsigned int* tickets = nullptr;
     double* red_out = nullptr;  // [KMAXP]
-    double* scale = nullptr;    // [KMAXP] refinement scales
-    double* invscale = nullptr;
+    // mixed path: refinement accumulator v_j as FP32 pairs hi + lo (Kp32 layout, two ping-pong copies),
+    // f as a pair, and the pair form of the level-0 operator's and the weighted sum's coefficients
+    float* vh[2] = {nullptr, nullptr};
+    float* vl[2] = {nullptr, nullptr};
+    int vcur = 0;
+    float* fh = nullptr;
+    float* fl = nullptr;
+    DfOpHost dfop;
+    float* cwh = nullptr;  // c_j hi / lo, KMAXP entries
+    float* cwl = nullptr;
     Scal* scal_outer = nullptr;
     Scal* hscal = nullptr;      // pinned host mirror
     double* hbuf = nullptr;     // pinned host scratch [4*KMAXP]
@@ -982,10 +990,13 @@ int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
 
 int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     Work<float>& w = p->w32;
-    const Launch& g64 = p->w64.g[0];
-    const Lev& L64 = p->w64.L[0];
+    const Launch& g32 = w.g[0];
+    const Lev& L32 = w.L[0];
     const long long N = p->hl[0].N;
-    CK(cudaMemsetAsync(p->v64, 0, (size_t)N * g64.Kp * sizeof(double), s));
+    const size_t vb = (size_t)N * w.Kp * sizeof(float);
+    p->vcur = 0;
+    CK(cudaMemsetAsync(p->vh[0], 0, vb, s));
+    CK(cudaMemsetAsync(p->vl[0], 0, vb, s));
     Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
     // the residual of the zero initial guess is f itself: only its norm is needed
     traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
@@ -993,6 +1004,10 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const double fnorm2 = p->hbuf[0];
+    if (!std::isfinite(fnorm2)) return BURA_ENOTSPD;
+    // The inner FP32 solves work on sf * residual with sf a power of two that brings f's typical entry
+    // near 1 (exact scaling, no FP32 range trouble); their thresholds are in the same units.
+    const double sf = fnorm2 > 0 ? std::ldexp(1.0, -(int)std::lround(0.5 * std::log2(fnorm2 / (double)N))) : 1.0;
     double thr64[KMAXP] = {0};
     double rr[KMAXP] = {0};
     thresholds(p, tol, fnorm2, thr64);
@@ -1012,12 +1027,17 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     int siters[KMAXP] = {0};
     for (;;) {
         if (outer > 0) {
-            traced(p, K_RES64, false, true, (double)N * 8 + vbytes<double>(p, 0, 2.0, true), s,
-                   [&] { launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s); });
+            // v <- v + x / sf and the next scaled right-hand side sf (f - (A - d_j I) v), in FP32 pairs
+            const int nxt = p->vcur ^ 1;
+            traced(p, K_RES64, true, true, vbytes<float>(p, 0, 6.0, true) + (double)N * 8, s, [&] {
+                launch_update_residual_df(g32, L32, p->dim, p->var, p->dfop, p->fh, p->fl, p->vh[p->vcur],
+                                          p->vl[p->vcur], w.x, p->vh[nxt], p->vl[nxt], w.r, (float)sf, store, s);
+            });
             CKL();
+            p->vcur = nxt;
             CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int j = 0; j < p->K; ++j) rr[j] = p->hbuf[j];
+            for (int j = 0; j < p->K; ++j) rr[j] = p->hbuf[j] / (sf * sf);
         }
         int act[KMAXP] = {0};
         int na = 0;
@@ -1028,39 +1048,30 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
         }
         if (na == 0) { rc = BURA_OK; break; }
         if (outer >= p->opt.max_outer) { rc = BURA_ENOCONV; break; }
-        double* hs = p->hbuf + KMAXP;
-        double* his = p->hbuf + 2 * KMAXP;
         double thr[KMAXP] = {0};
         for (int j = 0; j < KMAXP; ++j) {
-            const bool a = j < p->K && act[j];
-            hs[j] = a ? std::sqrt(rr[j]) : 0.0;
-            his[j] = a ? 1.0 / hs[j] : 0.0;
-            if (a) {
-                // relative target of this inner solve (the scaled rhs has unit norm): the planned
-                // share, or less if that already meets the FP64 threshold (with a margin of 2)
-                const double need = 0.5 * std::sqrt(thr64[j] / rr[j]);
-                const double t = std::max(step_target[j] * 0.5, need);
-                thr[j] = t * t;
-            }
+            if (!(j < p->K && act[j])) continue;
+            // relative target of this inner solve: the planned share, or less if that already meets the
+            // FP64 threshold (with a margin of 2); absolute in the scaled units of the inner solve
+            const double need = 0.5 * std::sqrt(thr64[j] / rr[j]);
+            const double t = std::max(step_target[j] * 0.5, need);
+            thr[j] = t * t * rr[j] * sf * sf;
         }
-        CK(cudaMemcpyAsync(p->scale, hs, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(p->invscale, his, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
-        if (outer == 0)
-            traced(p, K_CAST, false, true, (double)N * 8 + vbytes<float>(p, 0, 3.0, false), s,
-                   [&] { launch_cast_f(w.g[0], N, p->K, f, p->invscale, w.r, w.x, w.pa, s); });
-        else
-            traced(p, K_CAST, false, true, vbytes<double>(p, 0, 1.0, false) + vbytes<float>(p, 0, 3.0, false), s,
-                   [&] { launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s); });
-        CKL();
+        if (outer == 0) {
+            traced(p, K_CAST, false, true, (double)N * 8 + vbytes<float>(p, 0, 3.0, false) + (double)N * 8, s,
+                   [&] { launch_cast_f_df(g32, N, p->K, f, sf, w.r, w.x, w.pa, p->fh, p->fl, s); });
+            CKL();
+        } else {
+            // zero iterate and direction of the next inner solve (the residual kernel wrote its rhs)
+            CK(cudaMemsetAsync(w.x, 0, vb, s));
+            CK(cudaMemsetAsync(w.pa, 0, vb, s));
+        }
         CA(init_scal(p, w.scal, thr, act, s));
         int it = 0;
         int irc = pcg<float>(p, w, &it, s);
-        if (irc == BURA_ENOTSPD) return irc;
+        if (irc == BURA_ENOTSPD || irc == BURA_ETIMEOUT) return irc;
         for (int j = 0; j < p->K; ++j) siters[j] += p->hscal->iters[j];
         total_it += it;
-        traced(p, K_CORR64, false, true, vbytes<double>(p, 0, 2.0, false) + vbytes<float>(p, 0, 1.0, false), s,
-               [&] { launch_correct64(g64, w.g[0], N, p->K, p->v64, w.x, p->scale, s); });
-        CKL();
         ++outer;
     }
     p->st.iters = total_it;
@@ -1079,11 +1090,61 @@ int solve_core(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     return p->opt.precision == BURA_PREC_FP64 ? solve_fp64(p, f, tol, s) : solve_mixed(p, f, tol, s);
 }
 
-const double* solution_vectors(const bura_plan* p, int* Kp) {
-    if (p->opt.precision == BURA_PREC_FP64) { *Kp = p->w64.Kp; return p->w64.x; }
-    *Kp = p->w64.Kp;
-    return p->v64;
+// Split x into FP32 parts hi + lo with hi = fl32(x) and lo = fl32(x - hi) (x - hi is exact in FP64).
+void split_df(double x, float* hi, float* lo) {
+    *hi = (float)x;
+    *lo = (float)(x - (double)*hi);
 }
+
+// Buffers and coefficient tables of the double-float refinement of the mixed path.
+int build_df(bura_plan* p) {
+    const long long N = p->hl[0].N;
+    const int Kp = p->w32.Kp;
+    const size_t vb = (size_t)N * Kp * sizeof(float);
+    for (int i = 0; i < 2; ++i) {
+        CA(dalloc(p, &p->vh[i], vb));
+        CA(dalloc(p, &p->vl[i], vb));
+    }
+    CA(dalloc(p, &p->fh, (size_t)N * sizeof(float)));
+    CA(dalloc(p, &p->fl, (size_t)N * sizeof(float)));
+    const HostLevel& h = p->hl[0];
+    DfOpHost& op = p->dfop;
+    for (int a = 0; a < 3; ++a) split_df(a < p->dim ? h.w[a] : 0.0, &op.w[a][0], &op.w[a][1]);
+    // per-system tables (KMAXP entries, zero in the padding): diag - d_j, d_j, c_j
+    std::vector<float> t(6 * KMAXP, 0.f);
+    const double diag = 2.0 * (h.w[0] + h.w[1] + (p->dim == 3 ? h.w[2] : 0.0));
+    for (int j = 0; j < p->K; ++j) {
+        split_df(diag - p->d[j], &t[j], &t[KMAXP + j]);
+        split_df(p->d[j], &t[2 * KMAXP + j], &t[3 * KMAXP + j]);
+        split_df(p->c[j], &t[4 * KMAXP + j], &t[5 * KMAXP + j]);
+    }
+    float* dt = nullptr;
+    CA(dalloc(p, &dt, t.size() * sizeof(float)));
+    CK(cudaMemcpy(dt, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+    op.ch = dt;
+    op.cl = dt + KMAXP;
+    op.dh = dt + 2 * KMAXP;
+    op.dl = dt + 3 * KMAXP;
+    p->cwh = dt + 4 * KMAXP;
+    p->cwl = dt + 5 * KMAXP;
+    if (p->var) {
+        for (int a = 0; a < p->dim; ++a) {
+            std::vector<float> fh(h.a[a].size()), fl(h.a[a].size());
+            for (size_t i = 0; i < fh.size(); ++i) split_df(h.a[a][i] * h.w[a], &fh[i], &fl[i]);
+            float *dh = nullptr, *dl = nullptr;
+            CA(dalloc(p, &dh, fh.size() * sizeof(float)));
+            CA(dalloc(p, &dl, fl.size() * sizeof(float)));
+            CK(cudaMemcpy(dh, fh.data(), fh.size() * sizeof(float), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(dl, fl.data(), fl.size() * sizeof(float), cudaMemcpyHostToDevice));
+            op.fh[a] = dh;
+            op.fl[a] = dl;
+        }
+    }
+    return BURA_OK;
+}
+
+// FP64 path: the solutions are w64.x (Kp64 layout); mixed path: the FP32 pairs vh/vl[vcur] (Kp32).
+bool mixed(const bura_plan* p) { return p->opt.precision != BURA_PREC_FP64; }
 
 }  // namespace
 
@@ -1209,8 +1270,7 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if ((rc = dalloc(p, &p->tickets, (max_groups + 1) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
     if (cudaMemset(p->tickets, 0, (max_groups + 1) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
     if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if (o.precision == BURA_PREC_MIXED && (rc = build_df(p)) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     {
@@ -1240,11 +1300,14 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
-    int Kp = 0;
-    const double* v = solution_vectors(p, &Kp);
     const double N = (double)p->hl[0].N;
-    traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s,
-           [&] { launch_weighted_sum(p->hl[0].N, Kp, p->K, v, p->cdev, u, s); });
+    if (mixed(p))
+        traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s, [&] {
+            launch_weighted_sum_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], p->cwh, p->cwl, u, s);
+        });
+    else
+        traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s,
+               [&] { launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, p->w64.x, p->cdev, u, s); });
     CKL();
     p->st.launches = p->tr.launches;
     if (p->tr.on) {
@@ -1276,10 +1339,10 @@ int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, voi
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
-    int Kp = 0;
-    const double* v = solution_vectors(p, &Kp);
-    traced(p, K_GATHER, false, true, 2.0 * p->hl[0].N * p->K * 8.0, s,
-           [&] { launch_gather_systems(p->hl[0].N, Kp, p->K, v, V, s); });
+    traced(p, K_GATHER, false, true, 2.0 * p->hl[0].N * p->K * 8.0, s, [&] {
+        if (mixed(p)) launch_gather_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], V, s);
+        else launch_gather_systems(p->hl[0].N, p->w64.Kp, p->K, p->w64.x, V, s);
+    });
     CKL();
     p->st.launches = p->tr.launches;
     if (p->tr.on) {
