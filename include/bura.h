@@ -77,6 +77,13 @@ typedef enum {
     BURA_SWEEP_GRID = 1  /* grid-stride kernels with direct global loads everywhere */
 } bura_sweep_kind;
 
+/* Arithmetic of the iterative refinement of the mixed path (residual, correction, weighted sum). */
+typedef enum {
+    BURA_REFINE_FP64 = 0, /* IEEE FP64 (default) */
+    BURA_REFINE_DF = 1    /* double-float: FP32 pairs hi + lo (about 48 significant bits) with error-free
+                             FP32 transformations on the FP32 pipes; tolerances down to about 1e-12 */
+} bura_refine;
+
 /* Solver options; bura_default_options() fills the defaults. */
 typedef struct {
     int precision;        /* bura_precision; default BURA_PREC_MIXED */
@@ -94,7 +101,8 @@ typedef struct {
     int cluster_size;     /* largest cluster tried for BURA_COARSE_CLUSTER: 2, 4, 8 or 16; 0 = 16.  The
                              size used is the largest power of two <= this that the device co-schedules */
     int sweeps;           /* bura_sweep_kind; default BURA_SWEEP_AUTO */
-    int reserved[3];
+    int refine;           /* bura_refine (mixed precision only); default BURA_REFINE_FP64 */
+    int reserved[2];
 } bura_options;
 
 /* Statistics of the last bura_solve*/

@@ -23,6 +23,7 @@ BURA_COEF_CONSTANT, BURA_COEF_FACES = 0, 1
 BURA_PREC_FP64, BURA_PREC_MIXED = 0, 1
 BURA_COARSE_AUTO, BURA_COARSE_CLUSTER, BURA_COARSE_CTA, BURA_COARSE_NONE = 0, 1, 2, 3
 BURA_SWEEP_AUTO, BURA_SWEEP_GRID = 0, 1
+BURA_REFINE_FP64, BURA_REFINE_DF = 0, 1
 
 
 class bura_grid(C.Structure):
@@ -34,7 +35,7 @@ class bura_options(C.Structure):
                 ("max_iters", C.c_int), ("max_outer", C.c_int), ("inner_rtol", C.c_double),
                 ("coarse_degree", C.c_int), ("block_points", C.c_int), ("blocks_per_sm", C.c_int),
                 ("coarse_kernel", C.c_int), ("cluster_size", C.c_int), ("sweeps", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("refine", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class bura_stats(C.Structure):

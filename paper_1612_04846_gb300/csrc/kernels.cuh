@@ -194,7 +194,15 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// FP64 output kernels.
+// FP64 refinement and output kernels.
+void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
+                       double* r, const Red& red, cudaStream_t s);
+void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K, const double* r64,
+                        const double* scale, float* r32, float* x32, float* p32, cudaStream_t s);
+void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
+                      const double* scale, cudaStream_t s);
+void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const double* invscale, float* r32,
+                   float* x32, float* p32, cudaStream_t s);
 void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s);
 void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s);
 void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s);

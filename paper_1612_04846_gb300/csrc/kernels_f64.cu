@@ -1,11 +1,98 @@
-// FP64 instantiation of the multi-shift MG-PCG kernels, plus the FP64 reduction and output kernels
-// (norm of f, weighted sum, gather / scatter of the systems).
+// FP64 instantiation of the multi-shift MG-PCG kernels, plus the FP64 refinement, cast and output
+// kernels shared by both precision paths.
 #include <cstddef>
 
 #include "kernels_impl.cuh"
 
 namespace bura {
 template struct Ops<double>;
+
+// r = f - (A - d_j I) v (FP64 true residual of every system) and ||r_j||^2 -> red.out.
+template <int DIM, bool VAR>
+__global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const double* __restrict__ v,
+                             double* __restrict__ r, const double* __restrict__ dsh, Red red) {
+    constexpr int W = 2;
+    const int off = threadIdx.x * W;
+    double d[W];
+    for (int q = 0; q < W; ++q) d[q] = dsh[off + q];
+    LoadPlain<double> ld{v};
+    Accum<double> acc;
+    sweep_u<StencilState<double>>(
+        L.N, blockIdx.x, gridDim.x,
+        [&](int P, StencilState<double>& st) {
+            stencil<double, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag);
+            st.bv[0] = __ldg(f + P);
+        },
+        [&](int P, StencilState<double>& st) {
+            double rv[W];
+            for (int q = 0; q < W; ++q) rv[q] = st.bv[0] - fma(-d[q], st.xc[q], st.Ax[q]);
+            vst(r + (size_t)P * Kp + off, rv);
+            acc.add(rv, rv);
+        });
+    pdl_trigger();
+    reduce_finish<double>(acc, red, Kp);
+}
+
+void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
+                       double* r, const Red& red, cudaStream_t s) {
+    const size_t sh = (size_t)g.C * g.PPB * 2 * sizeof(double);
+    // the shifts live in the device Scal record (address arithmetic only, no host dereference)
+    const double* dsh = reinterpret_cast<const double*>(reinterpret_cast<const char*>(red.scal) + offsetof(Scal, dsh));
+    if (dim == 2 && !var) k_residual64<2, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else if (dim == 2) k_residual64<2, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else if (!var) k_residual64<3, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else k_residual64<3, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+}
+
+// r32 = r64 * invscale_j (systems j < K with invscale > 0, else 0); x32 = 0; p32 = 0.  FP32 layout.
+__global__ void k_cast_scaled(int N, int Kp64, int Kp32, int K, const double* __restrict__ r64,
+                              const double* __restrict__ invscale, float* __restrict__ r32, float* __restrict__ x32,
+                              float* __restrict__ p32) {
+    const int off = threadIdx.x * 4;
+    double is[4];
+    for (int q = 0; q < 4; ++q) is[q] = (off + q < K) ? invscale[off + q] : 0.0;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= N) continue;
+        float rv[4], zv[4];
+        for (int q = 0; q < 4; ++q) {
+            rv[q] = (off + q < K) ? (float)(r64[(size_t)P * Kp64 + off + q] * is[q]) : 0.f;
+            zv[q] = 0.f;
+        }
+        const size_t base = (size_t)P * Kp32 + off;
+        vst(r32 + base, rv);
+        vst(x32 + base, zv);
+        vst(p32 + base, zv);
+    }
+}
+
+void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K, const double* r64,
+                        const double* invscale, float* r32, float* x32, float* p32, cudaStream_t s) {
+    k_cast_scaled<<<g32.blocks, dim3(g32.C, g32.PPB), 0, s>>>((int)N, g64.Kp, g32.Kp, K, r64, invscale, r32, x32, p32);
+}
+
+// v += scale_j * e (FP32 correction promoted to FP64); one thread per (point, pair of systems).
+__global__ void k_correct64(int N, int Kp64, int Kp32, int K, double* __restrict__ v, const float* __restrict__ e,
+                            const double* __restrict__ scale) {
+    const int off = threadIdx.x * 2;
+    double sc[2];
+    for (int q = 0; q < 2; ++q) sc[q] = (off + q < K) ? scale[off + q] : 0.0;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= N) continue;
+        const size_t b64 = (size_t)P * Kp64 + off;
+        const float2 ev = *reinterpret_cast<const float2*>(e + (size_t)P * Kp32 + off);
+        double2 vv = *reinterpret_cast<double2*>(v + b64);
+        vv.x = fma(sc[0], (double)ev.x, vv.x);
+        vv.y = fma(sc[1], (double)ev.y, vv.y);
+        *reinterpret_cast<double2*>(v + b64) = vv;
+    }
+}
+
+void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
+                      const double* scale, cudaStream_t s) {
+    k_correct64<<<g64.blocks, dim3(g64.C, g64.PPB), 0, s>>>((int)N, g64.Kp, g32.Kp, K, v, e, scale);
+}
 
 // ||f||^2 of a plain FP64 vector (red.out[0]); threads laid out as (1, 256) with two lanes of which
 // the second stays zero, so the shared reduction machinery applies unchanged.
@@ -22,6 +109,30 @@ void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStr
     long long b = (N + 255) / 256;
     const int blocks = (int)(b < nsm * 8 ? (b > 0 ? b : 1) : nsm * 8);
     k_norm2<<<blocks, dim3(1, 256), 256 * 2 * sizeof(double), s>>>((int)N, f, red);
+}
+
+// r32 = f * invscale_j for every active system (the residual of the zero initial guess); x32 = p32 = 0.
+__global__ void k_cast_f(int N, int Kp32, int K, const double* __restrict__ f, const double* __restrict__ invscale,
+                         float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32) {
+    const int off = threadIdx.x * 4;
+    double is[4];
+    for (int q = 0; q < 4; ++q) is[q] = (off + q < K) ? invscale[off + q] : 0.0;
+    for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
+        const int P = tile * blockDim.y + threadIdx.y;
+        if (P >= N) continue;
+        const double fv = f[P];
+        float rv[4], zv[4];
+        for (int q = 0; q < 4; ++q) { rv[q] = (float)(fv * is[q]); zv[q] = 0.f; }
+        const size_t base = (size_t)P * Kp32 + off;
+        vst(r32 + base, rv);
+        vst(x32 + base, zv);
+        vst(p32 + base, zv);
+    }
+}
+
+void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const double* invscale, float* r32,
+                   float* x32, float* p32, cudaStream_t s) {
+    k_cast_f<<<g32.blocks, dim3(g32.C, g32.PPB), 0, s>>>((int)N, g32.Kp, K, f, invscale, r32, x32, p32);
 }
 
 // u = sum_j c_j v_j (FP64, fixed order j = 0..K-1); one thread per point.

@@ -30,7 +30,7 @@ struct HostLevel {
 
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
-           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_NK };
+           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -44,14 +44,16 @@ const char* const kNames[K_NK][2][2] = {
     {{"dot_f64", "dot_f64@coarse"}, {"dot_f32", "dot_f32@coarse"}},
     {{"broadcast_f64", "broadcast_f64"}, {"broadcast_f32", "broadcast_f32"}},
     {{"norm2", "norm2"}, {"norm2", "norm2"}},
-    {{"update_residual_df", "update_residual_df"}, {"update_residual_df", "update_residual_df"}},
-    {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}},
-    {{"unused", "unused"}, {"unused", "unused"}},
+    {{"residual64", "residual64"}, {"residual64", "residual64"}},
+    {{"cast_scaled", "cast_scaled"}, {"cast_scaled", "cast_scaled"}},
+    {{"correct64", "correct64"}, {"correct64", "correct64"}},
     {{"weighted_sum", "weighted_sum"}, {"weighted_sum", "weighted_sum"}},
     {{"gather_systems", "gather_systems"}, {"gather_systems", "gather_systems"}},
     {{"coarse_cluster_f64", "coarse_cluster_f64@coarse"}, {"coarse_cluster_f32", "coarse_cluster_f32@coarse"}},
     {{"pre2_restrict_f64", "pre2_restrict_f64@coarse"}, {"pre2_restrict_f32", "pre2_restrict_f32@coarse"}},
-    {{"prolong_cheb_f64", "prolong_cheb_f64@coarse"}, {"prolong_cheb_f32", "prolong_cheb_f32@coarse"}}};
+    {{"prolong_cheb_f64", "prolong_cheb_f64@coarse"}, {"prolong_cheb_f32", "prolong_cheb_f32@coarse"}},
+    {{"update_residual_df", "update_residual_df"}, {"update_residual_df", "update_residual_df"}},
+    {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -139,6 +141,8 @@ struct bura_plan {
     DfOpHost dfop;
     float* cwh = nullptr;  // c_j hi / lo, KMAXP entries
     float* cwl = nullptr;
+    double* scale = nullptr;    // [KMAXP] refinement scales (FP64 refinement)
+    double* invscale = nullptr;
     Scal* scal_outer = nullptr;
     Scal* hscal = nullptr;      // pinned host mirror
     double* hbuf = nullptr;     // pinned host scratch [4*KMAXP]
@@ -988,7 +992,101 @@ int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     return rc;
 }
 
-int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
+// Mixed path with IEEE FP64 refinement: v_j (Kp64 layout) += scale_j * x_j after each FP32 inner solve,
+// the true residual r_j = f - (A - d_j I) v_j in FP64, and the next inner rhs r_j / ||r_j|| in FP32.
+int solve_mixed_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
+    Work<float>& w = p->w32;
+    const Launch& g64 = p->w64.g[0];
+    const Lev& L64 = p->w64.L[0];
+    const long long N = p->hl[0].N;
+    CK(cudaMemsetAsync(p->v64, 0, (size_t)N * g64.Kp * sizeof(double), s));
+    Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
+    // the residual of the zero initial guess is f itself: only its norm is needed
+    traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
+    CKL();
+    CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double fnorm2 = p->hbuf[0];
+    double thr64[KMAXP] = {0};
+    double rr[KMAXP] = {0};
+    thresholds(p, tol, fnorm2, thr64);
+    for (int j = 0; j < p->K; ++j) rr[j] = fnorm2;
+    // Plan the refinement: system j needs its residual reduced by need_j = sqrt(thr64_j) / ||f||; one
+    // FP32 inner solve is asked for at most a reduction of inner_rtol, so n_j = ceil(log need_j /
+    // log inner_rtol) steps are needed and each takes the even share need_j^(1/n_j).
+    double step_target[KMAXP] = {0};
+    for (int j = 0; j < p->K; ++j) {
+        const double need = fnorm2 > 0 ? std::sqrt(thr64[j] / fnorm2) : 1.0;
+        if (need >= 1.0) { step_target[j] = 1.0; continue; }
+        const int n = std::max(1, (int)std::ceil(std::log(need) / std::log(p->opt.inner_rtol) - 1e-9));
+        step_target[j] = std::pow(need, 1.0 / n);
+    }
+    int total_it = 0, outer = 0;
+    int rc = BURA_ENOCONV;
+    int siters[KMAXP] = {0};
+    for (;;) {
+        if (outer > 0) {
+            traced(p, K_RES64, false, true, (double)N * 8 + vbytes<double>(p, 0, 2.0, true), s,
+                   [&] { launch_residual64(g64, L64, p->dim, p->var, f, p->v64, p->r64, store, s); });
+            CKL();
+            CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int j = 0; j < p->K; ++j) rr[j] = p->hbuf[j];
+        }
+        int act[KMAXP] = {0};
+        int na = 0;
+        for (int j = 0; j < p->K; ++j) {
+            if (!std::isfinite(rr[j])) return BURA_ENOTSPD;
+            act[j] = rr[j] > thr64[j] ? 1 : 0;
+            na += act[j];
+        }
+        if (na == 0) { rc = BURA_OK; break; }
+        if (outer >= p->opt.max_outer) { rc = BURA_ENOCONV; break; }
+        double* hs = p->hbuf + KMAXP;
+        double* his = p->hbuf + 2 * KMAXP;
+        double thr[KMAXP] = {0};
+        for (int j = 0; j < KMAXP; ++j) {
+            const bool a = j < p->K && act[j];
+            hs[j] = a ? std::sqrt(rr[j]) : 0.0;
+            his[j] = a ? 1.0 / hs[j] : 0.0;
+            if (a) {
+                // relative target of this inner solve (the scaled rhs has unit norm): the planned
+                // share, or less if that already meets the FP64 threshold (with a margin of 2)
+                const double need = 0.5 * std::sqrt(thr64[j] / rr[j]);
+                const double t = std::max(step_target[j] * 0.5, need);
+                thr[j] = t * t;
+            }
+        }
+        CK(cudaMemcpyAsync(p->scale, hs, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(p->invscale, his, KMAXP * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (outer == 0)
+            traced(p, K_CAST, false, true, (double)N * 8 + vbytes<float>(p, 0, 3.0, false), s,
+                   [&] { launch_cast_f(w.g[0], N, p->K, f, p->invscale, w.r, w.x, w.pa, s); });
+        else
+            traced(p, K_CAST, false, true, vbytes<double>(p, 0, 1.0, false) + vbytes<float>(p, 0, 3.0, false), s,
+                   [&] { launch_cast_scaled(g64, w.g[0], N, p->K, p->r64, p->invscale, w.r, w.x, w.pa, s); });
+        CKL();
+        CA(init_scal(p, w.scal, thr, act, s));
+        int it = 0;
+        int irc = pcg<float>(p, w, &it, s);
+        if (irc == BURA_ENOTSPD) return irc;
+        for (int j = 0; j < p->K; ++j) siters[j] += p->hscal->iters[j];
+        total_it += it;
+        traced(p, K_CORR64, false, true, vbytes<double>(p, 0, 2.0, false) + vbytes<float>(p, 0, 1.0, false), s,
+               [&] { launch_correct64(g64, w.g[0], N, p->K, p->v64, w.x, p->scale, s); });
+        CKL();
+        ++outer;
+    }
+    p->st.iters = total_it;
+    p->st.outer = outer;
+    for (int j = 0; j <= p->k; ++j) p->st.shift_iters[j] = siters[j];
+    finish_stats(p, rr, fnorm2);
+    return rc;
+}
+
+// Mixed path with double-float refinement (BURA_REFINE_DF): v_j kept as FP32 pairs, correction and true
+// residual fused in one FP32-pipe kernel.
+int solve_mixed_df(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     Work<float>& w = p->w32;
     const Launch& g32 = w.g[0];
     const Lev& L32 = w.L[0];
@@ -1029,7 +1127,7 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
         if (outer > 0) {
             // v <- v + x / sf and the next scaled right-hand side sf (f - (A - d_j I) v), in FP32 pairs
             const int nxt = p->vcur ^ 1;
-            traced(p, K_RES64, true, true, vbytes<float>(p, 0, 6.0, true) + (double)N * 8, s, [&] {
+            traced(p, K_RESDF, true, true, vbytes<float>(p, 0, 6.0, true) + (double)N * 8, s, [&] {
                 launch_update_residual_df(g32, L32, p->dim, p->var, p->dfop, p->fh, p->fl, p->vh[p->vcur],
                                           p->vl[p->vcur], w.x, p->vh[nxt], p->vl[nxt], w.r, (float)sf, store, s);
             });
@@ -1058,7 +1156,7 @@ int solve_mixed(bura_plan* p, const double* f, double tol, cudaStream_t s) {
             thr[j] = t * t * rr[j] * sf * sf;
         }
         if (outer == 0) {
-            traced(p, K_CAST, false, true, (double)N * 8 + vbytes<float>(p, 0, 3.0, false) + (double)N * 8, s,
+            traced(p, K_CASTDF, false, true, (double)N * 8 + vbytes<float>(p, 0, 3.0, false) + (double)N * 8, s,
                    [&] { launch_cast_f_df(g32, N, p->K, f, sf, w.r, w.x, w.pa, p->fh, p->fl, s); });
             CKL();
         } else {
@@ -1087,7 +1185,8 @@ int solve_core(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     p->tr.launches = 0;
     std::memset(p->st.shift_iters, 0, sizeof(p->st.shift_iters));
     std::memset(p->st.rel_res, 0, sizeof(p->st.rel_res));
-    return p->opt.precision == BURA_PREC_FP64 ? solve_fp64(p, f, tol, s) : solve_mixed(p, f, tol, s);
+    if (p->opt.precision == BURA_PREC_FP64) return solve_fp64(p, f, tol, s);
+    return p->opt.refine == BURA_REFINE_DF ? solve_mixed_df(p, f, tol, s) : solve_mixed_fp64(p, f, tol, s);
 }
 
 // Split x into FP32 parts hi + lo with hi = fl32(x) and lo = fl32(x - hi) (x - hi is exact in FP64).
@@ -1143,8 +1242,14 @@ int build_df(bura_plan* p) {
     return BURA_OK;
 }
 
-// FP64 path: the solutions are w64.x (Kp64 layout); mixed path: the FP32 pairs vh/vl[vcur] (Kp32).
-bool mixed(const bura_plan* p) { return p->opt.precision != BURA_PREC_FP64; }
+// Where the solutions are: FP64 path w64.x, mixed path with FP64 refinement v64 (both Kp64 layout),
+// mixed path with double-float refinement the FP32 pairs vh/vl[vcur] (Kp32 layout).
+bool df_solution(const bura_plan* p) {
+    return p->opt.precision != BURA_PREC_FP64 && p->opt.refine == BURA_REFINE_DF;
+}
+const double* solution_vectors(const bura_plan* p) {
+    return p->opt.precision == BURA_PREC_FP64 ? p->w64.x : p->v64;
+}
 
 }  // namespace
 
@@ -1188,7 +1293,8 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
         o.coarse_kernel < BURA_COARSE_AUTO || o.coarse_kernel > BURA_COARSE_NONE ||
         !(o.cluster_size == 0 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8 ||
           o.cluster_size == 16) ||
-        o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID)
+        o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
+        o.refine > BURA_REFINE_DF)
         return BURA_EINVAL;
 
     bura_plan* p = new (std::nothrow) bura_plan();
@@ -1270,7 +1376,9 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if ((rc = dalloc(p, &p->tickets, (max_groups + 1) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
     if (cudaMemset(p->tickets, 0, (max_groups + 1) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
     if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if (o.precision == BURA_PREC_MIXED && (rc = build_df(p)) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if (o.precision == BURA_PREC_MIXED && o.refine == BURA_REFINE_DF && (rc = build_df(p)) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     {
@@ -1301,13 +1409,13 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     const double N = (double)p->hl[0].N;
-    if (mixed(p))
+    if (df_solution(p))
         traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s, [&] {
             launch_weighted_sum_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], p->cwh, p->cwl, u, s);
         });
     else
         traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s,
-               [&] { launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, p->w64.x, p->cdev, u, s); });
+               [&] { launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), p->cdev, u, s); });
     CKL();
     p->st.launches = p->tr.launches;
     if (p->tr.on) {
@@ -1340,8 +1448,8 @@ int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, voi
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     traced(p, K_GATHER, false, true, 2.0 * p->hl[0].N * p->K * 8.0, s, [&] {
-        if (mixed(p)) launch_gather_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], V, s);
-        else launch_gather_systems(p->hl[0].N, p->w64.Kp, p->K, p->w64.x, V, s);
+        if (df_solution(p)) launch_gather_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], V, s);
+        else launch_gather_systems(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), V, s);
     });
     CKL();
     p->st.launches = p->tr.launches;

@@ -204,6 +204,40 @@ def test_mixed_variable_3d_within_tolerance(lib):
     assert _rel(u, direct.bura_sparse(A, f, ref["c"], ref["d"])) <= 1e-6
 
 
+@pytest.mark.parametrize("shape,alpha,k,tol,var", [((127, 127), 0.25, 7, 1e-6, False), ((255, 255), 0.75, 7, 1e-6, False),
+                                                   ((127, 127), 0.5, 7, 1e-9, False), ((31, 31, 31), 0.5, 9, 1e-6, True),
+                                                   ((1023, 1023), 0.75, 7, 1e-6, False)])
+def test_mixed_double_float_refinement(lib, shape, alpha, k, tol, var):
+    """BURA_REFINE_DF: the refinement accumulator as FP32 pairs (about 48 bits), residual and weighted
+    sum in double-float arithmetic.  Same tolerance as the FP64 refinement; bura_solve_systems reads
+    the same pairs (each v_j against the exact (A - d_j I)^{-1} f for constant coefficients)."""
+    nps = _np_shape(shape)
+    faces = W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 2) if var else None
+    f = W.rhs_uniform(nps, 4)
+    u, st, rc, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED, faces=faces, refine=lib.BURA_REFINE_DF)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(alpha, k)
+    if var:
+        A, _ = operators.scaled_matrix(nps, faces)
+        ur = direct.bura_sparse(A, f, ref["c"], ref["d"])
+    else:
+        ur = exact.bura_value(nps, f, ref["c"], ref["d"])
+    assert _rel(u, ur) <= tol, st
+    if not var and shape[0] <= 255:
+        plan = lib.bura_setup(shape, alpha, k, options=_opts(lib, lib.BURA_PREC_MIXED, refine=lib.BURA_REFINE_DF))
+        try:
+            V = torch.zeros((k + 1, f.size), dtype=torch.float64, device="cuda")
+            assert lib.bura_solve_systems(plan, torch.from_numpy(f).cuda(), V, tol) == lib.BURA_OK
+            V = V.cpu().numpy()
+            c, d, _ = lib.bura_get_rational(plan, k)
+        finally:
+            lib.bura_destroy(plan)
+        comp = exact.bura_components(nps, f, d)
+        for j in range(k + 1):
+            # ||e_j|| <= ||r_j|| / (lambda_lo - d_j) <= tol ||f|| / (K c_j), ||v_j|| >= ||f|| / (1 - d_j)
+            assert _rel(V[j], comp[j]) <= tol * (1 - d[j]) / ((k + 1) * c[j]) + 1e-12, j
+
+
 # ------------------------------------------------------------------ full size of the bench workload
 @pytest.mark.parametrize("alpha", [0.25, 0.5, 0.75])
 def test_full_size_1023_mixed_and_fp64(lib, alpha):
