@@ -32,6 +32,7 @@ struct Lev {
     long long N;        // nx*ny*nz
     long long plane;    // nx*ny
     double wx, wy, wz;  // constant-coefficient weights 1/(h^2 Lambda) per axis (wz = 0 in 2D)
+    float wxf, wyf, wzf;  // the same rounded to FP32 (read by the FP32 kernels: no FP64 conversions)
     const void* fx;     // variable coefficients: face weights a/(h^2 Lambda), element type T
     const void* fy;
     const void* fz;
@@ -46,6 +47,9 @@ struct Scal {
     double rr[KMAXP];     // ||r||^2
     double thr[KMAXP];    // stop when rr <= thr
     double dsh[KMAXP];    // shifts d_j
+    float alphaf[KMAXP];  // FP32 copies of alpha, beta and the shifts for the FP32 kernels (GB300's FP64
+    float betaf[KMAXP];   // pipe is too slow for every thread of every launch to convert them)
+    float dshf[KMAXP];
     int active[KMAXP];
     int iters[KMAXP];
     int nactive;
@@ -59,9 +63,10 @@ struct Scal {
 
 // Chebyshev step coefficients of one level: d_m = c1 d_{m-1} + c2 Dinv res (c2 includes 1/(diag - d)
 // for constant coefficients, where Dinv is a per-system scalar).
-struct ChebStep {
-    const double* c1;  // [Kp]
-    const double* c2;  // [Kp]
+template <class C>
+struct ChebStepT {
+    const C* c1;  // [Kp] (null: c1 = 0)
+    const C* c2;  // [Kp]
 };
 
 enum ReduceOp { RED_NONE = 0, RED_ALPHA = 1, RED_CONV = 2, RED_BETA = 3, RED_STORE = 4 };
@@ -84,8 +89,8 @@ struct CoarseLevel {
     Lev L;
     unsigned int b, xa, xb, dd;  // shared-memory byte offsets
     unsigned int result;         // offset of the buffer holding this level's V-cycle result
-    const double* c1;
-    const double* c2;
+    const void* c1;     // Chebyshev tables of the level, element type T
+    const void* c2;
     unsigned int cofs;  // shared-memory byte offset of a copy of c1 then c2 (kNoCopy: read them from global)
     int deg;
 };
@@ -98,8 +103,8 @@ struct ClusterLevel {
     void* xb;
     void* dd;
     const void* result;  // buffer holding this level's V-cycle result
-    const double* c1;
-    const double* c2;
+    const void* c1;     // element type T
+    const void* c2;
     int deg;
 };
 
@@ -108,7 +113,7 @@ struct ClusterArgs {
     int Kp;
     int exact;           // level solved with dense inverses (index in lev[]), -1: none
     const void* minv;
-    const double* dsh;
+    const void* dsh;  // shifts, element type T
     ClusterLevel lev[16];
 };
 constexpr int kClusterThreads = 512;        // threads per CTA of the clustered coarse V-cycle
@@ -124,16 +129,18 @@ constexpr int kSweepMinBlocks = 4;
 constexpr int kCoarseThreads = 512;            // CTA size of the single-CTA coarse V-cycle
 constexpr size_t kCoarseSmem = 200 * 1024;     // shared memory budget of that CTA's vectors
 constexpr size_t kCoarseTables = 16 * 1024;    // and of its copies of the small Chebyshev tables
+constexpr size_t kCoarseSmemMax = 227 * 1024;  // all of that CTA's dynamic shared memory
 struct CoarseArgs {
     int nlev;
     int Kp;
-    const double* dsh;
+    const void* dsh;  // shifts, element type T
     const void* b_in;  // right-hand side of the first coarse level (global)
     void* x_out;       // its V-cycle result (global)
     unsigned int smem_bytes;
     unsigned int dsh_ofs;  // shared-memory byte offset of a copy of the shifts (KMAXP doubles)
     int exact;             // level (index in lev[]) solved exactly by x = M_j b with dense inverses; -1: none
     const void* minv;      // M_j[(row * n + col) * Kp + j], n = points of that level (global, element type T)
+    unsigned int minv_ofs; // shared-memory byte offset of the CTA's chunk of M, [row][col][W] (kNoCopy: read global)
     CoarseLevel lev[kMaxCoarseLevels];
 };
 
@@ -149,17 +156,17 @@ struct Ops {
                        const Red& red, cudaStream_t s);
     static void cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, const T* pb, const T* q,
                           const Red& red, cudaStream_t s);
-    static void cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStep cs,
-                          const double* dsh, cudaStream_t s);
+    static void cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStepT<T> cs,
+                          const T* dsh, cudaStream_t s);
     static void cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,
-                          T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s);
+                          T* xout, T* dout, ChebStepT<T> cs, const T* dsh, const Red& red, cudaStream_t s);
     static void cheb_pre2(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* xout, T* dout,
-                          ChebStep cs0, ChebStep cs1, const double* dsh, cudaStream_t s);
+                          ChebStepT<T> cs0, ChebStepT<T> cs1, const T* dsh, cudaStream_t s);
     static void post_prolong(const Launch& g, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x,
-                             const T* ec, const T* b, T* xout, T* dout, ChebStep cs, const double* dsh,
+                             const T* ec, const T* b, T* xout, T* dout, ChebStepT<T> cs, const T* dsh,
                              const Red& red, cudaStream_t s);
     static void restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x,
-                             const T* b, T* bc, const double* dsh, cudaStream_t s);
+                             const T* b, T* bc, const T* dsh, cudaStream_t s);
     static void prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x,
                             cudaStream_t s);
     static void coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s);
@@ -168,7 +175,7 @@ struct Ops {
     // Largest cluster size (16, 8, 4, 2 or 1) that the device can co-schedule for this kernel.
     static cudaError_t cluster_prepare(int dim, bool var, int threads, int want, int* csize);
     static cudaError_t prepare_coarse(int dim, bool var, size_t smem_bytes);
-    static void apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const double* dsh,
+    static void apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const T* dsh,
                               cudaStream_t s);
     static void dot(const Launch& g, long long N, const T* a, const T* b, const Red& red, cudaStream_t s);
 };

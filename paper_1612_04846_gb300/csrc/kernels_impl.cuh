@@ -14,6 +14,13 @@ namespace cg = cooperative_groups;
 
 namespace bura {
 
+// A CG scalar of the Scal record in the kernel's precision: the FP32 kernels read the FP32 copies.
+template <class T>
+__device__ __forceinline__ T scal_val(const double* d, const float* f, int i) {
+    if constexpr (sizeof(T) == 4) return f[i];
+    else return d[i];
+}
+
 template <class T>
 __device__ __forceinline__ void vld(const T* p, T (&o)[VecT<T>::W]) {
     typename VecT<T>::V v = *reinterpret_cast<const typename VecT<T>::V*>(p);
@@ -99,9 +106,9 @@ __device__ __forceinline__ Wts<T> weights(const Lev& L, int P, const Coord& c) {
             w.zm = w.zp = T(0);
         }
     } else {
-        w.xm = w.xp = (T)L.wx;
-        w.ym = w.yp = (T)L.wy;
-        w.zm = w.zp = (T)L.wz;
+        w.xm = w.xp = sizeof(T) == 4 ? (T)L.wxf : (T)L.wx;
+        w.ym = w.yp = sizeof(T) == 4 ? (T)L.wyf : (T)L.wy;
+        w.zm = w.zp = sizeof(T) == 4 ? (T)L.wzf : (T)L.wz;
     }
     return w;
 }
@@ -255,6 +262,7 @@ __device__ __forceinline__ void finish_one(const Red& red, int s, double tot) {
                 else a = S->rz[s] / tot;
             }
             S->alpha[s] = a;
+            S->alphaf[s] = (float)a;
             break;
         }
         case RED_CONV: {
@@ -274,6 +282,7 @@ __device__ __forceinline__ void finish_one(const Red& red, int s, double tot) {
                 S->rz[s] = tot;
             }
             S->beta[s] = b;
+            S->betaf[s] = (float)b;
             break;
         }
         case RED_STORE:
@@ -418,7 +427,7 @@ struct StencilState {
 
 // x = c2_0 Dinv b (first Chebyshev step from a zero initial guess; pointwise).
 template <class T, int DIM, bool VAR>
-__device__ __forceinline__ void sw_cheb_zero(const Lev& L, int Kp, const T* b, T* x, ChebStep cs, const double* dsh,
+__device__ __forceinline__ void sw_cheb_zero(const Lev& L, int Kp, const T* b, T* x, ChebStepT<T> cs, const T* dsh,
                                              int b0, int nb) {
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
@@ -439,7 +448,7 @@ __device__ __forceinline__ void sw_cheb_zero(const Lev& L, int Kp, const T* b, T
 // din may be null (c1 = 0) and is the loader's own value when din_is_x; dout may be null.
 template <class T, int DIM, bool VAR, class LD>
 __device__ __forceinline__ void sw_cheb_step(const Lev& L, int Kp, const LD& ld, const T* din, bool din_is_x,
-                                             const T* b, T* xout, T* dout, ChebStep cs, const double* dsh,
+                                             const T* b, T* xout, T* dout, ChebStepT<T> cs, const T* dsh,
                                              Accum<T>* acc, int b0, int nb) {
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
@@ -478,7 +487,7 @@ __device__ __forceinline__ void sw_cheb_step(const Lev& L, int Kp, const LD& ld,
 // bc = R (b - (A - dI) x): full weighting, R = P^T / 2^DIM with 1D weights (1/4, 1/2, 1/4).
 template <class T, int DIM, bool VAR>
 __device__ __forceinline__ void sw_restrict(const Lev& Lf, const Lev& Lc, int Kp, const T* x, const T* b, T* bc,
-                                            const double* dsh, int b0, int nb) {
+                                            const T* dsh, int b0, int nb) {
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
     T d[W];
@@ -561,7 +570,10 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_spmv_p(Lev L
     ld.z = z;
     ld.p = pold;
     T dsh[W];
-    for (int v = 0; v < W; ++v) { ld.beta[v] = (T)red.scal->beta[off + v]; dsh[v] = (T)red.scal->dsh[off + v]; }
+    for (int v = 0; v < W; ++v) {
+        ld.beta[v] = scal_val<T>(red.scal->beta, red.scal->betaf, off + v);
+        dsh[v] = scal_val<T>(red.scal->dsh, red.scal->dshf, off + v);
+    }
     Accum<T> acc;
     sweep_u<StencilState<T>>(
         L.N, b0, nb, [&](int P, StencilState<T>& st) { stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag); },
@@ -586,7 +598,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cg_update(in
     const int b0 = blockIdx.x, nb = gridDim.x;
     const T* __restrict__ p = red.scal->parity ? pa : pb;  // the direction k_spmv_p just wrote
     T a[W];
-    for (int v = 0; v < W; ++v) a[v] = (T)red.scal->alpha[off + v];
+    for (int v = 0; v < W; ++v) a[v] = scal_val<T>(red.scal->alpha, red.scal->alphaf, off + v);
     Accum<T> acc;
     struct St { T xv[VecT<T>::W], rv[VecT<T>::W], pv[VecT<T>::W], qv[VecT<T>::W]; };
     sweep_u<St>(
@@ -613,8 +625,8 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cg_update(in
 }
 
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_zero(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ x, ChebStep cs,
-                            const double* __restrict__ dsh) {
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_zero(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ x, ChebStepT<T> cs,
+                            const T* __restrict__ dsh) {
     pdl_wait();
     sw_cheb_zero<T, DIM, VAR>(L, Kp, b, x, cs, dsh, blockIdx.x, gridDim.x);
 }
@@ -622,8 +634,8 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_zero(Le
 // Plain Chebyshev step (input iterate read from xin).
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_step(Lev L, int Kp, const T* __restrict__ xin, const T* __restrict__ din,
-                            const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStep cs,
-                            const double* __restrict__ dsh, Red red) {
+                            const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStepT<T> cs,
+                            const T* __restrict__ dsh, Red red) {
     pdl_wait();
     LoadPlain<T> ld{xin};
     Accum<T> acc;
@@ -638,7 +650,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_step(Le
 // stencil points on the fly (d_1 = x1), then the second step is applied.
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_pre2(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout,
-                            ChebStep cs0, ChebStep cs1, const double* __restrict__ dsh) {
+                            ChebStepT<T> cs0, ChebStepT<T> cs1, const T* __restrict__ dsh) {
     pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
@@ -652,8 +664,8 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_pre2(Le
 // First post-smoothing step with the coarse-grid correction added on the fly: xin = x + P ec.
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_post_prolong(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ ec,
-                               const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStep cs,
-                               const double* __restrict__ dsh, Red red) {
+                               const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStepT<T> cs,
+                               const T* __restrict__ dsh, Red red) {
     pdl_wait();
     constexpr int W = VecT<T>::W;
     LoadProlong<T, DIM> ld{Lf, Lc, Kp, (int)threadIdx.x * W, x, ec};
@@ -673,14 +685,14 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_prolong_add(
 
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_restrict_res(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ b,
-                               T* __restrict__ bc, const double* __restrict__ dsh) {
+                               T* __restrict__ bc, const T* __restrict__ dsh) {
     pdl_wait();
     sw_restrict<T, DIM, VAR>(Lf, Lc, Kp, x, b, bc, dsh, blockIdx.x, gridDim.x);
 }
 
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_apply_shifted(Lev L, int Kp, const T* __restrict__ x, T* __restrict__ y,
-                                const double* __restrict__ dsh) {
+                                const T* __restrict__ dsh) {
     pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
@@ -743,28 +755,41 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
             vst(dst + (size_t)i * Ks, v);
         }
         // the shifts and the small Chebyshev tables are read by every sweep: keep them on chip
-        double* ds = reinterpret_cast<double*>(csm + a.dsh_ofs);
-        for (int i = tid; i < W; i += nthr) ds[i] = a.dsh[ch + i];
+        T* ds = at(a.dsh_ofs);
+        for (int i = tid; i < W; i += nthr) ds[i] = reinterpret_cast<const T*>(a.dsh)[ch + i];
         for (int l = 0; l < a.nlev; ++l) {
             const CoarseLevel& c = a.lev[l];
             if (c.cofs == kNoCopy) continue;
-            double* t = reinterpret_cast<double*>(csm + c.cofs);
+            T* t = at(c.cofs);
             const int m = c.deg * W;
             for (int i = tid; i < m; i += nthr) {
                 const int row = i / W, v = i - row * W;
-                t[i] = c.c1[row * Kp + ch + v];
-                t[m + i] = c.c2[row * Kp + ch + v];
+                t[i] = reinterpret_cast<const T*>(c.c1)[row * Kp + ch + v];
+                t[m + i] = reinterpret_cast<const T*>(c.c2)[row * Kp + ch + v];
+            }
+        }
+        // this chunk's dense inverses (read once per V-cycle by the exact solve): independent 16-byte
+        // loads by every thread now instead of a chain of dependent global loads per row later
+        if (a.exact >= 0 && a.minv_ofs != kNoCopy) {
+            const int n = (int)a.lev[a.exact].L.N;
+            const T* src = reinterpret_cast<const T*>(a.minv) + ch;
+            T* dst = at(a.minv_ofs);
+            for (int i = tid; i < n * n; i += nthr) {
+                T v[W];
+                vld(src + (size_t)i * Kp, v);
+                vst(dst + (size_t)i * W, v);
             }
         }
     }
     __syncthreads();
-    const double* dsh = reinterpret_cast<const double*>(csm + a.dsh_ofs);
+    const T* dsh = at(a.dsh_ofs);
     // step m of level c's Chebyshev tables: compact copies in shared memory or the global rows
     auto step = [&](const CoarseLevel& c, int m, bool with_c1) {
         if (c.cofs == kNoCopy)
-            return ChebStep{with_c1 ? c.c1 + (size_t)m * Kp + ch : nullptr, c.c2 + (size_t)m * Kp + ch};
-        const double* t = reinterpret_cast<const double*>(csm + c.cofs);
-        return ChebStep{with_c1 ? t + m * W : nullptr, t + (c.deg + m) * W};
+            return ChebStepT<T>{with_c1 ? reinterpret_cast<const T*>(c.c1) + (size_t)m * Kp + ch : nullptr,
+                                reinterpret_cast<const T*>(c.c2) + (size_t)m * Kp + ch};
+        const T* t = at(c.cofs);
+        return ChebStepT<T>{with_c1 ? t + m * W : nullptr, t + (c.deg + m) * W};
     };
     // down: pre-smoothing and restriction
     for (int l = 0; l < a.nlev; ++l) {
@@ -776,15 +801,17 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_cycle(CoarseArgs a) {
         const T* b = at(c.b);
         if (l == a.exact) {  // dense exact solve of every shifted system: A = M_j b
             const int n = (int)c.L.N;
-            const T* M = reinterpret_cast<const T*>(a.minv) + ch;
+            const bool staged = a.minv_ofs != kNoCopy;
+            const T* M = staged ? at(a.minv_ofs) : reinterpret_cast<const T*>(a.minv) + ch;
+            const int ms = staged ? W : Kp;  // stride between the entries of M
             for (int i = threadIdx.y; i < n; i += blockDim.y) {
                 T acc[W];
                 for (int v = 0; v < W; ++v) acc[v] = T(0);
-                const T* row = M + (size_t)i * n * Kp;
+                const T* row = M + (size_t)i * n * ms;
 #pragma unroll 4
                 for (int jj = 0; jj < n; ++jj) {
                     T m[W], bv[W];
-                    vld(row + (size_t)jj * Kp, m);
+                    vld(row + (size_t)jj * ms, m);
                     vld(b + (size_t)jj * Ks, bv);
                     for (int v = 0; v < W; ++v) acc[v] = fma(m[v], bv[v], acc[v]);
                 }
@@ -851,6 +878,7 @@ template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kClusterThreads, 1) k_coarse_cluster(ClusterArgs a) {
     pdl_wait();
     cg::cluster_group cl = cg::this_cluster();
+    const T* dshT = reinterpret_cast<const T*>(a.dsh);
     const int rank = (int)cl.block_rank();
     const int ncta = (int)cl.num_blocks();
     for (int l = 0; l < a.nlev; ++l) {
@@ -881,7 +909,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_coarse_cluster(ClusterAr
             cl.sync();
             break;
         }
-        sw_cheb_zero<T, DIM, VAR>(c.L, a.Kp, b, A, ChebStep{c.c1, c.c2}, a.dsh, rank, ncta);
+        sw_cheb_zero<T, DIM, VAR>(c.L, a.Kp, b, A, ChebStepT<T>{reinterpret_cast<const T*>(c.c1), reinterpret_cast<const T*>(c.c2)}, dshT, rank, ncta);
         cl.sync();
         T* cur = A;
         T* oth = B;
@@ -889,12 +917,13 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_coarse_cluster(ClusterAr
             LoadPlain<T> ld{cur};
             // after the step from zero the previous Chebyshev direction is the iterate itself
             sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 1 ? nullptr : D, m == 1, b, oth, m < deg - 1 ? D : nullptr,
-                                      ChebStep{c.c1 + m * a.Kp, c.c2 + m * a.Kp}, a.dsh, nullptr, rank, ncta);
+                                      ChebStepT<T>{reinterpret_cast<const T*>(c.c1) + m * a.Kp, reinterpret_cast<const T*>(c.c2) + m * a.Kp},
+                                      dshT, nullptr, rank, ncta);
             cl.sync();
             T* t = cur; cur = oth; oth = t;
         }
         if (l + 1 < a.nlev) {
-            sw_restrict<T, DIM, VAR>(c.L, a.lev[l + 1].L, a.Kp, cur, b, reinterpret_cast<T*>(a.lev[l + 1].b), a.dsh,
+            sw_restrict<T, DIM, VAR>(c.L, a.lev[l + 1].L, a.Kp, cur, b, reinterpret_cast<T*>(a.lev[l + 1].b), dshT,
                                      rank, ncta);
             cl.sync();
         }
@@ -914,7 +943,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) k_coarse_cluster(ClusterAr
         for (int m = 0; m < deg; ++m) {
             LoadPlain<T> ld{cur};
             sw_cheb_step<T, DIM, VAR>(c.L, a.Kp, ld, m == 0 ? nullptr : D, false, b, oth, m < deg - 1 ? D : nullptr,
-                                      ChebStep{m == 0 ? nullptr : c.c1 + m * a.Kp, c.c2 + m * a.Kp}, a.dsh, nullptr,
+                                      ChebStepT<T>{m == 0 ? nullptr : reinterpret_cast<const T*>(c.c1) + m * a.Kp,
+                                                   reinterpret_cast<const T*>(c.c2) + m * a.Kp},
+                                      dshT, nullptr,
                                       rank, ncta);
             cl.sync();
             T* t = cur; cur = oth; oth = t;
@@ -960,28 +991,28 @@ void Ops<T>::cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, co
 }
 
 template <class T>
-void Ops<T>::cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStep cs,
-                       const double* dsh, cudaStream_t s) {
+void Ops<T>::cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStepT<T> cs,
+                       const T* dsh, cudaStream_t s) {
     BURA_DISPATCH_PDL(dim, var, k_cheb_zero, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, x, cs, dsh);
 }
 
 template <class T>
 void Ops<T>::cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,
-                       T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s) {
+                       T* xout, T* dout, ChebStepT<T> cs, const T* dsh, const Red& red, cudaStream_t s) {
     const size_t sh = red.op != RED_NONE ? shm(g, VecT<T>::W) : 0;
     BURA_DISPATCH_PDL(dim, var, k_cheb_step, dim3(g.blocks), blk(g), sh, s, L, g.Kp, xin, din, b, xout, dout, cs, dsh,
                       red);
 }
 
 template <class T>
-void Ops<T>::cheb_pre2(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* xout, T* dout, ChebStep cs0,
-                       ChebStep cs1, const double* dsh, cudaStream_t s) {
+void Ops<T>::cheb_pre2(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* xout, T* dout, ChebStepT<T> cs0,
+                       ChebStepT<T> cs1, const T* dsh, cudaStream_t s) {
     BURA_DISPATCH_PDL(dim, var, k_cheb_pre2, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, xout, dout, cs0, cs1, dsh);
 }
 
 template <class T>
 void Ops<T>::post_prolong(const Launch& g, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x, const T* ec,
-                          const T* b, T* xout, T* dout, ChebStep cs, const double* dsh, const Red& red,
+                          const T* b, T* xout, T* dout, ChebStepT<T> cs, const T* dsh, const Red& red,
                           cudaStream_t s) {
     const size_t sh = red.op != RED_NONE ? shm(g, VecT<T>::W) : 0;
     BURA_DISPATCH_PDL(dim, var, k_post_prolong, dim3(g.blocks), blk(g), sh, s, Lf, Lc, g.Kp, x, ec, b, xout, dout, cs,
@@ -990,7 +1021,7 @@ void Ops<T>::post_prolong(const Launch& g, const Lev& Lf, const Lev& Lc, int dim
 
 template <class T>
 void Ops<T>::restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x, const T* b,
-                          T* bc, const double* dsh, cudaStream_t s) {
+                          T* bc, const T* dsh, cudaStream_t s) {
     BURA_DISPATCH_PDL(dim, var, k_restrict_res, dim3(gc.blocks), blk(gc), 0, s, Lf, Lc, gc.Kp, x, b, bc, dsh);
 }
 
@@ -1071,7 +1102,7 @@ cudaError_t Ops<T>::cluster_prepare(int dim, bool var, int threads, int want, in
 }
 
 template <class T>
-void Ops<T>::apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const double* dsh,
+void Ops<T>::apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const T* dsh,
                            cudaStream_t s) {
     BURA_DISPATCH_PDL(dim, var, k_apply_shifted, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, y, dsh);
 }

@@ -146,7 +146,7 @@ __device__ __forceinline__ void stencil_tile(const TmaGeo& g, int hidx, const Va
 template <int C, bool HAS_DIN>
 __global__ void __launch_bounds__(kTmaThreads, 2)
     k_cheb_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout, float* __restrict__ dout,
-               ChebStep cs, const double* __restrict__ dsh, Red red) {
+               ChebStepT<float> cs, const float* __restrict__ dsh, Red red) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* smem = aligned_ring(smem_raw);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 template <int C>
 __global__ void __launch_bounds__(kTmaThreads, 2)
     k_pre2_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout, float* __restrict__ dout,
-               ChebStep cs0, ChebStep cs1, const double* __restrict__ dsh, Red none) {
+               ChebStepT<float> cs0, ChebStepT<float> cs1, const float* __restrict__ dsh, Red none) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* smem = aligned_ring(smem_raw);
@@ -288,8 +288,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     float* __restrict__ pnew = par ? pa : pb;
     float beta[4], dsh[4];
     for (int v = 0; v < 4; ++v) {
-        beta[v] = (float)red.scal->beta[off + v];
-        dsh[v] = (float)red.scal->dsh[off + v];
+        beta[v] = red.scal->betaf[off + v];
+        dsh[v] = red.scal->dshf[off + v];
     }
     const unsigned tx_bytes = (unsigned)(2 * kHaloPts * Kp * 4);
     Accum<float> acc;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 template <int C>
 __global__ void __launch_bounds__(kTmaThreads, 2)
     k_pre2_restrict_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ x2out,
-                        float* __restrict__ bc, ChebStep cs0, ChebStep cs1, const double* __restrict__ dsh, Red none) {
+                        float* __restrict__ bc, ChebStepT<float> cs0, ChebStepT<float> cs1, const float* __restrict__ dsh, Red none) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* smem = aligned_ring(smem_raw);
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 template <int C>
 __global__ void __launch_bounds__(kTmaThreads, 2)
     k_prolong_cheb_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout,
-                       float* __restrict__ dout, ChebStep cs, const double* __restrict__ dsh, Red none) {
+                       float* __restrict__ dout, ChebStepT<float> cs, const float* __restrict__ dsh, Red none) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* smem = aligned_ring(smem_raw);
@@ -664,7 +664,7 @@ int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind) {
     }
 
 cudaError_t tma_cheb_step(const TmaGeo& g, int nsm, const CUtensorMap& mx, const CUtensorMap* md, const CUtensorMap& mb,
-                          float* xout, float* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s) {
+                          float* xout, float* dout, ChebStepT<float> cs, const float* dsh, const Red& red, cudaStream_t s) {
     TmaMaps3 mp;
     mp.m[0] = mx;
     mp.m[1] = md ? *md : mx;
@@ -676,8 +676,8 @@ cudaError_t tma_cheb_step(const TmaGeo& g, int nsm, const CUtensorMap& mx, const
     BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, false>, nb, C, smem, s, mp, g, xout, dout, cs, dsh, red))
 }
 
-cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float* xout, float* dout, ChebStep cs0,
-                     ChebStep cs1, const double* dsh, const Red& none, cudaStream_t s) {
+cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float* xout, float* dout, ChebStepT<float> cs0,
+                     ChebStepT<float> cs1, const float* dsh, const Red& none, cudaStream_t s) {
     TmaMaps3 mp;
     mp.m[0] = mp.m[1] = mp.m[2] = mb_halo;
     const int nb = tma_blocks(g, g.Kp, nsm, TK_PRE2);
@@ -686,7 +686,7 @@ cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float
 }
 
 cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rsrc, float* x2out, float* bc,
-                              ChebStep cs0, ChebStep cs1, const double* dsh, const Red& none, cudaStream_t s) {
+                              ChebStepT<float> cs0, ChebStepT<float> cs1, const float* dsh, const Red& none, cudaStream_t s) {
     TmaMaps3 mp;
     mp.m[0] = mp.m[1] = mp.m[2] = mb_rsrc;
     const int nb = tma_blocks(g, g.Kp, nsm, TK_PRE2R);
@@ -695,7 +695,7 @@ cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rs
 }
 
 cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo, const CUtensorMap& mec_cpro,
-                             const CUtensorMap& mb, float* xout, float* dout, ChebStep cs, const double* dsh,
+                             const CUtensorMap& mb, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
                              const Red& none, cudaStream_t s) {
     TmaMaps3 mp;
     mp.m[0] = mx_halo;

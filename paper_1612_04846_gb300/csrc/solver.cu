@@ -75,16 +75,17 @@ struct Work {
     std::vector<Lev> L;
     T *x = nullptr, *r = nullptr, *pa = nullptr, *pb = nullptr, *q = nullptr;
     std::vector<T*> b, xa, xb, dd;
-    std::vector<double*> c1, c2;  // [level] -> deg rows of Kp coefficients
+    std::vector<T*> c1, c2;       // [level] -> deg rows of Kp coefficients, in the kernels' precision
     std::vector<int> deg;
     int lc = -1;                  // first level run by the coarse kernel (-1: none, grid kernels to the end)
     int coarse_kind = 0;          // BURA_COARSE_CLUSTER or BURA_COARSE_CTA
     int csize = 0;                // CTAs of the cluster (cluster kind)
     int le = -1;                  // level solved exactly with dense inverses inside that kernel (-1: none)
     T* minv = nullptr;            // the inverses, [row][col][Kp]
-    size_t coarse_smem = 0;       // shared-memory bytes of the single-CTA kind
+    size_t coarse_smem = 0;       // shared-memory bytes of the single-CTA kind's vectors
+    size_t minv_smem = 0;         // bytes of one chunk's inverses staged in its shared memory (0: not staged)
     Launch gc{};                  // launch shape of the coarse kernel (one CTA)
-    double* dsh = nullptr;
+    T* dsh = nullptr;  // the shifts d_j (KMAXP entries) in the kernels' precision
     Scal* scal = nullptr;
     // TMA-staged sweeps (FP32, 2-D, constant coefficients) of the levels with at least one tile per SM:
     // tensor maps of the level's vectors, with a halo box (stencil inputs) and a plain box
@@ -512,6 +513,9 @@ int build_work(bura_plan* p, Work<T>& w) {
         L.wx = h.w[0];
         L.wy = h.w[1];
         L.wz = p->dim == 3 ? h.w[2] : 0.0;
+        L.wxf = (float)L.wx;
+        L.wyf = (float)L.wy;
+        L.wzf = (float)L.wz;
         L.fx = L.fy = L.fz = nullptr;
         if (p->var) {
             for (int a = 0; a < p->dim; ++a) {
@@ -545,10 +549,11 @@ int build_work(bura_plan* p, Work<T>& w) {
                 f1[(size_t)m * w.Kp + s] = C1[m][s];
                 f2[(size_t)m * w.Kp + s] = C2[m][s];
             }
-        CA(dalloc(p, &w.c1[l], f1.size() * sizeof(double)));
-        CA(dalloc(p, &w.c2[l], f2.size() * sizeof(double)));
-        CK(cudaMemcpy(w.c1[l], f1.data(), f1.size() * sizeof(double), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(w.c2[l], f2.data(), f2.size() * sizeof(double), cudaMemcpyHostToDevice));
+        const std::vector<T> t1(f1.begin(), f1.end()), t2(f2.begin(), f2.end());
+        CA(dalloc(p, &w.c1[l], t1.size() * sizeof(T)));
+        CA(dalloc(p, &w.c2[l], t2.size() * sizeof(T)));
+        CK(cudaMemcpy(w.c1[l], t1.data(), t1.size() * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w.c2[l], t2.data(), t2.size() * sizeof(T), cudaMemcpyHostToDevice));
     }
     // the first level with at most kExactPoints points is solved exactly (dense inverses); the levels
     // below it are never visited
@@ -596,8 +601,15 @@ int build_work(bura_plan* p, Work<T>& w) {
     w.gc.C = w.C;
     w.gc.PPB = (w.coarse_kind == BURA_COARSE_CLUSTER ? kClusterThreads : kCoarseThreads) / w.C;
     w.gc.blocks = 1;
+    // the single-CTA kind stages its chunk of the dense inverses in shared memory when they fit
+    w.minv_smem = 0;
+    if (w.lc >= 0 && w.le >= 0 && w.coarse_kind == BURA_COARSE_CTA) {
+        const size_t mb = (size_t)p->hl[w.le].N * p->hl[w.le].N * w.W * sizeof(T);
+        if (w.coarse_smem + kCoarseTables + KMAXP * sizeof(double) + mb <= kCoarseSmemMax) w.minv_smem = mb;
+    }
     if (w.lc >= 0 && w.coarse_kind == BURA_COARSE_CTA)
-        CK(Ops<T>::prepare_coarse(p->dim, p->var, w.coarse_smem + kCoarseTables + KMAXP * sizeof(double)));
+        CK(Ops<T>::prepare_coarse(p->dim, p->var,
+                                  w.coarse_smem + kCoarseTables + KMAXP * sizeof(double) + w.minv_smem));
     const size_t vb0 = (size_t)p->hl[0].N * w.Kp * sizeof(T);
     CA(dalloc(p, &w.x, vb0));
     CA(dalloc(p, &w.r, vb0));
@@ -606,8 +618,9 @@ int build_work(bura_plan* p, Work<T>& w) {
     CA(dalloc(p, &w.q, vb0));
     std::vector<double> dsh(KMAXP, 0.0);
     for (int s = 0; s < p->K; ++s) dsh[s] = p->d[s];
-    CA(dalloc(p, &w.dsh, KMAXP * sizeof(double)));
-    CK(cudaMemcpy(w.dsh, dsh.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice));
+    const std::vector<T> dsht(dsh.begin(), dsh.end());
+    CA(dalloc(p, &w.dsh, KMAXP * sizeof(T)));
+    CK(cudaMemcpy(w.dsh, dsht.data(), KMAXP * sizeof(T), cudaMemcpyHostToDevice));
     CA(dalloc(p, &w.scal, sizeof(Scal)));
     CK(cudaMemset(w.scal, 0, sizeof(Scal)));
     CA(build_tma(p, w));
@@ -625,9 +638,18 @@ double vbytes(const bura_plan* p, int l, double vec, bool stencil) {
     return b;
 }
 
+// The TMA kernels are FP32 only: these views are taken only when T is float (w.tma[l].on is never set
+// for the FP64 work), where they are the identity.
 template <class T>
-ChebStep step_of(const Work<T>& w, int l, int m, bool with_c1 = true) {
-    return ChebStep{with_c1 ? w.c1[l] + (size_t)m * w.Kp : nullptr, w.c2[l] + (size_t)m * w.Kp};
+ChebStepT<float> f32_step(ChebStepT<T> c) {
+    return ChebStepT<float>{reinterpret_cast<const float*>(c.c1), reinterpret_cast<const float*>(c.c2)};
+}
+template <class T>
+const float* f32_ptr(const T* q) { return reinterpret_cast<const float*>(q); }
+
+template <class T>
+ChebStepT<T> step_of(const Work<T>& w, int l, int m, bool with_c1 = true) {
+    return ChebStepT<T>{with_c1 ? w.c1[l] + (size_t)m * w.Kp : nullptr, w.c2[l] + (size_t)m * w.Kp};
 }
 
 // Launch the shared-memory V-cycle over levels w.lc..nlev-1 for the right-hand side b (global), one
@@ -669,13 +691,18 @@ T* coarse_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
         c.c1 = w.c1[l];
         c.c2 = w.c2[l];
         c.deg = deg;
-        const unsigned int tb = (unsigned int)(2 * deg * w.W * sizeof(double));
+        const unsigned int tb = (unsigned int)(2 * deg * w.W * sizeof(T));
         if (tb <= 4096 && cof + tb <= w.coarse_smem + KMAXP * sizeof(double) + kCoarseTables) {
             c.cofs = cof;
             cof += tb;
         } else {
             c.cofs = kNoCopy;
         }
+    }
+    a.minv_ofs = kNoCopy;
+    if (w.minv_smem > 0) {
+        a.minv_ofs = (unsigned int)(w.coarse_smem + KMAXP * sizeof(double) + kCoarseTables);
+        cof = a.minv_ofs + (unsigned int)w.minv_smem;
     }
     a.smem_bytes = cof;
     traced(p, K_COARSE, sizeof(T) == 4, w.lc == 0, 0.0, s,
@@ -746,13 +773,13 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     T* oth = B;
     const auto& tl = w.tma[l];
     // one Chebyshev step, TMA-staged where the level has tensor maps
-    auto cheb = [&](const T* xin, const T* din, T* xout, T* dout, ChebStep cs, const Red& red) {
+    auto cheb = [&](const T* xin, const T* din, T* xout, T* dout, ChebStepT<T> cs, const Red& red) {
         const CUtensorMap* mx = tl.on ? tl.find(TB_HALO, xin) : nullptr;
         const CUtensorMap* md = tl.on && din ? tl.find(TB_PLAIN, din) : nullptr;
         const CUtensorMap* mb = tl.on ? tl.find(TB_PLAIN, b) : nullptr;
         if (mx && mb && (md || !din))
             (void)tma_cheb_step(tl.geo, p->nsm, *mx, md, *mb, reinterpret_cast<float*>(xout),
-                                reinterpret_cast<float*>(dout), cs, w.dsh, red, s);
+                                reinterpret_cast<float*>(dout), f32_step(cs), f32_ptr(w.dsh), red, s);
         else
             Ops<T>::cheb_step(g, L, dim, var, xin, din, b, xout, dout, cs, w.dsh, red, s);
     };
@@ -767,15 +794,16 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     if (m_rsrc && m_ca && m_cb && m_xa && m_bp) {
         traced(p, K_PRE2R, f32, fine, vbytes<T>(p, l, 2.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
             (void)tma_pre2_restrict(tl.geo, p->nsm, *m_rsrc, reinterpret_cast<float*>(A),
-                                    reinterpret_cast<float*>(w.b[l + 1]), step_of(w, l, 0), step_of(w, l, 1), w.dsh,
-                                    none, s);
+                                    reinterpret_cast<float*>(w.b[l + 1]), f32_step(step_of(w, l, 0)),
+                                    f32_step(step_of(w, l, 1)), f32_ptr(w.dsh), none, s);
         });
         T* ec = vcycle<T>(p, w, l + 1, w.b[l + 1], false, s);
         const CUtensorMap* mec = ec == w.xa[l + 1] ? m_ca : ec == w.xb[l + 1] ? m_cb : nullptr;
         if (mec) {
             traced(p, K_PROCHEB, f32, fine, vbytes<T>(p, l, 4.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
                 (void)tma_prolong_cheb(tl.geo, p->nsm, *m_xa, *mec, *m_bp, reinterpret_cast<float*>(B),
-                                       reinterpret_cast<float*>(D), step_of(w, l, 0, false), w.dsh, none, s);
+                                       reinterpret_cast<float*>(D), f32_step(step_of(w, l, 0, false)), f32_ptr(w.dsh),
+                                       none, s);
             });
         } else {  // a coarse result outside the level's two buffers: unfused correction and first step
             traced(p, K_PROLONG, f32, fine, vbytes<T>(p, l, 2.0, false) + vbytes<T>(p, l + 1, 1.0, false), s,
@@ -797,8 +825,8 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
             const CUtensorMap* mb = tl.on ? tl.find(TB_HALO, b) : nullptr;
             if (mb)
                 (void)tma_pre2(tl.geo, p->nsm, *mb, reinterpret_cast<float*>(A),
-                               reinterpret_cast<float*>(deg > 2 ? D : nullptr), step_of(w, l, 0), step_of(w, l, 1),
-                               w.dsh, none, s);
+                               reinterpret_cast<float*>(deg > 2 ? D : nullptr), f32_step(step_of(w, l, 0)),
+                               f32_step(step_of(w, l, 1)), f32_ptr(w.dsh), none, s);
             else
                 Ops<T>::cheb_pre2(g, L, dim, var, b, A, deg > 2 ? D : nullptr, step_of(w, l, 0), step_of(w, l, 1),
                                   w.dsh, s);
@@ -931,6 +959,7 @@ int init_scal(bura_plan* p, Scal* dev, const double* thr, const int* active, cud
         h.beta[j] = 0.0;
         h.alpha[j] = 0.0;
         h.dsh[j] = j < p->K ? p->d[j] : 0.0;
+        h.dshf[j] = (float)h.dsh[j];
         h.thr[j] = j < p->K ? thr[j] : 0.0;
         h.active[j] = (j < p->K && active[j]) ? 1 : 0;
         na += h.active[j];

@@ -142,17 +142,17 @@ cudaError_t tma_encode(CUtensorMap* m, const float* base, int Kp, int nx, int ny
 cudaError_t tma_prepare(int Kp);
 int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind);
 cudaError_t tma_cheb_step(const TmaGeo& g, int nsm, const CUtensorMap& mx, const CUtensorMap* md, const CUtensorMap& mb,
-                          float* xout, float* dout, ChebStep cs, const double* dsh, const Red& red, cudaStream_t s);
-cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float* xout, float* dout, ChebStep cs0,
-                     ChebStep cs1, const double* dsh, const Red& none, cudaStream_t s);
+                          float* xout, float* dout, ChebStepT<float> cs, const float* dsh, const Red& red, cudaStream_t s);
+cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float* xout, float* dout, ChebStepT<float> cs0,
+                     ChebStepT<float> cs1, const float* dsh, const Red& none, cudaStream_t s);
 // pre2 fused with the residual restriction: x2 = two Chebyshev steps from zero (written to x2out) and
 // bc = R (b - (A - dI) x2) on the coarse level; one tile = kTXc x kTYc coarse points.
 cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rsrc, float* x2out, float* bc,
-                              ChebStep cs0, ChebStep cs1, const double* dsh, const Red& none, cudaStream_t s);
+                              ChebStepT<float> cs0, ChebStepT<float> cs1, const float* dsh, const Red& none, cudaStream_t s);
 // First post-smoothing step on x + P ec (prolongation fused): xout = xin + dnew, dout = dnew with
 // dnew = c2 Dinv (b - (A - dI) xin), xin = x + P ec never stored.
 cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo, const CUtensorMap& mec_cpro,
-                             const CUtensorMap& mb, float* xout, float* dout, ChebStep cs, const double* dsh,
+                             const CUtensorMap& mb, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
                              const Red& none, cudaStream_t s);
 cudaError_t tma_spmv_p(const TmaGeo& g, int nsm, const CUtensorMap& mz, const CUtensorMap& mpa,
                        const CUtensorMap& mpb, float* pa, float* pb, float* q, const Red& red, cudaStream_t s);
