@@ -361,13 +361,42 @@ def bura(alpha, k, dps=60):
         else:
             nxt = 0.5 if abs(alpha - 0.5) <= 0.05 + 1e-12 else round(alpha - (0.05 if alpha > 0.5 else -0.05), 6)
             pbar, qbar, E, pts = _continue_alpha(alpha, k, nxt, list(bura(nxt, k, dps).eta), dps)
-            with mp.workdps(_work_dps(pts, dps)):
-                p, q, d, c, zeta = partial_fractions(pbar, qbar)
-                return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
-        with mp.workdps(_work_dps(pts, dps)):
-            pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=mp.mp.dps)
+            work = _work_dps(pts, dps)
+        if alpha == 0.5:
+            # k-continuation: a run that does not converge at the estimated precision is retried with
+            # 40 and then 80 more digits (Table tabLastS: convergence fails for lack of digits)
+            work = _work_dps(pts, dps)
+            for attempt in range(3):
+                try:
+                    with mp.workdps(work):
+                        pbar, qbar, E, pts1 = remez_bura(alpha, k, pts, dps=work)
+                    pts = pts1
+                    break
+                except RuntimeError:
+                    if attempt == 2:
+                        raise
+                    work += 40
+        # r(0) = E holds exactly for the BURA (t = 0 is an extreme point, where the error is -r(0)); the
+        # Step 3 system meets it only to its working precision divided by |Q(s = -1)|, which can be as
+        # small as 1e-89 of Q's coefficients.  When the computed r(0) misses E by more than 1e-25
+        # relative, Algorithm 1 is rerun from the converged points with 40 more digits.
+        for _ in range(4):
+            with mp.workdps(work):
+                if abs(_r_at_zero(pbar, qbar) - E) <= mp.mpf(10) ** -25 * abs(E):
+                    break
+            work += 40
+            with mp.workdps(work):
+                pbar, qbar, E, pts = remez_bura(alpha, k, pts, dps=work)
+        with mp.workdps(work):
             p, q, d, c, zeta = partial_fractions(pbar, qbar)
             return BuraResult(alpha, k, abs(E), pts, p, q, d, c, zeta, pbar, qbar)
+
+
+def _r_at_zero(pbar, qbar):
+    """r(0) = P(s = -1) / Q(s = -1) from the Chebyshev coefficients (T_i(-1) = (-1)^i)."""
+    num = mp.fsum(v if i % 2 == 0 else -v for i, v in enumerate(pbar))
+    den = mp.fsum(v if i % 2 == 0 else -v for i, v in enumerate(qbar))
+    return num / den
 
 
 def _work_dps(pts, dps):

@@ -98,10 +98,8 @@ def test_stahl_asymptotics_bound_the_error():
 
 
 # ---------------------------------------------------------------- structure of the BURA
-# (0.9, 10) is not in the table: the oracle's alpha-continuation from 0.5 stops converging near
-# alpha = 0.8 at k = 10 and raises rather than return a non-equioscillating approximation.
-@pytest.mark.parametrize("alpha,k", [(a, k) for a in (0.1, 0.25, 0.5, 0.75, 0.9) for k in range(1, 11)
-                                     if (a, k) != (0.9, 10)])
+@pytest.mark.parametrize("alpha,k", [(a, k) for a in (0.1, 0.25, 0.5, 0.75, 0.9) for k in range(1, 11)]
+                         + [(0.5, 11), (0.5, 12)])
 def test_bura_structure(alpha, k):
     """Lemma BURA_caracter (Sec. 2.2) and eqs. (c0,beta), (sum coeff) (Sec. 4.1):
     c_0 = E, sum_j c_j = p_k/q_k, c_j > 0, interlacing 0 > zeta_1 > d_1 > ... > zeta_k > d_k,
