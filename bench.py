@@ -367,6 +367,28 @@ def main(argv=None):
     fp64_solves = n64 / (t64 / 1e3)
     bura.bura_destroy(p64)
 
+    # ---- the same workload with the double-float refinement option (BURA_REFINE_DF), not the headline
+    df_plans = {}
+    for a in ALPHAS:
+        o = bura.bura_default_options()
+        o.refine = bura.BURA_REFINE_DF
+        df_plans[a] = bura.bura_setup(SHAPE, a, K_DEG, options=o)
+    ndf = max(3, args.steps // 4)
+    for i in range(len(ALPHAS)):
+        step(i, df_plans)
+    torch.cuda.synchronize()
+    tdf = 0.0
+    for i in range(ndf):
+        flush.zero_()
+        e0.record(stream)
+        step(i, df_plans)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tdf += e0.elapsed_time(e1)
+    df_solves = ndf / (tdf / 1e3)
+    for a in ALPHAS:
+        bura.bura_destroy(df_plans[a])
+
     # ---- end to end through the host-buffer entry point (H2D of f and D2H of u inside the timing)
     fh = torch.from_numpy(f_host).pin_memory().numpy()
     uh = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
@@ -419,6 +441,7 @@ def main(argv=None):
                 "Gunknown_shifts_per_s": value * N * (K_DEG + 1) / 1e9,
                 "p50_ms": p50, "p99_ms": p99, "per_alpha": per_alpha,
                 "fp64_path_solves_per_s": fp64_solves,
+                "df_refine_solves_per_s": df_solves,
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3}}
         print(json.dumps(line), flush=True)
