@@ -102,7 +102,9 @@ typedef struct {
                              size used is the largest power of two <= this that the device co-schedules */
     int sweeps;           /* bura_sweep_kind; default BURA_SWEEP_AUTO */
     int refine;           /* bura_refine (mixed precision only); default BURA_REFINE_FP64 */
-    int reserved[2];
+    int tma_stages;       /* depth of the shared-memory ring of the TMA-staged sweeps, 1..4 (a kernel whose
+                             ring does not fit shared memory uses fewer); 0 = auto (2) */
+    int reserved[1];
 } bura_options;
 
 /* Statistics of the last bura_solve*/

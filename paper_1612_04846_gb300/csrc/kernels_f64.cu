@@ -15,20 +15,60 @@ __global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const 
     const int off = threadIdx.x * W;
     double d[W];
     for (int q = 0; q < W; ++q) d[q] = dsh[off + q];
-    LoadPlain<double> ld{v};
     Accum<double> acc;
-    sweep_u<StencilState<double>>(
-        L.N, blockIdx.x, gridDim.x,
-        [&](int P, StencilState<double>& st) {
-            stencil<double, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag);
-            st.bv[0] = __ldg(f + P);
-        },
-        [&](int P, StencilState<double>& st) {
-            double rv[W];
-            for (int q = 0; q < W; ++q) rv[q] = st.bv[0] - fma(-d[q], st.xc[q], st.Ax[q]);
-            vst(r + (size_t)P * Kp + off, rv);
-            acc.add(rv, rv);
-        });
+    if constexpr (!VAR) {
+        // constant coefficients: (A - d_j I) v = (diag - d_j) v_c - wx (v_w + v_e) - wy (v_s + v_n) [- wz (...)],
+        // 6 (2-D) FP64 operations per value instead of 7 (GB300's FP64 rate bounds this kernel)
+        const double diag = 2.0 * (L.wx + L.wy + (DIM == 3 ? L.wz : 0.0));
+        double c0[W];
+        for (int q = 0; q < W; ++q) c0[q] = diag - d[q];
+        struct St { double xc[W], sx[W], sy[W], sz[W], fv; };
+        sweep_u<St>(
+            L.N, blockIdx.x, gridDim.x,
+            [&](int P, St& st) {
+                const Coord c = coord<DIM>(L, P);
+                const size_t base = (size_t)P * Kp + off;
+                const size_t sy = (size_t)L.nx * Kp, sz = (size_t)L.plane * Kp;
+                double a[W], b[W];
+                vld(v + base, st.xc);
+                auto pair = [&](bool lo_in, bool hi_in, size_t step, double (&out)[W]) {
+                    for (int q = 0; q < W; ++q) { a[q] = 0.0; b[q] = 0.0; }
+                    if (lo_in) vld(v + base - step, a);
+                    if (hi_in) vld(v + base + step, b);
+                    for (int q = 0; q < W; ++q) out[q] = a[q] + b[q];
+                };
+                pair(c.i > 0, c.i < L.nx - 1, (size_t)Kp, st.sx);
+                pair(c.j > 0, c.j < L.ny - 1, sy, st.sy);
+                if (DIM == 3) pair(c.l > 0, c.l < L.nz - 1, sz, st.sz);
+                st.fv = __ldg(f + P);
+            },
+            [&](int P, St& st) {
+                double rv[W];
+                for (int q = 0; q < W; ++q) {
+                    double t = c0[q] * st.xc[q];
+                    t = fma(-L.wx, st.sx[q], t);
+                    t = fma(-L.wy, st.sy[q], t);
+                    if (DIM == 3) t = fma(-L.wz, st.sz[q], t);
+                    rv[q] = st.fv - t;
+                }
+                vst(r + (size_t)P * Kp + off, rv);
+                acc.add(rv, rv);
+            });
+    } else {
+        LoadPlain<double> ld{v};
+        sweep_u<StencilState<double>>(
+            L.N, blockIdx.x, gridDim.x,
+            [&](int P, StencilState<double>& st) {
+                stencil<double, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag);
+                st.bv[0] = __ldg(f + P);
+            },
+            [&](int P, StencilState<double>& st) {
+                double rv[W];
+                for (int q = 0; q < W; ++q) rv[q] = st.bv[0] - fma(-d[q], st.xc[q], st.Ax[q]);
+                vst(r + (size_t)P * Kp + off, rv);
+                acc.add(rv, rv);
+            });
+    }
     pdl_trigger();
     reduce_finish<double>(acc, red, Kp);
 }
@@ -98,31 +138,41 @@ void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, 
 // the second stays zero, so the shared reduction machinery applies unchanged.
 __global__ void k_norm2(int N, const double* __restrict__ f, Red red) {
     Accum<double> acc;
-    for (int P = blockIdx.x * blockDim.y + threadIdx.y; P < N; P += gridDim.x * blockDim.y) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    for (int P = blockIdx.x * nthr + tid; P < N; P += gridDim.x * nthr) {
         const double a[2] = {f[P], 0.0};
         acc.add(a, a);
     }
-    reduce_finish<double>(acc, red, 2);
+    // launched as (8, 32) threads: the shared reduction sees 32 "points" of KMAXP = 8 x 2 "systems", so the
+    // block tail sums 16 groups instead of 128; red.out[0..KMAXP-1] holds KMAXP partial sums that the host
+    // adds in a fixed order
+    reduce_finish<double>(acc, red, KMAXP);
 }
 
 void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s) {
     long long b = (N + 255) / 256;
-    const int blocks = (int)(b < nsm * 8 ? (b > 0 ? b : 1) : nsm * 8);
-    k_norm2<<<blocks, dim3(1, 256), 256 * 2 * sizeof(double), s>>>((int)N, f, red);
+    const int blocks = (int)(b < nsm * 2 ? (b > 0 ? b : 1) : nsm * 2);
+    static_assert(KMAXP == 8 * 2, "k_norm2's launch shape gives KMAXP lanes");
+    k_norm2<<<blocks, dim3(8, 32), 256 * 2 * sizeof(double), s>>>((int)N, f, red);
 }
 
 // r32 = f * invscale_j for every active system (the residual of the zero initial guess); x32 = p32 = 0.
 __global__ void k_cast_f(int N, int Kp32, int K, const double* __restrict__ f, const double* __restrict__ invscale,
                          float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32) {
     const int off = threadIdx.x * 4;
-    double is[4];
-    for (int q = 0; q < 4; ++q) is[q] = (off + q < K) ? invscale[off + q] : 0.0;
+    // in the first refinement step every active system has the same scale 1/||f|| (0 for the inactive
+    // ones): one FP64 product and one conversion per point serve all of them
+    double is = 0.0;
+    bool on[4];
+    for (int q = 0; q < K && q < KMAXP; ++q) is = fmax(is, invscale[q]);
+    for (int q = 0; q < 4; ++q) on[q] = (off + q < K) && invscale[off + q] != 0.0;
     for (int tile = blockIdx.x; (long long)tile * blockDim.y < N; tile += gridDim.x) {
         const int P = tile * blockDim.y + threadIdx.y;
         if (P >= N) continue;
-        const double fv = f[P];
+        const float rf = (float)(f[P] * is);
         float rv[4], zv[4];
-        for (int q = 0; q < 4; ++q) { rv[q] = (float)(fv * is[q]); zv[q] = 0.f; }
+        for (int q = 0; q < 4; ++q) { rv[q] = on[q] ? rf : 0.f; zv[q] = 0.f; }
         const size_t base = (size_t)P * Kp32 + off;
         vst(r32 + base, rv);
         vst(x32 + base, zv);

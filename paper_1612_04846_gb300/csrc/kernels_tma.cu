@@ -2,7 +2,7 @@
 //
 // A persistent grid walks tiles of kTX x kTY grid points (tile t = blockIdx.x + k * gridDim.x, a fixed
 // order, so the per-thread partial sums and hence the reductions are deterministic).  For each tile one
-// thread issues tiled TMA loads of the vectors the sweep reads into a kTmaStages-deep ring of
+// thread issues tiled TMA loads of the vectors the sweep reads into a ring of 2 to kTmaMaxStages
 // shared-memory stages, each completed on its own mbarrier; the vectors a stencil reads are loaded with
 // a one-point halo, and TMA's zero fill outside the grid is the homogeneous Dirichlet boundary.  All
 // threads then compute the tile from shared memory and store their results straight to global memory
@@ -40,13 +40,15 @@ static_assert(kTX % 2 == 0 && kTY % 2 == 0, "fine tiles start on even grid coord
 __host__ __device__ constexpr size_t vec_bytes(int pts, int Kp) { return align_up((size_t)pts * Kp * sizeof(float), 1024); }
 
 // Shared-memory bytes of one stage of each kernel kind, and of its unstaged scratch.
-enum TmaKind { TK_CHEB = 0, TK_CHEB_D = 1, TK_PRE2 = 2, TK_SPMV = 3, TK_PRE2R = 4, TK_PROCHEB = 5, TK_NKIND = 6 };
+enum TmaKind { TK_CHEB = 0, TK_CHEB_D = 1, TK_PRE2 = 2, TK_SPMV = 3, TK_PRE2R = 4, TK_PROCHEB = 5, TK_CG = 6,
+               TK_NKIND = 7 };
 __host__ __device__ constexpr size_t stage_bytes(int kind, int Kp) {
     return kind == TK_CHEB ? halo_bytes(Kp) + plain_bytes(Kp)
          : kind == TK_CHEB_D ? halo_bytes(Kp) + 2 * plain_bytes(Kp)
          : kind == TK_PRE2 ? halo_bytes(Kp)
          : kind == TK_SPMV ? 2 * halo_bytes(Kp)
          : kind == TK_PRE2R ? vec_bytes(kRsX * kRsY, Kp)
+         : kind == TK_CG ? 4 * plain_bytes(Kp)
          : halo_bytes(Kp) + vec_bytes(kCpX * kCpY, Kp) + plain_bytes(Kp);
 }
 __host__ __device__ constexpr size_t scratch_bytes(int kind, int Kp) {
@@ -54,43 +56,47 @@ __host__ __device__ constexpr size_t scratch_bytes(int kind, int Kp) {
          : kind == TK_PROCHEB ? halo_bytes(Kp)
          : 0;
 }
-__host__ __device__ constexpr size_t dyn_smem(int kind, int Kp) {
-    return kTmaStages * stage_bytes(kind, Kp) + scratch_bytes(kind, Kp);
+__host__ __device__ constexpr size_t dyn_smem(int kind, int Kp, int S) {
+    return S * stage_bytes(kind, Kp) + scratch_bytes(kind, Kp);
 }
+constexpr size_t kSmemPerSM = 228 * 1024;    // shared memory of an SM
+constexpr size_t kSmemPerCTA = 226 * 1024;   // largest dynamic allocation of one CTA (the 227 KB opt-in limit
+                                             // covers static shared memory too: keep 1 KB for it)
+constexpr size_t kSmemReserved = 1024;       // per CTA, by the system
 
 // The tile pipeline.  issue(stage, tile, bar) is called by thread 0 only; compute(stage, tile) by
 // every thread.  Returns false (after draining the copies in flight and flagging the fault) when a
 // stage did not arrive in time; the caller still runs its epilogue, so every block joins the grid
 // reduction and the reduction tickets stay consistent.
 template <class Issue, class Compute>
-__device__ __forceinline__ bool tile_loop(int ntiles, unsigned char* smem, size_t sbytes, Scal* scal, Issue&& issue,
-                                          Compute&& compute) {
-    __shared__ __align__(8) uint64_t bars[kTmaStages];
+__device__ __forceinline__ bool tile_loop(int ntiles, int S, unsigned char* smem, size_t sbytes, Scal* scal,
+                                          Issue&& issue, Compute&& compute) {
+    __shared__ __align__(8) uint64_t bars[kTmaMaxStages];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nmine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     if (tid == 0) {
-        for (int s = 0; s < kTmaStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
     if (tid == 0)
-        for (int s = 0; s < kTmaStages && s < nmine; ++s)
+        for (int s = 0; s < S && s < nmine; ++s)
             issue(smem + s * sbytes, (int)blockIdx.x + s * (int)gridDim.x, &bars[s]);
     int k = 0;
     bool ok = true;
     for (; k < nmine; ++k) {
-        const int s = k % kTmaStages;
-        const bool got = mbar_wait_bounded(&bars[s], (unsigned)(k / kTmaStages) & 1u);
+        const int s = k % S;
+        const bool got = mbar_wait_bounded(&bars[s], (unsigned)(k / S) & 1u);
         if (__syncthreads_or(!got)) { ok = false; break; }
         compute(smem + s * sbytes, (int)blockIdx.x + k * (int)gridDim.x);
         __syncthreads();  // stage s is free again
-        if (tid == 0 && k + kTmaStages < nmine)
-            issue(smem + s * sbytes, (int)blockIdx.x + (k + kTmaStages) * (int)gridDim.x, &bars[s]);
+        if (tid == 0 && k + S < nmine)
+            issue(smem + s * sbytes, (int)blockIdx.x + (k + S) * (int)gridDim.x, &bars[s]);
     }
     if (!ok) {
-        // tiles k .. k+kTmaStages-1 may still have copies in flight into this CTA's shared memory
-        for (int j = k; j < nmine && j < k + kTmaStages; ++j)
-            (void)mbar_wait_bounded(&bars[j % kTmaStages], (unsigned)(j / kTmaStages) & 1u);
+        // tiles k .. k+S-1 may still have copies in flight into this CTA's shared memory
+        for (int j = k; j < nmine && j < k + S; ++j)
+            (void)mbar_wait_bounded(&bars[j % S], (unsigned)(j / S) & 1u);
         if (tid == 0) atomicExch(&scal->fault, 1);
         __syncthreads();
     }
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     Accum<float> acc;
     const bool dot = red.op != RED_NONE;
     tile_loop(
-        g.ntiles, smem, sb, red.scal,
+        g.ntiles, g.stages, smem, sb, red.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
             tile_origin(g, t, x0, y0);
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     }
     const unsigned tx_bytes = (unsigned)(kHaloPts * Kp * 4);
     tile_loop(
-        g.ntiles, smem, sb, none.scal,
+        g.ntiles, g.stages, smem, sb, none.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
             tile_origin(g, t, x0, y0);
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     const unsigned tx_bytes = (unsigned)(2 * kHaloPts * Kp * 4);
     Accum<float> acc;
     tile_loop(
-        g.ntiles, smem, sb, red.scal,
+        g.ntiles, g.stages, smem, sb, red.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
             tile_origin(g, t, x0, y0);
@@ -347,8 +353,8 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     unsigned char* smem = aligned_ring(smem_raw);
     const int Kp = C * 4;
     const size_t sb = stage_bytes(TK_PRE2R, Kp);
-    float* X2s = reinterpret_cast<float*>(smem + kTmaStages * sb);
-    float* Rs = reinterpret_cast<float*>(smem + kTmaStages * sb + vec_bytes(kE1X * kE1Y, Kp));
+    float* X2s = reinterpret_cast<float*>(smem + g.stages * sb);
+    float* Rs = reinterpret_cast<float*>(smem + g.stages * sb + vec_bytes(kE1X * kE1Y, Kp));
     const int off = threadIdx.x * 4;
     float c20[4], c1[4], c2[4], d[4];
     for (int v = 0; v < 4; ++v) {
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     const float diag = g.wx + g.wx + g.wy + g.wy;
     const unsigned tx_bytes = (unsigned)(kRsX * kRsY * Kp * 4);
     tile_loop(
-        g.nctiles, smem, sb, none.scal,
+        g.nctiles, g.stages, smem, sb, none.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             const int cy = t / g.ncx, cx = t - cy * g.ncx;
             mbar_expect_tx(bar, tx_bytes);
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     unsigned char* smem = aligned_ring(smem_raw);
     const int Kp = C * 4;
     const size_t sb = stage_bytes(TK_PROCHEB, Kp);
-    float* Xn = reinterpret_cast<float*>(smem + kTmaStages * sb);
+    float* Xn = reinterpret_cast<float*>(smem + g.stages * sb);
     const int off = threadIdx.x * 4;
     float c2[4], d[4];
     for (int v = 0; v < 4; ++v) {
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     }
     const unsigned tx_bytes = (unsigned)((kHaloPts + kCpX * kCpY + kTilePts) * Kp * 4);
     tile_loop(
-        g.ntiles, smem, sb, none.scal,
+        g.ntiles, g.stages, smem, sb, none.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
             tile_origin(g, t, x0, y0);
@@ -538,27 +544,88 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
     pdl_trigger();
 }
 
+// CG vector update from TMA-staged tiles: x += alpha p, r -= alpha q and r.r per system (pointwise, no
+// halo).  The grid-stride kernel is limited to 8 CTAs of 4 warps per SM by its registers; here the bytes
+// in flight are the ring's stages, whatever the occupancy.
+template <int C>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+    k_cg_update_tma(const __grid_constant__ TmaMaps5 mp, TmaGeo g, float* __restrict__ x, float* __restrict__ r,
+                    Red red) {
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* smem = aligned_ring(smem_raw);
+    const int Kp = C * 4;
+    const size_t sb = stage_bytes(TK_CG, Kp);
+    const size_t pb = plain_bytes(Kp);
+    const int off = threadIdx.x * 4;
+    // the direction k_spmv_tma just wrote (its pnew), selected by the same parity
+    const CUtensorMap* mp_dir = red.scal->parity ? &mp.m[2] : &mp.m[3];
+    float a[4];
+    for (int v = 0; v < 4; ++v) a[v] = red.scal->alphaf[off + v];
+    const unsigned tx_bytes = (unsigned)(4 * kTilePts * Kp * 4);
+    Accum<float> acc;
+    tile_loop(
+        g.ntiles, g.stages, smem, sb, red.scal,
+        [&](unsigned char* st, int t, uint64_t* bar) {
+            int x0, y0;
+            tile_origin(g, t, x0, y0);
+            mbar_expect_tx(bar, tx_bytes);
+            tma_load_pt(st, &mp.m[0], g, x0, y0, bar);
+            tma_load_pt(st + pb, &mp.m[1], g, x0, y0, bar);
+            tma_load_pt(st + 2 * pb, mp_dir, g, x0, y0, bar);
+            tma_load_pt(st + 3 * pb, &mp.m[4], g, x0, y0, bar);
+        },
+        [&](unsigned char* st, int t) {
+            int x0, y0;
+            tile_origin(g, t, x0, y0);
+            const float* X = reinterpret_cast<const float*>(st);
+            const float* R = reinterpret_cast<const float*>(st + pb);
+            const float* P = reinterpret_cast<const float*>(st + 2 * pb);
+            const float* Q = reinterpret_cast<const float*>(st + 3 * pb);
+            for (int p = threadIdx.y; p < kTilePts; p += blockDim.y) {
+                const int ly = p / kTX, lx = p - ly * kTX;
+                const int gx = x0 + lx, gy = y0 + ly;
+                if (gx >= g.nx || gy >= g.ny) continue;
+                const int i = p * Kp + off;
+                float xv[4], rv[4], pv[4], qv[4];
+                ld4(X + i, xv);
+                ld4(R + i, rv);
+                ld4(P + i, pv);
+                ld4(Q + i, qv);
+                for (int v = 0; v < 4; ++v) {
+                    xv[v] = fmaf(a[v], pv[v], xv[v]);
+                    rv[v] = fmaf(-a[v], qv[v], rv[v]);
+                }
+                const size_t gidx = ((size_t)gy * g.nx + gx) * Kp + off;
+                st4(x + gidx, xv);
+                st4(r + gidx, rv);
+                acc.add(rv, rv);
+            }
+        });
+    pdl_trigger();
+    reduce_finish<float>(acc, red, Kp);
+}
+
 template <int C>
 cudaError_t prepare_c() {
-    const int Kp = 4 * C;
+    // every TMA kernel may take up to a whole SM's worth of ring (the launch asks for what it uses)
+    const int mx = (int)kSmemPerCTA;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_cheb_tma<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(dyn_smem(TK_CHEB, Kp) + kRingSlack))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_cheb_tma<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_cheb_tma<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(dyn_smem(TK_CHEB_D, Kp) + kRingSlack))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_cheb_tma<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_pre2_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(dyn_smem(TK_PRE2, Kp) + kRingSlack))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_pre2_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_pre2_restrict_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(dyn_smem(TK_PRE2R, Kp) + kRingSlack))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_pre2_restrict_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+        cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(k_prolong_cheb_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(dyn_smem(TK_PROCHEB, Kp) + kRingSlack))) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_prolong_cheb_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+        cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_spmv_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(dyn_smem(TK_SPMV, Kp) + kRingSlack));
+    if ((e = cudaFuncSetAttribute(k_cg_update_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_spmv_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 template <class K, class... Args>
@@ -599,6 +666,7 @@ TmaGeo tma_geo(const Lev& L, const Lev* Lc, int Kp) {
     g.wx = (float)L.wx;
     g.wy = (float)L.wy;
     g.flat = tma_flat(Kp) ? 1 : 0;
+    g.stages = kTmaStages;
     return g;
 }
 
@@ -646,12 +714,34 @@ cudaError_t tma_prepare(int Kp) {
     }
 }
 
-// Persistent grid: as many CTAs per SM as the stages of this kind fit in shared memory (at most 2).
-int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind) {
-    const size_t smem = dyn_smem(kind, Kp) + kRingSlack + 1024;  // + static and reserved
-    const int per_sm = smem * 2 <= 227 * 1024 ? 2 : 1;
+// Ring depth of a launch: the requested depth, reduced until the ring fits one CTA (at least 1).
+int ring_stages(const TmaGeo& g, int kind) {
+    int S = g.stages < 1 ? kTmaStages : (g.stages > kTmaMaxStages ? kTmaMaxStages : g.stages);
+    while (S > 1 && dyn_smem(kind, g.Kp, S) + kRingSlack > kSmemPerCTA) --S;
+    return S;
+}
+
+// Persistent grid: as many CTAs per SM as their rings fit in shared memory (at most 2).
+int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind, int S) {
+    const size_t smem = dyn_smem(kind, Kp, S) + kRingSlack + kSmemReserved + 64;  // + static
+    const int per_sm = 2 * smem <= kSmemPerSM ? 2 : 1;
     const int nt = kind == TK_PRE2R ? g.nctiles : g.ntiles;
     return nt < nsm * per_sm ? nt : nsm * per_sm;
+}
+
+// Launch geometry of one kind: g with its ring depth, CTAs, dynamic shared memory.
+struct Shape {
+    TmaGeo g;
+    int blocks;
+    size_t smem;
+};
+Shape shape_of(const TmaGeo& g0, int nsm, int kind) {
+    Shape sh;
+    sh.g = g0;
+    sh.g.stages = ring_stages(g0, kind);
+    sh.blocks = tma_blocks(sh.g, g0.Kp, nsm, kind, sh.g.stages);
+    sh.smem = dyn_smem(kind, g0.Kp, sh.g.stages) + kRingSlack;
+    return sh;
 }
 
 #define BURA_TMA_C(Kp, CALL)            \
@@ -669,29 +759,30 @@ cudaError_t tma_cheb_step(const TmaGeo& g, int nsm, const CUtensorMap& mx, const
     mp.m[0] = mx;
     mp.m[1] = md ? *md : mx;
     mp.m[2] = mb;
-    const int kind = md ? TK_CHEB_D : TK_CHEB;
-    const int nb = tma_blocks(g, g.Kp, nsm, kind);
-    const size_t smem = dyn_smem(kind, g.Kp) + kRingSlack;
-    if (md) BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, true>, nb, C, smem, s, mp, g, xout, dout, cs, dsh, red))
-    BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, false>, nb, C, smem, s, mp, g, xout, dout, cs, dsh, red))
+    const Shape sh = shape_of(g, nsm, md ? TK_CHEB_D : TK_CHEB);
+    if (md)
+        BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, true>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
+                                            red))
+    BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, false>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
+                                        red))
 }
 
 cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float* xout, float* dout, ChebStepT<float> cs0,
                      ChebStepT<float> cs1, const float* dsh, const Red& none, cudaStream_t s) {
     TmaMaps3 mp;
     mp.m[0] = mp.m[1] = mp.m[2] = mb_halo;
-    const int nb = tma_blocks(g, g.Kp, nsm, TK_PRE2);
-    const size_t smem = dyn_smem(TK_PRE2, g.Kp) + kRingSlack;
-    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_tma<C>, nb, C, smem, s, mp, g, xout, dout, cs0, cs1, dsh, none))
+    const Shape sh = shape_of(g, nsm, TK_PRE2);
+    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs0, cs1, dsh,
+                                        none))
 }
 
 cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rsrc, float* x2out, float* bc,
                               ChebStepT<float> cs0, ChebStepT<float> cs1, const float* dsh, const Red& none, cudaStream_t s) {
     TmaMaps3 mp;
     mp.m[0] = mp.m[1] = mp.m[2] = mb_rsrc;
-    const int nb = tma_blocks(g, g.Kp, nsm, TK_PRE2R);
-    const size_t smem = dyn_smem(TK_PRE2R, g.Kp) + kRingSlack;
-    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_restrict_tma<C>, nb, C, smem, s, mp, g, x2out, bc, cs0, cs1, dsh, none))
+    const Shape sh = shape_of(g, nsm, TK_PRE2R);
+    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_restrict_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, x2out, bc, cs0,
+                                        cs1, dsh, none))
 }
 
 cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo, const CUtensorMap& mec_cpro,
@@ -701,9 +792,9 @@ cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_hal
     mp.m[0] = mx_halo;
     mp.m[1] = mec_cpro;
     mp.m[2] = mb;
-    const int nb = tma_blocks(g, g.Kp, nsm, TK_PROCHEB);
-    const size_t smem = dyn_smem(TK_PROCHEB, g.Kp) + kRingSlack;
-    BURA_TMA_C(g.Kp, return launch_tile(k_prolong_cheb_tma<C>, nb, C, smem, s, mp, g, xout, dout, cs, dsh, none))
+    const Shape sh = shape_of(g, nsm, TK_PROCHEB);
+    BURA_TMA_C(g.Kp, return launch_tile(k_prolong_cheb_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
+                                        none))
 }
 
 cudaError_t tma_spmv_p(const TmaGeo& g, int nsm, const CUtensorMap& mz, const CUtensorMap& mpa,
@@ -712,9 +803,25 @@ cudaError_t tma_spmv_p(const TmaGeo& g, int nsm, const CUtensorMap& mz, const CU
     mp.m[0] = mz;
     mp.m[1] = mpa;
     mp.m[2] = mpb;
-    const int nb = tma_blocks(g, g.Kp, nsm, TK_SPMV);
-    const size_t smem = dyn_smem(TK_SPMV, g.Kp) + kRingSlack;
-    BURA_TMA_C(g.Kp, return launch_tile(k_spmv_tma<C>, nb, C, smem, s, mp, g, pa, pb, q, red))
+    const Shape sh = shape_of(g, nsm, TK_SPMV);
+    BURA_TMA_C(g.Kp, return launch_tile(k_spmv_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, pa, pb, q, red))
+}
+
+bool tma_cg_fits(int Kp) { return dyn_smem(TK_CG, Kp, 2) + kRingSlack <= kSmemPerCTA; }
+
+cudaError_t tma_cg_update(const TmaGeo& g, int nsm, const CUtensorMap& mx, const CUtensorMap& mr,
+                          const CUtensorMap& mpa, const CUtensorMap& mpb, const CUtensorMap& mq, float* x, float* r,
+                          const Red& red, cudaStream_t s) {
+    TmaMaps5 mp;
+    mp.m[0] = mx;
+    mp.m[1] = mr;
+    mp.m[2] = mpa;
+    mp.m[3] = mpb;
+    mp.m[4] = mq;
+    TmaGeo g1 = g;
+    if (g1.stages < 3) g1.stages = 3;  // pointwise: the deepest ring that fits (1 CTA per SM)
+    const Shape sh = shape_of(g1, nsm, TK_CG);
+    BURA_TMA_C(g.Kp, return launch_tile(k_cg_update_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, x, r, red))
 }
 
 }  // namespace bura

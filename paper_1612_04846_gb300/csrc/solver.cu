@@ -445,7 +445,8 @@ int build_tma(bura_plan* p, Work<T>& w) {
     for (int l = 0; l < nlev; ++l) {
         if (w.lc >= 0 && l >= w.lc) break;
         const bool has_coarse = l + 1 < nlev;
-        const TmaGeo g = tma_geo(w.L[l], has_coarse ? &w.L[l + 1] : nullptr, w.Kp);
+        TmaGeo g = tma_geo(w.L[l], has_coarse ? &w.L[l + 1] : nullptr, w.Kp);
+        if (p->opt.tma_stages > 0) g.stages = p->opt.tma_stages;
         // every grid level: even with fewer tiles than SMs the fused 3-launch V-cycle step beats the
         // 5 grid launches of a small level (measured on GB300: 255^2 ... 63^2 levels of a 1023^2 solve)
         auto& t = w.tma[l];
@@ -457,6 +458,11 @@ int build_tma(bura_plan* p, Work<T>& w) {
         if (l == 0) {
             want.push_back({TB_HALO, w.pa, 0});
             want.push_back({TB_HALO, w.pb, 0});
+            // the CG update's pointwise tiles
+            want.push_back({TB_PLAIN, w.x, 0});
+            want.push_back({TB_PLAIN, w.pa, 0});
+            want.push_back({TB_PLAIN, w.pb, 0});
+            want.push_back({TB_PLAIN, w.q, 0});
         }
         if (has_coarse) {  // the fused transfers: b with a two-point halo, coarse results for prolongation
             want.push_back({TB_RSRC, bl, l});
@@ -884,8 +890,20 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
         else
             Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s);
     });
-    traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s,
-           [&] { Ops<T>::cg_update(g, L.N, w.x, w.r, w.pa, w.pb, w.q, rconv, s); });
+    traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s, [&] {
+        const CUtensorMap* mx = tl.on ? tl.find(TB_PLAIN, w.x) : nullptr;
+        const CUtensorMap* mr = tl.on ? tl.find(TB_PLAIN, w.r) : nullptr;
+        const CUtensorMap* mpa = tl.on ? tl.find(TB_PLAIN, w.pa) : nullptr;
+        const CUtensorMap* mpb = tl.on ? tl.find(TB_PLAIN, w.pb) : nullptr;
+        const CUtensorMap* mq = tl.on ? tl.find(TB_PLAIN, w.q) : nullptr;
+        // the TMA-staged CG update (one CTA per SM, a 3-stage ring) measured no faster than the grid
+        // kernel on GB300 (42.6 vs 41.3 us at 1023^2, k = 7); it is used only with a deeper ring requested
+        if (mx && mr && mpa && mpb && mq && tma_cg_fits(w.Kp) && p->opt.tma_stages >= 3)
+            (void)tma_cg_update(tl.geo, p->nsm, *mx, *mr, *mpa, *mpb, *mq, reinterpret_cast<float*>(w.x),
+                                reinterpret_cast<float*>(w.r), rconv, s);
+        else
+            Ops<T>::cg_update(g, L.N, w.x, w.r, w.pa, w.pb, w.q, rconv, s);
+    });
     CKL();
     return BURA_OK;
 }
@@ -1001,9 +1019,10 @@ int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
     traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
     CKL();
-    CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const double fnorm2 = p->hbuf[0];
+    double fnorm2 = 0.0;  // k_norm2 leaves KMAXP partial sums
+    for (int i = 0; i < KMAXP; ++i) fnorm2 += p->hbuf[i];
     double thr[KMAXP] = {0};
     int act[KMAXP] = {0};
     thresholds(p, tol, fnorm2, thr);
@@ -1033,9 +1052,10 @@ int solve_mixed_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) 
     // the residual of the zero initial guess is f itself: only its norm is needed
     traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
     CKL();
-    CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const double fnorm2 = p->hbuf[0];
+    double fnorm2 = 0.0;  // k_norm2 leaves KMAXP partial sums
+    for (int i = 0; i < KMAXP; ++i) fnorm2 += p->hbuf[i];
     double thr64[KMAXP] = {0};
     double rr[KMAXP] = {0};
     thresholds(p, tol, fnorm2, thr64);
@@ -1128,9 +1148,10 @@ int solve_mixed_df(bura_plan* p, const double* f, double tol, cudaStream_t s) {
     // the residual of the zero initial guess is f itself: only its norm is needed
     traced(p, K_NORM, false, true, (double)N * 8, s, [&] { launch_norm2(N, f, store, p->nsm, s); });
     CKL();
-    CK(cudaMemcpyAsync(p->hbuf, p->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p->hbuf, p->red_out, KMAXP * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    const double fnorm2 = p->hbuf[0];
+    double fnorm2 = 0.0;  // k_norm2 leaves KMAXP partial sums
+    for (int i = 0; i < KMAXP; ++i) fnorm2 += p->hbuf[i];
     if (!std::isfinite(fnorm2)) return BURA_ENOTSPD;
     // The inner FP32 solves work on sf * residual with sf a power of two that brings f's typical entry
     // near 1 (exact scaling, no FP32 range trouble); their thresholds are in the same units.
@@ -1323,7 +1344,7 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
         !(o.cluster_size == 0 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8 ||
           o.cluster_size == 16) ||
         o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
-        o.refine > BURA_REFINE_DF)
+        o.refine > BURA_REFINE_DF || o.tma_stages < 0 || o.tma_stages > 4)
         return BURA_EINVAL;
 
     bura_plan* p = new (std::nothrow) bura_plan();

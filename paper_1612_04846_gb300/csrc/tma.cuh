@@ -39,7 +39,8 @@ inline void tma_box_dims(int kind, int* bx, int* by) {
     }
 }
 constexpr int kTmaThreads = 256;
-constexpr int kTmaStages = 2;
+constexpr int kTmaStages = 2;     // default depth of the shared-memory ring of a CTA
+constexpr int kTmaMaxStages = 4;  // deepest ring (bura_options.tma_stages)
 constexpr long long kTmaWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
 
 #ifdef __CUDACC__
@@ -116,6 +117,8 @@ struct TmaGeo {
     int nctiles;
     int flat;          // 1: 2-D maps over 8-byte elements (a tile row is one contiguous box row),
                        // 0: 3-D maps (Kp floats innermost), used when a box row would exceed 256 elements
+    int stages;        // requested depth of the shared-memory ring (2..kTmaMaxStages); each launch uses the
+                       // deepest ring up to this that fits its kind's shared memory
 };
 
 #ifdef __CUDACC__
@@ -132,6 +135,10 @@ struct TmaMaps3 {
     CUtensorMap m[3];
 };
 
+struct TmaMaps5 {
+    CUtensorMap m[5];
+};
+
 // Host side.  Every launcher returns the launch status; the kernels take the fault flag from red.scal.
 bool tma_supported(int Kp);
 TmaGeo tma_geo(const Lev& L, const Lev* Lc, int Kp);
@@ -140,7 +147,6 @@ bool tma_flat(int Kp);
 // Tensor map of an [ny][nx][Kp] float vector with a box of kind TmaBox.
 cudaError_t tma_encode(CUtensorMap* m, const float* base, int Kp, int nx, int ny, int box);
 cudaError_t tma_prepare(int Kp);
-int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind);
 cudaError_t tma_cheb_step(const TmaGeo& g, int nsm, const CUtensorMap& mx, const CUtensorMap* md, const CUtensorMap& mb,
                           float* xout, float* dout, ChebStepT<float> cs, const float* dsh, const Red& red, cudaStream_t s);
 cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float* xout, float* dout, ChebStepT<float> cs0,
@@ -154,6 +160,13 @@ cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rs
 cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo, const CUtensorMap& mec_cpro,
                              const CUtensorMap& mb, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
                              const Red& none, cudaStream_t s);
+// CG update x += alpha p, r -= alpha q with r.r (RED_CONV) from TMA-staged tiles of x, r, p, q (pointwise);
+// the direction is pa or pb by the Scal parity, as in the grid kernel.  False from tma_cg_fits when the
+// ring of at least two stages does not fit.
+bool tma_cg_fits(int Kp);
+cudaError_t tma_cg_update(const TmaGeo& g, int nsm, const CUtensorMap& mx, const CUtensorMap& mr,
+                          const CUtensorMap& mpa, const CUtensorMap& mpb, const CUtensorMap& mq, float* x, float* r,
+                          const Red& red, cudaStream_t s);
 cudaError_t tma_spmv_p(const TmaGeo& g, int nsm, const CUtensorMap& mz, const CUtensorMap& mpa,
                        const CUtensorMap& mpb, float* pa, float* pb, float* q, const Red& red, cudaStream_t s);
 
