@@ -71,9 +71,12 @@ struct ChebStepT {
 
 enum ReduceOp { RED_NONE = 0, RED_ALPHA = 1, RED_CONV = 2, RED_BETA = 3, RED_STORE = 4 };
 
-// Grid reductions are two-level: blocks in groups of kRedGroup; the last block of a group to finish
-// sums the group's block partials, and the last group to finish sums the group partials.
+// Grid reductions: every block writes its partial sums; on grids of up to kRedOneLevel blocks the last
+// block to finish sums all block partials in block order.  Larger grids use two levels: blocks in groups
+// of kRedGroup, the last block of a group sums the group's partials, and the last group to finish sums
+// the group partials in group order.  Either way the order is fixed: results are deterministic.
 constexpr int kRedGroup = 16;
+constexpr int kRedOneLevel = 640;
 struct Red {
     double* partial;          // [gridDim.x * Kp] block partials, then [groups * Kp] group partials
     unsigned int* tickets;    // [max groups + 1] counters, zero between reductions

@@ -315,9 +315,12 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     if (tid < Kp * G) sm[tid] = part;
     __syncthreads();
     const int nblk = (int)gridDim.x;
-    const int group = (int)blockIdx.x / kRedGroup;
-    const int ngroups = (nblk + kRedGroup - 1) / kRedGroup;
-    const int gsize = min(kRedGroup, nblk - group * kRedGroup);
+    // one level (the last block sums every block partial) for grids up to kRedOneLevel blocks, such as
+    // the persistent TMA kernels; two levels (groups of kRedGroup blocks) for the grid-stride kernels
+    const bool one_level = nblk <= kRedOneLevel;
+    const int group = one_level ? 0 : (int)blockIdx.x / kRedGroup;
+    const int ngroups = one_level ? 1 : (nblk + kRedGroup - 1) / kRedGroup;
+    const int gsize = one_level ? nblk : min(kRedGroup, nblk - group * kRedGroup);
     double* part2 = red.partial + (size_t)nblk * Kp;
     if (tid < Kp) {
         double tot = 0.0;
@@ -326,7 +329,7 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
         __threadfence();  // only the writers of the partials need their stores visible before the ticket
     }
     __syncthreads();
-    // level 1: the last block of the group sums the group's block partials in block order
+    // level 1: the last block of the group (of the grid, with one level) sums its block partials
     if (tid == 0) {
         const unsigned t = atomicAdd(&red.tickets[group], 1u);
         am_last = (t == (unsigned)gsize - 1);
@@ -334,38 +337,46 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    if (tid < Kp) {
-        const double* src = red.partial + (size_t)group * kRedGroup * Kp + tid;
-        double v[kRedGroup];
+    // the partials to sum in the final step, in a fixed order: the block partials (one level) or the
+    // group partials (two levels)
+    const double* fin = red.partial;
+    int nfin = nblk;
+    if (!one_level) {
+        if (tid < Kp) {
+            const double* src = red.partial + (size_t)group * kRedGroup * Kp + tid;
+            double v[kRedGroup];
 #pragma unroll
-        for (int b = 0; b < kRedGroup; ++b) v[b] = b < gsize ? __ldcg(src + (size_t)b * Kp) : 0.0;
-        double tot = 0.0;
+            for (int b = 0; b < kRedGroup; ++b) v[b] = b < gsize ? __ldcg(src + (size_t)b * Kp) : 0.0;
+            double tot = 0.0;
 #pragma unroll
-        for (int b = 0; b < kRedGroup; ++b) tot += v[b];
-        part2[(size_t)group * Kp + tid] = tot;
+            for (int b = 0; b < kRedGroup; ++b) tot += v[b];
+            part2[(size_t)group * Kp + tid] = tot;
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            red.tickets[group] = 0u;
+            const unsigned t = atomicAdd(&red.tickets[ngroups], 1u);
+            am_last = (t == (unsigned)ngroups - 1);
+        }
+        __syncthreads();
+        if (!am_last) return;
         __threadfence();
+        fin = part2;
+        nfin = ngroups;
     }
-    __syncthreads();
-    if (tid == 0) {
-        red.tickets[group] = 0u;
-        const unsigned t = atomicAdd(&red.tickets[ngroups], 1u);
-        am_last = (t == (unsigned)ngroups - 1);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    // level 2: the last group sums the group partials in group order; thread t adds system t % Kp
+    // final step: thread (s, g) adds partials g, g + G, ... of system s, then the G sums in order
     part = 0.0;
     if (tid < Kp * G) {
         const int s = tid % Kp, g = tid / Kp;
         int b = g;
-        for (; b + G < ngroups; b += 2 * G) {
-            const double v0 = __ldcg(part2 + (size_t)b * Kp + s);
-            const double v1 = __ldcg(part2 + (size_t)(b + G) * Kp + s);
+        for (; b + G < nfin; b += 2 * G) {
+            const double v0 = __ldcg(fin + (size_t)b * Kp + s);
+            const double v1 = __ldcg(fin + (size_t)(b + G) * Kp + s);
             part += v0;
             part += v1;
         }
-        for (; b < ngroups; b += G) part += __ldcg(part2 + (size_t)b * Kp + s);
+        for (; b < nfin; b += G) part += __ldcg(fin + (size_t)b * Kp + s);
     }
     __syncthreads();
     if (tid < Kp * G) sm[tid] = part;
@@ -377,7 +388,7 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     }
     __syncthreads();
     if (tid == 0) {
-        red.tickets[ngroups] = 0u;
+        red.tickets[one_level ? 0 : ngroups] = 0u;
         if (red.op == RED_CONV) {
             Scal* S = red.scal;
             int na = 0;

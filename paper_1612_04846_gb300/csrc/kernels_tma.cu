@@ -150,7 +150,7 @@ __device__ __forceinline__ void stencil_tile(const TmaGeo& g, int hidx, const Va
 // One Chebyshev step, xout = xin + dnew with dnew = c1 din + c2 Dinv (b - (A - dI) xin); stages hold
 // xin (halo), [din,] b.  With a reduction, also sum b . xout per system (the CG r.z).
 template <int C, bool HAS_DIN>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_cheb_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout, float* __restrict__ dout,
                ChebStepT<float> cs, const float* __restrict__ dsh, Red red) {
     pdl_wait();
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 // The first two Chebyshev steps from a zero guess: x1 = c2_0 Dinv b at the stencil points (d_1 = x1),
 // then the second step; the stage holds b with its halo.
 template <int C>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_pre2_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout, float* __restrict__ dout,
                ChebStepT<float> cs0, ChebStepT<float> cs1, const float* __restrict__ dsh, Red none) {
     pdl_wait();
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 // p_new, and p_new . q per system; the stages hold z and p_old with their halos.  The direction
 // buffers alternate by the parity in the Scal record, as in the grid kernel.
 template <int C>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_spmv_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* pa, float* pb, float* __restrict__ q, Red red) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 // one-point halo (recomputed by neighbouring tiles, bit for bit the same), the residual on the fine
 // points the coarse tile's full weighting reads, and the weighted sums in the grid kernel's order.
 template <int C>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_pre2_restrict_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ x2out,
                         float* __restrict__ bc, ChebStepT<float> cs0, ChebStepT<float> cs1, const float* __restrict__ dsh, Red none) {
     pdl_wait();
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 // adds +0 where the grid kernel skips a zero weight), then the Chebyshev step without a previous
 // direction.  xin itself is never stored: only xout and dout are.
 template <int C>
-__global__ void __launch_bounds__(kTmaThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_prolong_cheb_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout,
                        float* __restrict__ dout, ChebStepT<float> cs, const float* __restrict__ dsh, Red none) {
     pdl_wait();
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(kTmaThreads, 2)
 // halo).  The grid-stride kernel is limited to 8 CTAs of 4 warps per SM by its registers; here the bytes
 // in flight are the ring's stages, whatever the occupancy.
 template <int C>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_cg_update_tma(const __grid_constant__ TmaMaps5 mp, TmaGeo g, float* __restrict__ x, float* __restrict__ r,
                     Red red) {
     pdl_wait();
@@ -629,10 +629,10 @@ cudaError_t prepare_c() {
 }
 
 template <class K, class... Args>
-cudaError_t launch_tile(K kernel, int blocks, int C, size_t smem, cudaStream_t s, Args... args) {
+cudaError_t launch_tile(K kernel, int blocks, int threads, int C, size_t smem, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(C, kTmaThreads / C);
+    cfg.blockDim = dim3(C, threads / C);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -721,10 +721,11 @@ int ring_stages(const TmaGeo& g, int kind) {
     return S;
 }
 
-// Persistent grid: as many CTAs per SM as their rings fit in shared memory (at most 2).
+// Persistent grid: as many CTAs per SM as their rings fit in shared memory (at most kTmaMaxCtasPerSM).
 int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind, int S) {
     const size_t smem = dyn_smem(kind, Kp, S) + kRingSlack + kSmemReserved + 64;  // + static
-    const int per_sm = 2 * smem <= kSmemPerSM ? 2 : 1;
+    int per_sm = (int)(kSmemPerSM / smem);
+    per_sm = per_sm < 1 ? 1 : (per_sm > kTmaMaxCtasPerSM ? kTmaMaxCtasPerSM : per_sm);
     const int nt = kind == TK_PRE2R ? g.nctiles : g.ntiles;
     return nt < nsm * per_sm ? nt : nsm * per_sm;
 }
@@ -733,6 +734,7 @@ int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind, int S) {
 struct Shape {
     TmaGeo g;
     int blocks;
+    int threads;
     size_t smem;
 };
 Shape shape_of(const TmaGeo& g0, int nsm, int kind) {
@@ -740,6 +742,7 @@ Shape shape_of(const TmaGeo& g0, int nsm, int kind) {
     sh.g = g0;
     sh.g.stages = ring_stages(g0, kind);
     sh.blocks = tma_blocks(sh.g, g0.Kp, nsm, kind, sh.g.stages);
+    sh.threads = kTmaThreads;
     sh.smem = dyn_smem(kind, g0.Kp, sh.g.stages) + kRingSlack;
     return sh;
 }
@@ -761,9 +764,9 @@ cudaError_t tma_cheb_step(const TmaGeo& g, int nsm, const CUtensorMap& mx, const
     mp.m[2] = mb;
     const Shape sh = shape_of(g, nsm, md ? TK_CHEB_D : TK_CHEB);
     if (md)
-        BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, true>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
+        BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, true>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
                                             red))
-    BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, false>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
+    BURA_TMA_C(g.Kp, return launch_tile(k_cheb_tma<C, false>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
                                         red))
 }
 
@@ -772,7 +775,7 @@ cudaError_t tma_pre2(const TmaGeo& g, int nsm, const CUtensorMap& mb_halo, float
     TmaMaps3 mp;
     mp.m[0] = mp.m[1] = mp.m[2] = mb_halo;
     const Shape sh = shape_of(g, nsm, TK_PRE2);
-    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs0, cs1, dsh,
+    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, xout, dout, cs0, cs1, dsh,
                                         none))
 }
 
@@ -781,7 +784,7 @@ cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rs
     TmaMaps3 mp;
     mp.m[0] = mp.m[1] = mp.m[2] = mb_rsrc;
     const Shape sh = shape_of(g, nsm, TK_PRE2R);
-    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_restrict_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, x2out, bc, cs0,
+    BURA_TMA_C(g.Kp, return launch_tile(k_pre2_restrict_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, x2out, bc, cs0,
                                         cs1, dsh, none))
 }
 
@@ -793,7 +796,7 @@ cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_hal
     mp.m[1] = mec_cpro;
     mp.m[2] = mb;
     const Shape sh = shape_of(g, nsm, TK_PROCHEB);
-    BURA_TMA_C(g.Kp, return launch_tile(k_prolong_cheb_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
+    BURA_TMA_C(g.Kp, return launch_tile(k_prolong_cheb_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
                                         none))
 }
 
@@ -804,7 +807,7 @@ cudaError_t tma_spmv_p(const TmaGeo& g, int nsm, const CUtensorMap& mz, const CU
     mp.m[1] = mpa;
     mp.m[2] = mpb;
     const Shape sh = shape_of(g, nsm, TK_SPMV);
-    BURA_TMA_C(g.Kp, return launch_tile(k_spmv_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, pa, pb, q, red))
+    BURA_TMA_C(g.Kp, return launch_tile(k_spmv_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, pa, pb, q, red))
 }
 
 bool tma_cg_fits(int Kp) { return dyn_smem(TK_CG, Kp, 2) + kRingSlack <= kSmemPerCTA; }
@@ -821,7 +824,7 @@ cudaError_t tma_cg_update(const TmaGeo& g, int nsm, const CUtensorMap& mx, const
     TmaGeo g1 = g;
     if (g1.stages < 3) g1.stages = 3;  // pointwise: the deepest ring that fits (1 CTA per SM)
     const Shape sh = shape_of(g1, nsm, TK_CG);
-    BURA_TMA_C(g.Kp, return launch_tile(k_cg_update_tma<C>, sh.blocks, C, sh.smem, s, mp, sh.g, x, r, red))
+    BURA_TMA_C(g.Kp, return launch_tile(k_cg_update_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, x, r, red))
 }
 
 }  // namespace bura

@@ -16,7 +16,7 @@ namespace bura {
 // Tile of grid points staged per TMA load (x extent, y extent); the stencil input is loaded with a
 // one-point halo on every side, (kTX + 2) x (kTY + 2) points.
 constexpr int kTX = 32;
-constexpr int kTY = 16;
+constexpr int kTY = 8;
 // Coarse tile of the fused smoothing + restriction kernel: kTXc x kTYc coarse points, i.e. the fine
 // region of one fine tile; its right-hand side is loaded with a two-point halo (2 kTXc + 5 points).
 constexpr int kTXc = kTX / 2;
@@ -38,7 +38,8 @@ inline void tma_box_dims(int kind, int* bx, int* by) {
         default: *bx = kTX / 2 + 2; *by = kTY / 2 + 2; break;
     }
 }
-constexpr int kTmaThreads = 256;
+constexpr int kTmaThreads = 256;     // threads per CTA
+constexpr int kTmaMaxCtasPerSM = 3;  // CTAs per SM when their rings fit shared memory
 constexpr int kTmaStages = 2;     // default depth of the shared-memory ring of a CTA
 constexpr int kTmaMaxStages = 4;  // deepest ring (bura_options.tma_stages)
 constexpr long long kTmaWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
