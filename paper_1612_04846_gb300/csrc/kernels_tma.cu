@@ -68,15 +68,20 @@ constexpr size_t kSmemReserved = 1024;       // per CTA, by the system
 // every thread.  Returns false (after draining the copies in flight and flagging the fault) when a
 // stage did not arrive in time; the caller still runs its epilogue, so every block joins the grid
 // reduction and the reduction tickets stay consistent.
-template <class Issue, class Compute>
+// SYNC_COMPUTE: compute() has CTA barriers of its own, so every thread must call it for every tile and
+// the threads agree on a timed-out wait before it (one more barrier per tile).  Without, a thread whose
+// wait timed out skips compute() and the agreement rides on the barrier that frees the stage.
+template <bool SYNC_COMPUTE, class Issue, class Compute>
 __device__ __forceinline__ bool tile_loop(int ntiles, int S, unsigned char* smem, size_t sbytes, Scal* scal,
                                           Issue&& issue, Compute&& compute) {
     __shared__ __align__(8) uint64_t bars[kTmaMaxStages];
+    __shared__ int timed_out;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nmine = ntiles > (int)blockIdx.x ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
+        timed_out = 0;
     }
     __syncthreads();
     if (tid == 0)
@@ -87,9 +92,16 @@ __device__ __forceinline__ bool tile_loop(int ntiles, int S, unsigned char* smem
     for (; k < nmine; ++k) {
         const int s = k % S;
         const bool got = mbar_wait_bounded(&bars[s], (unsigned)(k / S) & 1u);
-        if (__syncthreads_or(!got)) { ok = false; break; }
-        compute(smem + s * sbytes, (int)blockIdx.x + k * (int)gridDim.x);
-        __syncthreads();  // stage s is free again
+        if constexpr (SYNC_COMPUTE) {
+            if (__syncthreads_or(!got)) { ok = false; break; }
+            compute(smem + s * sbytes, (int)blockIdx.x + k * (int)gridDim.x);
+            __syncthreads();  // stage s is free again
+        } else {
+            if (got) compute(smem + s * sbytes, (int)blockIdx.x + k * (int)gridDim.x);
+            else timed_out = 1;
+            __syncthreads();  // stage s is free again; timed_out is the same for every thread now
+            if (timed_out) { ok = false; break; }
+        }
         if (tid == 0 && k + S < nmine)
             issue(smem + s * sbytes, (int)blockIdx.x + (k + S) * (int)gridDim.x, &bars[s]);
     }
@@ -169,7 +181,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     const unsigned tx_bytes = (unsigned)(kHaloPts * Kp * 4 + (HAS_DIN ? 2 : 1) * kTilePts * Kp * 4);
     Accum<float> acc;
     const bool dot = red.op != RED_NONE;
-    tile_loop(
+    tile_loop<false>(
         g.ntiles, g.stages, smem, sb, red.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
         d[v] = (float)dsh[off + v];
     }
     const unsigned tx_bytes = (unsigned)(kHaloPts * Kp * 4);
-    tile_loop(
+    tile_loop<false>(
         g.ntiles, g.stages, smem, sb, none.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
@@ -299,7 +311,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     }
     const unsigned tx_bytes = (unsigned)(2 * kHaloPts * Kp * 4);
     Accum<float> acc;
-    tile_loop(
+    tile_loop<false>(
         g.ntiles, g.stages, smem, sb, red.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     const float w1[3] = {0.25f, 0.5f, 0.25f};
     const float diag = g.wx + g.wx + g.wy + g.wy;
     const unsigned tx_bytes = (unsigned)(kRsX * kRsY * Kp * 4);
-    tile_loop(
+    tile_loop<true>(
         g.nctiles, g.stages, smem, sb, none.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             const int cy = t / g.ncx, cx = t - cy * g.ncx;
@@ -476,7 +488,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
         d[v] = (float)dsh[off + v];
     }
     const unsigned tx_bytes = (unsigned)((kHaloPts + kCpX * kCpY + kTilePts) * Kp * 4);
-    tile_loop(
+    tile_loop<true>(
         g.ntiles, g.stages, smem, sb, none.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
@@ -564,7 +576,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     for (int v = 0; v < 4; ++v) a[v] = red.scal->alphaf[off + v];
     const unsigned tx_bytes = (unsigned)(4 * kTilePts * Kp * 4);
     Accum<float> acc;
-    tile_loop(
+    tile_loop<false>(
         g.ntiles, g.stages, smem, sb, red.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
