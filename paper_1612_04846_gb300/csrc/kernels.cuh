@@ -133,6 +133,7 @@ constexpr int kCoarseThreads = 512;            // CTA size of the single-CTA coa
 constexpr size_t kCoarseSmem = 200 * 1024;     // shared memory budget of that CTA's vectors
 constexpr size_t kCoarseTables = 16 * 1024;    // and of its copies of the small Chebyshev tables
 constexpr size_t kCoarseSmemMax = 227 * 1024;  // all of that CTA's dynamic shared memory
+constexpr int kMaxDevices = 64;               // devices whose per-function launch limits are tracked
 struct CoarseArgs {
     int nlev;
     int Kp;

@@ -8,6 +8,8 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -1042,13 +1044,31 @@ void Ops<T>::prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim
     else launch_pdl(k_prolong_add<T, 3>, dim3(gf.blocks), blk(gf), 0, s, Lf, Lc, gf.Kp, ec, x);
 }
 
+// The dynamic shared memory limit is a property of the kernel function (per device), not of a launch, so
+// it is only ever raised: a plan set up later with a smaller coarse CTA must not lower the limit under a
+// plan whose graph launches more.
+template <class T, int DIM, bool VAR>
+cudaError_t prepare_coarse_t(int bytes) {
+    static std::mutex m;
+    static int limit[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(m);
+    if (bytes <= limit[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_coarse_cycle<T, DIM, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) limit[dev] = bytes;
+    return e;
+}
+
 template <class T>
 cudaError_t Ops<T>::prepare_coarse(int dim, bool var, size_t smem_bytes) {
     const int b = (int)smem_bytes;
-    if (dim == 2 && !var) return cudaFuncSetAttribute(k_coarse_cycle<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (dim == 2 && var) return cudaFuncSetAttribute(k_coarse_cycle<T, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (dim == 3 && !var) return cudaFuncSetAttribute(k_coarse_cycle<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    return cudaFuncSetAttribute(k_coarse_cycle<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (dim == 2 && !var) return prepare_coarse_t<T, 2, false>(b);
+    if (dim == 2 && var) return prepare_coarse_t<T, 2, true>(b);
+    if (dim == 3 && !var) return prepare_coarse_t<T, 3, false>(b);
+    return prepare_coarse_t<T, 3, true>(b);
 }
 
 template <class T>

@@ -351,3 +351,29 @@ def test_full_size_3d_variable_coefficients(lib):
     assert bound <= tol * fn, bound / fn
     usum = sum(c[j] * V[j] for j in range(k + 1))
     assert _rel(u, usum) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("MIXED", 1e-6), ("FP64", 1e-10)])
+def test_plan_set_up_after_a_larger_coarse_cta_solves_both(lib, precision, tol):
+    """The single-CTA coarse kernel's shared-memory limit belongs to the kernel, not to a plan: a plan
+    set up later with a smaller coarse CTA (31^2: three levels, ~134 KB) must not lower the limit under
+    an earlier plan whose CTA holds its whole hierarchy (63x31: four levels, ~187 KB).  Both plans are
+    solved after both are set up, first the larger one."""
+    probs = [((63, 31), 0.25, 9), ((31, 31), 0.5, 5)]
+    prec = getattr(lib, "BURA_PREC_" + precision)
+    plans = []
+    try:
+        for shape, alpha, k in probs:
+            plans.append(lib.bura_setup(shape, alpha, k, options=_opts(lib, prec)))
+        for i, (shape, alpha, k) in enumerate(probs):
+            nps = _np_shape(shape)
+            f = W.rhs_uniform(nps, 30 + i)
+            fd = torch.from_numpy(f).cuda()
+            ud = torch.zeros_like(fd)
+            assert lib.bura_solve(plans[i], fd, ud, tol) == lib.BURA_OK
+            torch.cuda.synchronize()
+            ref = tables.entry(alpha, k)
+            assert _rel(ud.cpu().numpy(), exact.bura_value(nps, f, ref["c"], ref["d"])) <= tol, shape
+    finally:
+        for p in plans:
+            lib.bura_destroy(p)
