@@ -237,11 +237,29 @@ int bura_residual_norms_noalloc(const bura_grid* grid, int nsys, const double* d
 /* Frees every device and host resource of the plan (NULL is accepted). */
 int bura_destroy(bura_plan* plan);
 
+/* Batched solves: n independent problems, one per plan, solved concurrently on this GPU (the first row
+ * of the "next" list of the build: many systems x shifts x right-hand sides in flight together).
+ *   plans[i]  plan of problem i (grid, coefficients, alpha, k, options of its own); a plan may appear
+ *             only once in the list (its buffers serve one solve at a time);
+ *   f[i]      device FP64 right-hand side of plan i's grid (N_i values, lexicographic, x fastest);
+ *   u[i]      device FP64 output, N_i values;
+ *   tol       the relative tolerance of bura_solve, for every problem;
+ *   nworkers  host worker threads, each with its own non-blocking CUDA stream, taking the problems in
+ *             list order (0: 16; at most n);
+ *   status    optional, n entries: the status bura_solve returns for each problem.
+ * Each problem is solved exactly as bura_solve solves it alone (the plan's own buffers and captured
+ * PCG graph, deterministic reductions), so u[i] is bit-for-bit the single-problem result; the workers'
+ * streams overlap the problems' kernels on the device.  Blocks until every solve has finished.
+ * Returns BURA_OK, BURA_ENOCONV if some problem missed the tolerance (its u still written), the first
+ * other error of any problem, or BURA_EINVAL (null pointers, n < 0, a plan listed twice). */
+int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
+                     int nworkers, int* status);
+
 /* Static description of a status code. */
 const char* bura_strerror(int status);
 
 /* Name and description of the CUDA runtime error behind the last BURA_ECUDA / BURA_ENOMEM returned
- * by this library in this process ("no error" if none); a static string. */
+ * by this library to the calling thread ("no error" if none); a thread-local static string. */
 const char* bura_last_cuda_error(void);
 
 #ifdef __cplusplus

@@ -91,6 +91,7 @@ def _lib():
         L.bura_get_stats.argtypes = [P, C.POINTER(bura_stats)]
         L.bura_destroy.argtypes = [P]
         L.bura_residual_norms_noalloc.argtypes = [C.POINTER(bura_grid), I, dp, P, P, P, P]
+        L.bura_solve_batch.argtypes = [C.POINTER(P), C.POINTER(P), C.POINTER(P), I, D, I, C.POINTER(I)]
         L.bura_set_profiling.argtypes = [P, I]
         L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
         L.bura_strerror.argtypes = [I]
@@ -99,7 +100,8 @@ def _lib():
         L.bura_last_cuda_error.restype = C.c_char_p
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
-                     "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc"):
+                     "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
+                     "bura_solve_batch"):
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -183,6 +185,22 @@ def bura_solve(plan, f, u, tol, stream=None):
                   allow=(BURA_ENOCONV,))
 
 
+def bura_solve_batch(plans, fs, us, tol, nworkers=0):
+    """Solve len(plans) independent problems concurrently (device float64 tensors fs[i], us[i]).
+    Returns the list of per-problem statuses; raises on an error other than BURA_ENOCONV."""
+    n = len(plans)
+    if len(fs) != n or len(us) != n:
+        raise ValueError("plans, fs and us must have the same length")
+    P = C.c_void_p
+    pa = (P * max(n, 1))(*[C.cast(p, P) for p in plans])
+    fa = (P * max(n, 1))(*[_dptr(t) for t in fs])
+    ua = (P * max(n, 1))(*[_dptr(t) for t in us])
+    st = (C.c_int * max(n, 1))()
+    _check(_lib().bura_solve_batch(pa, fa, ua, int(n), float(tol), int(nworkers), st), "bura_solve_batch",
+           allow=(BURA_ENOCONV,))
+    return list(st)[:n]
+
+
 def bura_solve_host(plan, f, u, tol, stream=None):
     """Same with host numpy arrays (copies inside the call)."""
     return _check(_lib().bura_solve_host(plan, _hptr(f), _hptr(u), float(tol), _stream(stream)),
@@ -249,4 +267,4 @@ def bura_destroy(plan):
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
             "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-            "bura_last_cuda_error"]
+            "bura_last_cuda_error", "bura_solve_batch"]

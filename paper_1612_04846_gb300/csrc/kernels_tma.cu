@@ -683,15 +683,15 @@ TmaGeo tma_geo(const Lev& L, const Lev* Lc, int Kp) {
 }
 
 cudaError_t tma_encode(CUtensorMap* m, const float* base, int Kp, int nx, int ny, int boxkind) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // resolved once per process (a thread-safe static initialisation: plans may be set up concurrently)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess) return e;
-        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+        return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                                                                        : nullptr;
+    }();
+    if (!encode) return cudaErrorNotSupported;
     int bx = 0, by = 0;
     tma_box_dims(boxkind, &bx, &by);
     const cuuint32_t estr[3] = {1, 1, 1};

@@ -8,6 +8,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <atomic>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/bura.h"
@@ -157,7 +160,7 @@ struct bura_plan {
 
 namespace {
 
-cudaError_t g_last = cudaSuccess;
+thread_local cudaError_t g_last = cudaSuccess;  // per calling thread (batch workers run in parallel)
 #define CK(call)                                  \
     do {                                          \
         cudaError_t e_ = (call);                  \
@@ -492,9 +495,11 @@ int build_tma(bura_plan* p, Work<T>& w) {
     return BURA_OK;
 }
 
+// full = false: only what the mixed path's FP64 refinement and bura_apply_shifted use of the FP64 work
+// (level-0 launch shape, geometry and face coefficients, the shifts); no hierarchy, no PCG buffers.
 template <class T>
-int build_work(bura_plan* p, Work<T>& w) {
-    const int nlev = (int)p->hl.size();
+int build_work(bura_plan* p, Work<T>& w, bool full = true) {
+    const int nlev = full ? (int)p->hl.size() : 1;
     w.W = VecT<T>::W;
     w.Kp = ceil_to(p->K, w.W);
     w.C = w.Kp / w.W;
@@ -535,6 +540,7 @@ int build_work(bura_plan* p, Work<T>& w) {
                 else L.fz = dptr;
             }
         }
+        if (!full) break;
         const size_t vb = (size_t)h.N * w.Kp * sizeof(T);
         CA(dalloc(p, &w.b[l], vb));  // level 0 uses the CG residual instead; kept for the coarse CTA
         CA(dalloc(p, &w.xa[l], vb));
@@ -560,6 +566,13 @@ int build_work(bura_plan* p, Work<T>& w) {
         CA(dalloc(p, &w.c2[l], t2.size() * sizeof(T)));
         CK(cudaMemcpy(w.c1[l], t1.data(), t1.size() * sizeof(T), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(w.c2[l], t2.data(), t2.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    if (!full) {
+        std::vector<T> dsht(KMAXP, T(0));
+        for (int s = 0; s < p->K; ++s) dsht[s] = (T)p->d[s];
+        CA(dalloc(p, &w.dsh, KMAXP * sizeof(T)));
+        CK(cudaMemcpy(w.dsh, dsht.data(), KMAXP * sizeof(T), cudaMemcpyHostToDevice));
+        return BURA_OK;  // w.ready stays false: this work never runs a PCG
     }
     // the first level with at most kExactPoints points is solved exactly (dense inverses); the levels
     // below it are never visited
@@ -913,6 +926,10 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
 template <class T>
 int build_graph(bura_plan* p, Work<T>& w) {
     if (w.exec) return BURA_OK;
+    // capture and instantiation happen once per plan; plans solved concurrently by batch workers build
+    // their graphs one at a time
+    static std::mutex build_mutex;
+    std::lock_guard<std::mutex> lock(build_mutex);
     CK(cudaGraphCreate(&w.graph, 0));
     CK(cudaGraphConditionalHandleCreate(&w.cond, w.graph, 1u, cudaGraphCondAssignDefault));
     // the parameter struct holds a union with no default constructor: start from zeroed storage
@@ -935,9 +952,15 @@ int build_graph(bura_plan* p, Work<T>& w) {
     p->tr.launches = before;
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(p->cap, &captured);
-    if (rc != BURA_OK) return rc;
-    CK(e);
-    CK(cudaGraphInstantiate(&w.exec, w.graph, 0));
+    if (rc == BURA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&w.exec, w.graph, 0);
+    if (rc != BURA_OK || e != cudaSuccess) {
+        // drop the partial graph, so that the plan stays destroyable and a later solve captures afresh
+        cudaGraphDestroy(w.graph);
+        w.graph = nullptr;
+        w.exec = nullptr;
+        if (rc != BURA_OK) return rc;
+        CK(e);
+    }
     return BURA_OK;
 }
 
@@ -1411,7 +1434,7 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     p->cluster_ok = cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, p->dev) == cudaSuccess && cl != 0;
     if (o.coarse_kernel == BURA_COARSE_CLUSTER && !p->cluster_ok) return fail(BURA_EINVAL);
 
-    rc = build_work<double>(p, p->w64);
+    rc = build_work<double>(p, p->w64, o.precision == BURA_PREC_FP64);
     if (rc != BURA_OK) return fail(rc);
     if (o.precision == BURA_PREC_MIXED) {
         rc = build_work<float>(p, p->w32);
@@ -1506,6 +1529,72 @@ int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, voi
     if (p->tr.on) {
         CK(cudaStreamSynchronize(s));
         collect_trace(p);
+    }
+    return rc;
+}
+
+int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
+                     int nworkers, int* status) {
+    if (n < 0 || nworkers < 0 || (n > 0 && (!plans || !f || !u))) return BURA_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || !f[i] || !u[i]) return BURA_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return BURA_EINVAL;  // a plan's buffers serve one solve at a time
+    }
+    if (n == 0) return BURA_OK;
+    const int nw = std::max(1, std::min(nworkers > 0 ? nworkers : 16, n));
+    std::vector<int> st(n, BURA_OK);
+    std::atomic<int> next(0);
+    std::mutex err_mutex;
+    cudaError_t first_err = cudaSuccess;  // reported to the calling thread by bura_last_cuda_error
+    auto worker = [&]() {
+        // one stream per worker; the plans are taken in list order, each solved exactly as bura_solve
+        // does it alone (its own buffers, deterministic reductions), so its result does not depend on
+        // which other solves run beside it
+        cudaStream_t s = nullptr;
+        int dev = -1;
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= n) break;
+            bura_plan* p = plans[i];
+            if (p->dev != dev) {
+                if (s) {
+                    cudaStreamSynchronize(s);
+                    cudaStreamDestroy(s);
+                    s = nullptr;
+                }
+                cudaError_t e = cudaSetDevice(p->dev);
+                if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+                if (e != cudaSuccess) {
+                    s = nullptr;
+                    g_last = e;
+                    st[i] = BURA_ECUDA;
+                    std::lock_guard<std::mutex> lock(err_mutex);
+                    if (first_err == cudaSuccess) first_err = e;
+                    continue;
+                }
+                dev = p->dev;
+            }
+            st[i] = bura_solve(p, f[i], u[i], tol, s);
+            if (st[i] == BURA_ECUDA) {
+                std::lock_guard<std::mutex> lock(err_mutex);
+                if (first_err == cudaSuccess) first_err = g_last;
+            }
+        }
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    };
+    std::vector<std::thread> pool;
+    pool.reserve(nw);
+    for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    if (first_err != cudaSuccess) g_last = first_err;
+    int rc = BURA_OK;
+    for (int i = 0; i < n; ++i) {
+        if (status) status[i] = st[i];
+        if (st[i] != BURA_OK && (rc == BURA_OK || rc == BURA_ENOCONV)) rc = st[i];
     }
     return rc;
 }

@@ -65,6 +65,20 @@ def test_setup_rejects_bad_options_on_the_host(lib, field, value):
     assert ei.value.code == lib.BURA_EINVAL
 
 
+def test_batch_arguments_on_the_host(lib):
+    """bura_solve_batch: an empty batch is a no-op; null arrays and a negative count are rejected before
+    any CUDA call."""
+    import ctypes as C
+    assert lib.bura_solve_batch([], [], [], 1e-6) == []
+    L = lib._lib()
+    st = (C.c_int * 1)()
+    assert L.bura_solve_batch(None, None, None, 1, 1e-6, 1, st) == lib.BURA_EINVAL
+    assert L.bura_solve_batch(None, None, None, -1, 1e-6, 1, st) == lib.BURA_EINVAL
+    P = C.c_void_p
+    nulls = (P * 1)()
+    assert L.bura_solve_batch(nulls, nulls, nulls, 1, 1e-6, 1, st) == lib.BURA_EINVAL
+
+
 def test_setup_rejects_nonpositive_coefficients(lib):
     from paper_1612_04846_gb300 import workloads as W
     faces = list(W.constant_faces((4, 5)))
