@@ -46,6 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing leg")
     ap.add_argument("--profile-steps", type=int, default=6, help="solves timed kernel by kernel for the roofline")
     ap.add_argument("--skip-3d", action="store_true", help="skip the 3D variable-coefficient workload")
+    ap.add_argument("--skip-batch", action="store_true", help="skip the batched 256-problem workload")
     return ap.parse_args(argv)
 
 
@@ -251,6 +252,49 @@ def bench_3d(bura, W, np, torch, dev, stream, flush, rank, steps):
             "err_bound": st["err_bound"], "levels": st["levels"], "setup_s": setup_s}
 
 
+WORKLOAD_BATCH = ("batched: 256 right-hand sides over 2D 5-point grids drawn uniformly from {63^2,127^2,255^2,511^2}, "
+                  "alpha ~ U(0.1,0.9), k ~ U{5..9}, f ~ U[-1,1] (seed 4), FP32 MG-PCG inner + FP64 refinement, "
+                  "tol 1e-6; bura_solve_batch, 32 worker streams")
+
+
+def bench_batch(bura, W, np, torch, dev, rank, reps):
+    """Solves/s of the batched workload: bura_solve_batch over 256 resident plans (setup timed apart),
+    against the same 256 problems solved one after another on one stream."""
+    rng = np.random.default_rng(4 + 1000 * rank)
+    sizes = [63, 127, 255, 511]
+    plans, fs, us, unk = [], [], [], 0
+    t0 = time.perf_counter()
+    try:
+        for i in range(256):
+            n = sizes[rng.integers(len(sizes))]
+            alpha = float(rng.uniform(0.1, 0.9))
+            k = int(rng.integers(5, 10))
+            plans.append(bura.bura_setup((n, n), alpha, k))
+            fs.append(torch.from_numpy(W.rhs_uniform((n, n), 10000 + i)).to(dev))
+            us.append(torch.zeros_like(fs[-1]))
+            unk += n * n * (k + 1)
+        setup_s = time.perf_counter() - t0
+        bura.bura_solve_batch(plans, fs, us, TOL, 32)  # warm-up: captures every plan's PCG graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            st = bura.bura_solve_batch(plans, fs, us, TOL, 32)
+        torch.cuda.synchronize()
+        tb = (time.perf_counter() - t0) / reps
+        if any(x != bura.BURA_OK for x in st):
+            raise RuntimeError("batched solve did not converge")
+        t0 = time.perf_counter()
+        bura.bura_solve_batch(plans, fs, us, TOL, 1)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+    finally:
+        for p in plans:
+            bura.bura_destroy(p)
+    return {"workload": WORKLOAD_BATCH, "solves_per_s": 256 / tb, "ms_per_batch": 1e3 * tb, "reps": reps,
+            "Gunknown_shifts_per_s": unk / tb / 1e9, "one_stream_solves_per_s": 256 / ts, "setup_s": setup_s,
+            "timing": "host wall clock around the blocking bura_solve_batch call"}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -429,6 +473,9 @@ def main(argv=None):
     w3 = None
     if not args.skip_3d:
         w3 = bench_3d(bura, W, np, torch, dev, stream, flush, rank, max(3, args.steps // 20))
+    wb = None
+    if not args.skip_batch:
+        wb = bench_batch(bura, W, np, torch, dev, rank, 2)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -443,7 +490,7 @@ def main(argv=None):
                 "fp64_path_solves_per_s": fp64_solves,
                 "df_refine_solves_per_s": df_solves,
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3}}
+                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "batch_256_mixed_2d": wb}}
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
         dist.destroy_process_group()
