@@ -104,7 +104,12 @@ typedef struct {
     int refine;           /* bura_refine (mixed precision only); default BURA_REFINE_FP64 */
     int tma_stages;       /* depth of the shared-memory ring of the TMA-staged sweeps, 1..4 (a kernel whose
                              ring does not fit shared memory uses fewer); 0 = auto (2) */
-    int reserved[1];
+    int post_smooth_split; /* 0 (default): on TMA-staged levels with degree-2 smoothing, the prolongation and
+                             both post-smoothing steps run as one sweep (the first step recomputed on a
+                             one-point halo); 1: as two sweeps (prolongation + first step, then the second
+                             step).  Every point gets the same operations either way; r.z is summed by
+                             a sweep with another CTA count, so the iterates may differ in the last
+                             bits of the FP32 beta. */
 } bura_options;
 
 /* Statistics of the last bura_solve*/

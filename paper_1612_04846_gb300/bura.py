@@ -35,7 +35,7 @@ class bura_options(C.Structure):
                 ("max_iters", C.c_int), ("max_outer", C.c_int), ("inner_rtol", C.c_double),
                 ("coarse_degree", C.c_int), ("block_points", C.c_int), ("blocks_per_sm", C.c_int),
                 ("coarse_kernel", C.c_int), ("cluster_size", C.c_int), ("sweeps", C.c_int),
-                ("refine", C.c_int), ("tma_stages", C.c_int), ("reserved", C.c_int * 1)]
+                ("refine", C.c_int), ("tma_stages", C.c_int), ("post_smooth_split", C.c_int)]
 
 
 class bura_stats(C.Structure):

@@ -77,6 +77,7 @@ enum ReduceOp { RED_NONE = 0, RED_ALPHA = 1, RED_CONV = 2, RED_BETA = 3, RED_STO
 // the group partials in group order.  Either way the order is fixed: results are deterministic.
 constexpr int kRedGroup = 16;
 constexpr int kRedOneLevel = 640;
+constexpr int kRedFinBatch = 16;  // partials loaded at once per thread in the final step
 struct Red {
     double* partial;          // [gridDim.x * Kp] block partials, then [groups * Kp] group partials
     unsigned int* tickets;    // [max groups + 1] counters, zero between reductions
@@ -84,7 +85,16 @@ struct Red {
     double* out;              // RED_STORE destination [Kp]
     int op;
     unsigned long long cond;  // cudaGraphConditionalHandle of a captured PCG loop (0: none)
+    int defer;                // 1: blocks only store their partials and block 0 the grid size in *nblk;
+                              // a k_red_finish launched next on the stream sums them (no fences, no
+                              // tickets, no serial tail in the producing grid)
+    unsigned int* nblk;       // grid size of a deferred reduction's producer
 };
+
+// The final step of a deferred reduction: one CTA of kRedFinishThreads sums the producer's block
+// partials in block order and applies op; launched right after the producer on the same stream.
+constexpr int kRedFinishThreads = 256;
+void launch_red_finish(const Red& red, int Kp, cudaStream_t s);
 
 // One level of the single-CTA coarse V-cycle: its vectors live in the CTA's shared memory at the
 // given byte offsets.  c1/c2 hold deg rows of Kp Chebyshev coefficients (global memory).

@@ -157,6 +157,36 @@ void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStr
     k_norm2<<<blocks, dim3(8, 32), 256 * 2 * sizeof(double), s>>>((int)N, f, red);
 }
 
+// Final step of a deferred grid reduction (Red::defer): the producer, the previous kernel on the
+// stream, has completed when griddepcontrol.wait returns, so its partials are visible without fences.
+// The CG state record is loaded into shared memory together with the partials (one L2 round trip for
+// both), updated there and written back whole; no other kernel touches it meanwhile.
+__global__ void __launch_bounds__(kRedFinishThreads) k_red_finish(Red red, int Kp) {
+    __shared__ double sm[kRedFinishThreads];
+    __shared__ Scal sc;
+    constexpr int kWords = (int)(sizeof(Scal) / sizeof(unsigned));
+    static_assert(sizeof(Scal) % sizeof(unsigned) == 0 && kWords <= 2 * kRedFinishThreads, "Scal copy");
+    pdl_trigger();  // the next kernel may start its prologue; it waits for this grid to complete
+    pdl_wait();
+    const int tid = threadIdx.x;
+    const unsigned* gs = reinterpret_cast<const unsigned*>(red.scal);
+    const unsigned w0 = tid < kWords ? __ldcg(gs + tid) : 0u;
+    const unsigned w1 = tid + kRedFinishThreads < kWords ? __ldcg(gs + tid + kRedFinishThreads) : 0u;
+    const double part = red_thread_sum(red.partial, (int)__ldcg(red.nblk), Kp);
+    unsigned* ss = reinterpret_cast<unsigned*>(&sc);
+    if (tid < kWords) ss[tid] = w0;
+    if (tid + kRedFinishThreads < kWords) ss[tid + kRedFinishThreads] = w1;
+    red_apply(red, &sc, part, Kp, sm);  // its first barrier publishes the copy
+    __syncthreads();
+    unsigned* gd = reinterpret_cast<unsigned*>(red.scal);
+    if (tid < kWords) gd[tid] = ss[tid];
+    if (tid + kRedFinishThreads < kWords) gd[tid + kRedFinishThreads] = ss[tid + kRedFinishThreads];
+}
+
+void launch_red_finish(const Red& red, int Kp, cudaStream_t s) {
+    launch_pdl(k_red_finish, dim3(1), dim3(kRedFinishThreads), 0, s, red, Kp);
+}
+
 // r32 = f * invscale_j for every active system (the residual of the zero initial guess); x32 = p32 = 0.
 __global__ void k_cast_f(int N, int Kp32, int K, const double* __restrict__ f, const double* __restrict__ invscale,
                          float* __restrict__ r32, float* __restrict__ x32, float* __restrict__ p32) {

@@ -253,8 +253,7 @@ __device__ __forceinline__ void stencil(const Lev& L, int Kp, int P, int off, co
 }
 
 // ------------------------------------------------------------------ reductions
-__device__ __forceinline__ void finish_one(const Red& red, int s, double tot) {
-    Scal* S = red.scal;
+__device__ __forceinline__ void finish_one(const Red& red, Scal* S, int s, double tot) {
     switch (red.op) {
         case RED_ALPHA: {
             S->pq[s] = tot;
@@ -295,8 +294,60 @@ __device__ __forceinline__ void finish_one(const Red& red, int s, double tot) {
     }
 }
 
+// Final step of a grid reduction, by every thread of one block.  red_thread_sum: thread (s, g) adds
+// partials g, g + G, g + 2G, ... of system s in that order (G = threads / Kp), with up to kRedFinBatch
+// loads in flight (one L2 round trip per batch, not per partial).  red_apply: the G sums of each system
+// in order, op applied to the CG state S and, for RED_CONV, the PCG bookkeeping and loop control.  sm
+// holds at least one double per thread.
+__device__ __forceinline__ double red_thread_sum(const double* fin, int nfin, int Kp) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int G = (int)(blockDim.x * blockDim.y) / Kp;
+    double part = 0.0;
+    if (tid < Kp * G) {
+        const int s = tid % Kp, g = tid / Kp;
+        for (int b0 = g; b0 < nfin; b0 += kRedFinBatch * G) {
+            double v[kRedFinBatch];
+#pragma unroll
+            for (int j = 0; j < kRedFinBatch; ++j) {
+                const int b = b0 + j * G;
+                v[j] = b < nfin ? __ldcg(fin + (size_t)b * Kp + s) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < kRedFinBatch; ++j) part += v[j];
+        }
+    }
+    return part;
+}
+
+__device__ __forceinline__ void red_apply(const Red& red, Scal* S, double part, int Kp, double* sm) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int G = (int)(blockDim.x * blockDim.y) / Kp;
+    __syncthreads();
+    if (tid < Kp * G) sm[tid] = part;
+    __syncthreads();
+    if (tid < Kp) {
+        double tot = 0.0;
+        for (int g = 0; g < G; ++g) tot += sm[g * Kp + tid];
+        finish_one(red, S, tid, tot);
+    }
+    __syncthreads();
+    if (tid == 0 && red.op == RED_CONV) {
+        int na = 0;
+        for (int s = 0; s < Kp; ++s) na += S->active[s] ? 1 : 0;
+        S->nactive = na;
+        S->it += 1;
+        S->parity ^= 1;
+        // device-side loop control of a captured PCG loop (conditional WHILE node)
+        if (red.cond) {
+            const bool go = na > 0 && !S->breakdown && !S->fault && S->it < S->max_it;
+            cudaGraphSetConditional(red.cond, go ? 1u : 0u);
+        }
+    }
+}
+
 // Block reduction of per-thread partials (W systems per thread, chunk = threadIdx.x) followed by
-// the grid reduction in the last block.  Every thread of the block must call this.
+// the grid reduction in the last block, or, for a deferred reduction, by k_red_finish.  Every thread
+// of the block must call this.
 template <class T>
 __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     constexpr int W = VecT<T>::W;
@@ -317,6 +368,16 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
     if (tid < Kp * G) sm[tid] = part;
     __syncthreads();
     const int nblk = (int)gridDim.x;
+    if (red.defer) {
+        // visible to k_red_finish, which waits for this grid to complete
+        if (tid < Kp) {
+            double tot = 0.0;
+            for (int g = 0; g < G; ++g) tot += sm[g * Kp + tid];
+            red.partial[(size_t)blockIdx.x * Kp + tid] = tot;
+        }
+        if (tid == 0 && blockIdx.x == 0) *red.nblk = (unsigned)nblk;
+        return;
+    }
     // one level (the last block sums every block partial) for grids up to kRedOneLevel blocks, such as
     // the persistent TMA kernels; two levels (groups of kRedGroup blocks) for the grid-stride kernels
     const bool one_level = nblk <= kRedOneLevel;
@@ -367,44 +428,8 @@ __device__ void reduce_finish(Accum<T>& acc, const Red& red, int Kp) {
         fin = part2;
         nfin = ngroups;
     }
-    // final step: thread (s, g) adds partials g, g + G, ... of system s, then the G sums in order
-    part = 0.0;
-    if (tid < Kp * G) {
-        const int s = tid % Kp, g = tid / Kp;
-        int b = g;
-        for (; b + G < nfin; b += 2 * G) {
-            const double v0 = __ldcg(fin + (size_t)b * Kp + s);
-            const double v1 = __ldcg(fin + (size_t)(b + G) * Kp + s);
-            part += v0;
-            part += v1;
-        }
-        for (; b < nfin; b += G) part += __ldcg(fin + (size_t)b * Kp + s);
-    }
-    __syncthreads();
-    if (tid < Kp * G) sm[tid] = part;
-    __syncthreads();
-    if (tid < Kp) {
-        double tot = 0.0;
-        for (int g = 0; g < G; ++g) tot += sm[g * Kp + tid];
-        finish_one(red, tid, tot);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        red.tickets[one_level ? 0 : ngroups] = 0u;
-        if (red.op == RED_CONV) {
-            Scal* S = red.scal;
-            int na = 0;
-            for (int s = 0; s < Kp; ++s) na += S->active[s] ? 1 : 0;
-            S->nactive = na;
-            S->it += 1;
-            S->parity ^= 1;
-            // device-side loop control of a captured PCG loop (conditional WHILE node)
-            if (red.cond) {
-                const bool go = na > 0 && !S->breakdown && !S->fault && S->it < S->max_it;
-                cudaGraphSetConditional(red.cond, go ? 1u : 0u);
-            }
-        }
-    }
+    if (tid == 0) red.tickets[one_level ? 0 : ngroups] = 0u;
+    red_apply(red, red.scal, red_thread_sum(fin, nfin, Kp), Kp, sm);
 }
 
 // ------------------------------------------------------------------ sweeps (per level)

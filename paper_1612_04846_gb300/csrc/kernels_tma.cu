@@ -35,13 +35,17 @@ constexpr int kE1X = 2 * kTXc + 3, kE1Y = 2 * kTYc + 3;
 constexpr int kRX = 2 * kTXc + 1, kRY = 2 * kTYc + 1;
 // Fused prolongation + smoothing: coarse correction box (kCpX x kCpY) of one fine tile + halo.
 constexpr int kCpX = kTX / 2 + 2, kCpY = kTY / 2 + 2;
+// Fused prolongation + both post-smoothing steps: x on a two-point halo (kH2X x kH2Y) and its coarse
+// correction box (kCp2X x kCp2Y).
+constexpr int kH2X = kTX + 4, kH2Y = kTY + 4;
+constexpr int kCp2X = kTX / 2 + 3, kCp2Y = kTY / 2 + 3;
 static_assert(kTX % 2 == 0 && kTY % 2 == 0, "fine tiles start on even grid coordinates");
 
 __host__ __device__ constexpr size_t vec_bytes(int pts, int Kp) { return align_up((size_t)pts * Kp * sizeof(float), 1024); }
 
 // Shared-memory bytes of one stage of each kernel kind, and of its unstaged scratch.
 enum TmaKind { TK_CHEB = 0, TK_CHEB_D = 1, TK_PRE2 = 2, TK_SPMV = 3, TK_PRE2R = 4, TK_PROCHEB = 5, TK_CG = 6,
-               TK_NKIND = 7 };
+               TK_POST2 = 7, TK_NKIND = 8 };
 __host__ __device__ constexpr size_t stage_bytes(int kind, int Kp) {
     return kind == TK_CHEB ? halo_bytes(Kp) + plain_bytes(Kp)
          : kind == TK_CHEB_D ? halo_bytes(Kp) + 2 * plain_bytes(Kp)
@@ -49,11 +53,13 @@ __host__ __device__ constexpr size_t stage_bytes(int kind, int Kp) {
          : kind == TK_SPMV ? 2 * halo_bytes(Kp)
          : kind == TK_PRE2R ? vec_bytes(kRsX * kRsY, Kp)
          : kind == TK_CG ? 4 * plain_bytes(Kp)
+         : kind == TK_POST2 ? vec_bytes(kH2X * kH2Y, Kp) + vec_bytes(kCp2X * kCp2Y, Kp) + halo_bytes(Kp)
          : halo_bytes(Kp) + vec_bytes(kCpX * kCpY, Kp) + plain_bytes(Kp);
 }
 __host__ __device__ constexpr size_t scratch_bytes(int kind, int Kp) {
     return kind == TK_PRE2R ? vec_bytes(kE1X * kE1Y, Kp) + vec_bytes(kRX * kRY, Kp)
          : kind == TK_PROCHEB ? halo_bytes(Kp)
+         : kind == TK_POST2 ? halo_bytes(Kp) + plain_bytes(Kp)
          : 0;
 }
 __host__ __device__ constexpr size_t dyn_smem(int kind, int Kp, int S) {
@@ -139,11 +145,11 @@ __device__ __forceinline__ void st4(float* p, const float (&o)[4]) {
 
 // A x at a tile point (no shift term) from a halo tile H ([kTY+2][kTX+2][Kp] floats) whose values are
 // x(point) = val(h) for a loader `val` of the halo index; diag = 2 wx + 2 wy.
-template <class Val>
+template <int ROW = kTX + 2, class Val>
 __device__ __forceinline__ void stencil_tile(const TmaGeo& g, int hidx, const Val& val, float (&xc)[4],
                                              float (&Ax)[4]) {
     const float diag = g.wx + g.wx + g.wy + g.wy;
-    const int sy = (kTX + 2) * g.Kp;
+    const int sy = ROW * g.Kp;
     float n[4];
     val(hidx, xc);
     float acc[4];
@@ -290,8 +296,9 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
 }
 
 // CG direction update and operator apply: p_new = z + beta p_old at the stencil points, q = (A - dI)
-// p_new, and p_new . q per system; the stages hold z and p_old with their halos.  The direction
-// buffers alternate by the parity in the Scal record, as in the grid kernel.
+// p_new, and p_new . q per system; the stages hold z and p_old with their halos.  p_new is formed once
+// per halo point, in place over z in the stage, and the stencil then reads it from there.  The
+// direction buffers alternate by the parity in the Scal record, as in the grid kernel.
 template <int C>
 __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     k_spmv_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* pa, float* pb, float* __restrict__ q, Red red) {
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     }
     const unsigned tx_bytes = (unsigned)(2 * kHaloPts * Kp * 4);
     Accum<float> acc;
-    tile_loop<false>(
+    tile_loop<true>(
         g.ntiles, g.stages, smem, sb, red.scal,
         [&](unsigned char* st, int t, uint64_t* bar) {
             int x0, y0;
@@ -323,22 +330,26 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
         [&](unsigned char* st, int t) {
             int x0, y0;
             tile_origin(g, t, x0, y0);
-            const float* Z = reinterpret_cast<const float*>(st);
+            float* Z = reinterpret_cast<float*>(st);
             const float* Po = reinterpret_cast<const float*>(st + halo_bytes(Kp));
+            // p_new on the tile and its halo (zero outside the grid, where z and p_old are zero-filled)
+            for (int p = threadIdx.y; p < kHaloPts; p += blockDim.y) {
+                const int h = p * Kp + off;
+                float a[4], b[4];
+                ld4(Z + h, a);
+                ld4(Po + h, b);
+                for (int v = 0; v < 4; ++v) a[v] = fmaf(beta[v], b[v], a[v]);
+                st4(Z + h, a);
+            }
+            fence_proxy_async_smem();  // the stage is refilled by TMA after the tile
+            __syncthreads();
             for (int p = threadIdx.y; p < kTilePts; p += blockDim.y) {
                 const int ly = p / kTX, lx = p - ly * kTX;
                 const int gx = x0 + lx, gy = y0 + ly;
                 if (gx >= g.nx || gy >= g.ny) continue;
                 const int hidx = ((ly + 1) * (kTX + 2) + lx + 1) * Kp + off;
                 float pc[4], Ax[4];
-                stencil_tile(g, hidx,
-                             [&](int h, float (&o)[4]) {
-                                 float a[4], b[4];
-                                 ld4(Z + h, a);
-                                 ld4(Po + h, b);
-                                 for (int v = 0; v < 4; ++v) o[v] = fmaf(beta[v], b[v], a[v]);
-                             },
-                             pc, Ax);
+                stencil_tile(g, hidx, [&](int h, float (&o)[4]) { ld4(Z + h, o); }, pc, Ax);
                 float qv[4];
                 for (int v = 0; v < 4; ++v) qv[v] = fmaf(-dsh[v], pc[v], Ax[v]);
                 const size_t gidx = ((size_t)gy * g.nx + gx) * Kp + off;
@@ -556,6 +567,135 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
     pdl_trigger();
 }
 
+// Prolongation and both post-smoothing steps in one sweep.  Per tile: (1) xin = x + P ec on the tile and
+// a two-point halo, in place over the x stage; (2) the first step on the tile and a one-point halo,
+// x1 = xin + d1 (recomputed by neighbouring tiles, bit for bit the same) into scratch, d1 kept for the
+// tile points; (3) the second step on the tile, stored, with b . xout when red asks for it.  Each step
+// is k_prolong_cheb_tma's and k_cheb_tma's arithmetic, operation for operation; points outside the grid
+// hold zero (Dirichlet).  Traffic per tile: x, ec, b in, xout out, against x, ec, b in and x1, d1 out,
+// then x1, d1, b in and xout out for the two-kernel form.
+template <int C>
+__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
+    k_post2_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout, ChebStepT<float> cs0,
+                ChebStepT<float> cs1, const float* __restrict__ dsh, Red red) {
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* smem = aligned_ring(smem_raw);
+    const int Kp = C * 4;
+    const size_t sb = stage_bytes(TK_POST2, Kp);
+    float* X1 = reinterpret_cast<float*>(smem + g.stages * sb);
+    float* D1 = reinterpret_cast<float*>(smem + g.stages * sb + halo_bytes(Kp));
+    const int off = threadIdx.x * 4;
+    float c20[4], c11[4], c21[4], d[4];
+    for (int v = 0; v < 4; ++v) {
+        c20[v] = (float)cs0.c2[off + v];
+        c11[v] = cs1.c1 ? (float)cs1.c1[off + v] : 0.f;
+        c21[v] = (float)cs1.c2[off + v];
+        d[v] = (float)dsh[off + v];
+    }
+    const size_t e_ofs = vec_bytes(kH2X * kH2Y, Kp);
+    const size_t b_ofs = e_ofs + vec_bytes(kCp2X * kCp2Y, Kp);
+    const unsigned tx_bytes = (unsigned)((kH2X * kH2Y + kCp2X * kCp2Y + kHaloPts) * Kp * 4);
+    const bool dot = red.op != RED_NONE;
+    Accum<float> acc;
+    tile_loop<true>(
+        g.ntiles, g.stages, smem, sb, red.scal,
+        [&](unsigned char* st, int t, uint64_t* bar) {
+            int x0, y0;
+            tile_origin(g, t, x0, y0);
+            mbar_expect_tx(bar, tx_bytes);
+            tma_load_pt(st, &mp.m[0], g, x0 - 2, y0 - 2, bar);
+            tma_load_pt(st + e_ofs, &mp.m[1], g, x0 / 2 - 2, y0 / 2 - 2, bar);
+            tma_load_pt(st + b_ofs, &mp.m[2], g, x0 - 1, y0 - 1, bar);
+        },
+        [&](unsigned char* st, int t) {
+            int x0, y0;
+            tile_origin(g, t, x0, y0);
+            float* X = reinterpret_cast<float*>(st);
+            const float* E = reinterpret_cast<const float*>(st + e_ofs);
+            const float* B = reinterpret_cast<const float*>(st + b_ofs);
+            // (1) xin = x + P ec on the two-point halo region, by 2 x 2 blocks of fine points: the block
+            // at even (fi, fj) interpolates from coarse points (fi/2 - 1 .. fi/2) x (fj/2 - 1 .. fj/2),
+            // at box offsets (bx, by); the weighted sums are k_prolong_cheb_tma's, term for term
+            for (int q = threadIdx.y; q < (kH2X / 2) * (kH2Y / 2); q += blockDim.y) {
+                const int by = q / (kH2X / 2), bx = q - by * (kH2X / 2);
+                float e00[4], e01[4], e10[4], e11[4];
+                ld4(E + (by * kCp2X + bx) * Kp + off, e00);
+                ld4(E + (by * kCp2X + bx + 1) * Kp + off, e01);
+                ld4(E + ((by + 1) * kCp2X + bx) * Kp + off, e10);
+                ld4(E + ((by + 1) * kCp2X + bx + 1) * Kp + off, e11);
+                float s4[4][4];  // [fine point of the block: (0,0), (1,0), (0,1), (1,1)][value]
+                for (int v = 0; v < 4; ++v) {
+                    float t = fmaf(0.25f, e00[v], 0.f);
+                    t = fmaf(0.25f, e01[v], t);
+                    t = fmaf(0.25f, e10[v], t);
+                    s4[0][v] = fmaf(0.25f, e11[v], t);
+                    s4[1][v] = fmaf(0.5f, e11[v], fmaf(0.5f, e01[v], 0.f));
+                    s4[2][v] = fmaf(0.5f, e11[v], fmaf(0.5f, e10[v], 0.f));
+                    s4[3][v] = fmaf(1.f, e11[v], 0.f);
+                }
+                for (int j = 0; j < 4; ++j) {
+                    const int hx = 2 * bx + (j & 1), hy = 2 * by + (j >> 1);
+                    const int fi = x0 - 2 + hx, fj = y0 - 2 + hy;
+                    const int h = (hy * kH2X + hx) * Kp + off;
+                    float xn[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny) {
+                        ld4(X + h, xn);
+                        for (int v = 0; v < 4; ++v) xn[v] += s4[j][v];
+                    }
+                    st4(X + h, xn);
+                }
+            }
+            fence_proxy_async_smem();  // the x stage is refilled by TMA after the tile
+            __syncthreads();
+            // (2) first step on the one-point halo region
+            for (int p = threadIdx.y; p < kHaloPts; p += blockDim.y) {
+                const int hy = p / (kTX + 2), hx = p - hy * (kTX + 2);
+                const int fi = x0 - 1 + hx, fj = y0 - 1 + hy;
+                float xo[4] = {0.f, 0.f, 0.f, 0.f};
+                if (fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny) {
+                    const int hidx = ((hy + 1) * kH2X + hx + 1) * Kp + off;
+                    float xc[4], Ax[4], bv[4], dv[4];
+                    stencil_tile<kH2X>(g, hidx, [&](int h, float (&o)[4]) { ld4(X + h, o); }, xc, Ax);
+                    ld4(B + p * Kp + off, bv);
+                    for (int v = 0; v < 4; ++v) {
+                        const float res = bv[v] - fmaf(-d[v], xc[v], Ax[v]);
+                        const float gg = c20[v] * res;
+                        dv[v] = fmaf(0.f, 0.f, gg);
+                        xo[v] = xc[v] + dv[v];
+                    }
+                    if (hx >= 1 && hx <= kTX && hy >= 1 && hy <= kTY)
+                        st4(D1 + ((hy - 1) * kTX + hx - 1) * Kp + off, dv);
+                }
+                st4(X1 + p * Kp + off, xo);
+            }
+            __syncthreads();
+            // (3) second step on the tile
+            for (int p = threadIdx.y; p < kTilePts; p += blockDim.y) {
+                const int ly = p / kTX, lx = p - ly * kTX;
+                const int gx = x0 + lx, gy = y0 + ly;
+                if (gx >= g.nx || gy >= g.ny) continue;
+                const int hidx = ((ly + 1) * (kTX + 2) + lx + 1) * Kp + off;
+                float xc[4], Ax[4], bv[4], dv[4];
+                stencil_tile(g, hidx, [&](int h, float (&o)[4]) { ld4(X1 + h, o); }, xc, Ax);
+                ld4(B + hidx, bv);
+                ld4(D1 + p * Kp + off, dv);
+                float xo[4];
+                for (int v = 0; v < 4; ++v) {
+                    const float res = bv[v] - fmaf(-d[v], xc[v], Ax[v]);
+                    const float gg = c21[v] * res;
+                    dv[v] = fmaf(c11[v], dv[v], gg);
+                    xo[v] = xc[v] + dv[v];
+                }
+                const size_t gidx = ((size_t)gy * g.nx + gx) * Kp + off;
+                st4(xout + gidx, xo);
+                if (dot) acc.add(bv, xo);
+            }
+        });
+    pdl_trigger();
+    if (dot) reduce_finish<float>(acc, red, Kp);
+}
+
 // CG vector update from TMA-staged tiles: x += alpha p, r -= alpha q and r.r per system (pointwise, no
 // halo).  The grid-stride kernel is limited to 8 CTAs of 4 warps per SM by its registers; here the bytes
 // in flight are the ring's stages, whatever the occupancy.
@@ -634,6 +774,8 @@ cudaError_t prepare_c() {
         return e;
     if ((e = cudaFuncSetAttribute(k_prolong_cheb_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
         cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_post2_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_cg_update_tma<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
         return e;
@@ -810,6 +952,18 @@ cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_hal
     const Shape sh = shape_of(g, nsm, TK_PROCHEB);
     BURA_TMA_C(g.Kp, return launch_tile(k_prolong_cheb_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, xout, dout, cs, dsh,
                                         none))
+}
+
+cudaError_t tma_post2(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo2, const CUtensorMap& mec_cpro2,
+                      const CUtensorMap& mb_halo, float* xout, ChebStepT<float> cs0, ChebStepT<float> cs1,
+                      const float* dsh, const Red& red, cudaStream_t s) {
+    TmaMaps3 mp;
+    mp.m[0] = mx_halo2;
+    mp.m[1] = mec_cpro2;
+    mp.m[2] = mb_halo;
+    const Shape sh = shape_of(g, nsm, TK_POST2);
+    BURA_TMA_C(g.Kp, return launch_tile(k_post2_tma<C>, sh.blocks, sh.threads, C, sh.smem, s, mp, sh.g, xout, cs0, cs1,
+                                        dsh, red))
 }
 
 cudaError_t tma_spmv_p(const TmaGeo& g, int nsm, const CUtensorMap& mz, const CUtensorMap& mpa,

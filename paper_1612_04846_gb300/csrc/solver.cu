@@ -33,7 +33,8 @@ struct HostLevel {
 
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
-           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_NK };
+           K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_REDFIN,
+           K_POST2, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -56,7 +57,9 @@ const char* const kNames[K_NK][2][2] = {
     {{"pre2_restrict_f64", "pre2_restrict_f64@coarse"}, {"pre2_restrict_f32", "pre2_restrict_f32@coarse"}},
     {{"prolong_cheb_f64", "prolong_cheb_f64@coarse"}, {"prolong_cheb_f32", "prolong_cheb_f32@coarse"}},
     {{"update_residual_df", "update_residual_df"}, {"update_residual_df", "update_residual_df"}},
-    {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}}};
+    {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}},
+    {{"red_finish_f64", "red_finish_f64"}, {"red_finish_f32", "red_finish_f32"}},
+    {{"post2_f64", "post2_f64@coarse"}, {"post2_f32", "post2_f32@coarse"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -134,6 +137,7 @@ struct bura_plan {
     double* cdev = nullptr;  // c_j, Kp64 entries
     double* partial = nullptr;
     unsigned int* tickets = nullptr;
+    unsigned int* red_nblk = nullptr;  // grid size of a deferred reduction's producer (after the tickets)
     double* red_out = nullptr;  // [KMAXP]
     // mixed path: refinement accumulator v_j as FP32 pairs hi + lo (Kp32 layout, two ping-pong copies),
     // f as a pair, and the pair form of the level-0 operator's and the weighted sum's coefficients
@@ -208,6 +212,19 @@ void traced(bura_plan* p, int kid, bool is_f32, bool fine, double bytes, cudaStr
         cudaEventRecord(t.ev[2 * t.pending.size() + 1], s);
         t.pending.push_back({slot, bytes});
     }
+}
+
+// The per-iteration reductions of the PCG (r.z, p.q, r.r) are deferred: the producing grid only stores
+// block partials and a one-CTA k_red_finish sums them next on the stream, so the large grids end
+// without fences, tickets or a serial last block.
+Red deferred(const bura_plan* p, Red r) {
+    r.defer = 1;
+    r.nblk = p->red_nblk;
+    return r;
+}
+
+void red_finish(bura_plan* p, const Red& r, int Kp, bool is_f32, cudaStream_t s) {
+    traced(p, K_REDFIN, is_f32, true, 0.0, s, [&] { launch_red_finish(r, Kp, s); });
 }
 
 // Fold the timed launches of the finished solve into the per-kernel totals (stream must be idle).
@@ -457,7 +474,7 @@ int build_tma(bura_plan* p, Work<T>& w) {
         const void* bl = l == 0 ? (const void*)w.r : (const void*)w.b[l];
         struct Want { int box; const void* buf; int lev; };
         std::vector<Want> want = {{TB_HALO, bl, l}, {TB_HALO, w.xa[l], l}, {TB_HALO, w.xb[l], l},
-                                  {TB_PLAIN, bl, l}, {TB_PLAIN, w.dd[l], l}};
+                                  {TB_PLAIN, bl, l}, {TB_PLAIN, w.dd[l], l}, {TB_HALO2, w.xa[l], l}};
         if (l == 0) {
             want.push_back({TB_HALO, w.pa, 0});
             want.push_back({TB_HALO, w.pb, 0});
@@ -471,6 +488,8 @@ int build_tma(bura_plan* p, Work<T>& w) {
             want.push_back({TB_RSRC, bl, l});
             want.push_back({TB_CPRO, w.xa[l + 1], l + 1});
             want.push_back({TB_CPRO, w.xb[l + 1], l + 1});
+            want.push_back({TB_CPRO2, w.xa[l + 1], l + 1});
+            want.push_back({TB_CPRO2, w.xb[l + 1], l + 1});
         }
         bool ok = true;
         for (const Want& e : want) {
@@ -778,11 +797,13 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     const bool f32 = sizeof(T) == 4;
     const bool fine = (l == 0);
     Red none{p->partial, p->tickets, w.scal, nullptr, RED_NONE, 0};
-    Red beta{p->partial, p->tickets, w.scal, nullptr, RED_BETA, 0};
+    const Red beta = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_BETA, 0});
     if (l == w.lc) {  // the rest of the hierarchy in one kernel
         T* res = w.coarse_kind == BURA_COARSE_CLUSTER ? cluster_part(p, w, b, s) : coarse_part(p, w, b, s);
-        if (rz_fused)
+        if (rz_fused) {
             traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, res, beta, s); });
+            red_finish(p, beta, w.Kp, f32, s);
+        }
         return res;
     }
     T* A = w.xa[l];
@@ -817,6 +838,22 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
                                     f32_step(step_of(w, l, 1)), f32_ptr(w.dsh), none, s);
         });
         T* ec = vcycle<T>(p, w, l + 1, w.b[l + 1], false, s);
+        // prolongation and both post-smoothing steps in one sweep: x (= A) on a two-point halo, ec, b in;
+        // the smoothed result out to B
+        const int lc1 = l + 1 < (int)p->hl.size() ? l + 1 : l;
+        const CUtensorMap* mec2 = ec == w.xa[lc1] ? tl.find(TB_CPRO2, w.xa[lc1])
+                                : ec == w.xb[lc1] ? tl.find(TB_CPRO2, w.xb[lc1]) : nullptr;
+        const CUtensorMap* m_xa2 = tl.find(TB_HALO2, A);
+        const CUtensorMap* m_bh = tl.find(TB_HALO, b);
+        if (!p->opt.post_smooth_split && mec2 && m_xa2 && m_bh) {
+            const Red& red = rz_fused ? beta : none;
+            traced(p, K_POST2, f32, fine, vbytes<T>(p, l, 3.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
+                (void)tma_post2(tl.geo, p->nsm, *m_xa2, *mec2, *m_bh, reinterpret_cast<float*>(B),
+                                f32_step(step_of(w, l, 0, false)), f32_step(step_of(w, l, 1)), f32_ptr(w.dsh), red, s);
+            });
+            if (rz_fused) red_finish(p, beta, w.Kp, f32, s);
+            return B;
+        }
         const CUtensorMap* mec = ec == w.xa[l + 1] ? m_ca : ec == w.xb[l + 1] ? m_cb : nullptr;
         if (mec) {
             traced(p, K_PROCHEB, f32, fine, vbytes<T>(p, l, 4.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
@@ -833,6 +870,7 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
         const Red& red = rz_fused ? beta : none;
         traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0, true), s,
                [&] { cheb(B, D, A, nullptr, step_of(w, l, 1), red); });
+        if (rz_fused) red_finish(p, beta, w.Kp, f32, s);
         return A;
     }
     // pre-smoothing from a zero initial guess; the first two Chebyshev steps share one sweep
@@ -858,8 +896,10 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
         }
     }
     if (l == (int)p->hl.size() - 1) {  // coarsest level on the grid kernels: the Chebyshev solve above
-        if (rz_fused)
+        if (rz_fused) {
             traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, cur, beta, s); });
+            red_finish(p, beta, w.Kp, f32, s);
+        }
         return cur;
     }
     // coarse-grid correction: residual + restriction, then the coarser levels
@@ -879,6 +919,7 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
                [&] { cheb(cur, din, oth, dout, step_of(w, l, m, m != 0), red); });
         std::swap(cur, oth);
     }
+    if (rz_fused) red_finish(p, beta, w.Kp, f32, s);
     return cur;
 }
 
@@ -889,8 +930,8 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
     const Launch& g = w.g[0];
     const Lev& L = w.L[0];
     const bool f32 = sizeof(T) == 4;
-    Red ralpha{p->partial, p->tickets, w.scal, nullptr, RED_ALPHA, 0};
-    Red rconv{p->partial, p->tickets, w.scal, nullptr, RED_CONV, cond};
+    const Red ralpha = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_ALPHA, 0});
+    const Red rconv = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_CONV, cond});
     T* z = vcycle<T>(p, w, 0, w.r, true, s);
     const auto& tl = w.tma[0];
     traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s, [&] {
@@ -903,6 +944,7 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
         else
             Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s);
     });
+    red_finish(p, ralpha, w.Kp, f32, s);
     traced(p, K_CGUPD, f32, true, vbytes<T>(p, 0, 6.0, false), s, [&] {
         const CUtensorMap* mx = tl.on ? tl.find(TB_PLAIN, w.x) : nullptr;
         const CUtensorMap* mr = tl.on ? tl.find(TB_PLAIN, w.r) : nullptr;
@@ -917,12 +959,13 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
         else
             Ops<T>::cg_update(g, L.N, w.x, w.r, w.pa, w.pb, w.q, rconv, s);
     });
+    red_finish(p, rconv, w.Kp, f32, s);
     CKL();
     return BURA_OK;
 }
 
-// Capture the PCG loop once: a conditional WHILE node whose body is one iteration; the last block
-// of k_cg_update clears the condition when every system has converged, on breakdown, or at the cap.
+// Capture the PCG loop once: a conditional WHILE node whose body is one iteration; the k_red_finish
+// after k_cg_update clears the condition when every system has converged, on breakdown, or at the cap.
 template <class T>
 int build_graph(bura_plan* p, Work<T>& w) {
     if (w.exec) return BURA_OK;
@@ -1367,7 +1410,8 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
         !(o.cluster_size == 0 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8 ||
           o.cluster_size == 16) ||
         o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
-        o.refine > BURA_REFINE_DF || o.tma_stages < 0 || o.tma_stages > 4)
+        o.refine > BURA_REFINE_DF || o.tma_stages < 0 || o.tma_stages > 4 || o.post_smooth_split < 0 ||
+        o.post_smooth_split > 1)
         return BURA_EINVAL;
 
     bura_plan* p = new (std::nothrow) bura_plan();
@@ -1446,8 +1490,9 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     const size_t max_blocks = (size_t)nsm * std::max(8, o.blocks_per_sm);
     const size_t max_groups = (max_blocks + kRedGroup - 1) / kRedGroup;
     if ((rc = dalloc(p, &p->partial, (max_blocks + max_groups) * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->tickets, (max_groups + 1) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
-    if (cudaMemset(p->tickets, 0, (max_groups + 1) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
+    if ((rc = dalloc(p, &p->tickets, (max_groups + 2) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
+    if (cudaMemset(p->tickets, 0, (max_groups + 2) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
+    p->red_nblk = p->tickets + max_groups + 1;
     if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);

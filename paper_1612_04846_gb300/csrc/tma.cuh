@@ -28,13 +28,17 @@ enum TmaBox {
     TB_PLAIN = 1,  // (kTX, kTY): pointwise input of a fine tile
     TB_RSRC = 2,   // (2 kTXc + 5, 2 kTYc + 5): right-hand side of the fused smoothing + restriction
     TB_CPRO = 3,   // (kTX / 2 + 2, kTY / 2 + 2): coarse correction prolongated onto a fine tile + halo
-    TB_N = 4
+    TB_HALO2 = 4,  // (kTX + 4, kTY + 4): input of two stencil steps on a fine tile (two-point halo)
+    TB_CPRO2 = 5,  // (kTX / 2 + 3, kTY / 2 + 3): coarse correction prolongated onto a fine tile + 2 halo
+    TB_N = 6
 };
 inline void tma_box_dims(int kind, int* bx, int* by) {
     switch (kind) {
         case TB_HALO: *bx = kTX + 2; *by = kTY + 2; break;
         case TB_PLAIN: *bx = kTX; *by = kTY; break;
         case TB_RSRC: *bx = 2 * kTXc + 5; *by = 2 * kTYc + 5; break;
+        case TB_HALO2: *bx = kTX + 4; *by = kTY + 4; break;
+        case TB_CPRO2: *bx = kTX / 2 + 3; *by = kTY / 2 + 3; break;
         default: *bx = kTX / 2 + 2; *by = kTY / 2 + 2; break;
     }
 }
@@ -54,6 +58,12 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 // Make the initialised barriers visible to the async (TMA) proxy.
 __device__ __forceinline__ void mbar_fence_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Order this thread's generic-proxy writes to shared memory before later async-proxy (TMA) writes to
+// the same bytes; executed by the writers, before the barrier after which the TMA load is issued.
+__device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
@@ -161,6 +171,14 @@ cudaError_t tma_pre2_restrict(const TmaGeo& g, int nsm, const CUtensorMap& mb_rs
 cudaError_t tma_prolong_cheb(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo, const CUtensorMap& mec_cpro,
                              const CUtensorMap& mb, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
                              const Red& none, cudaStream_t s);
+// Both post-smoothing steps with the prolongation fused: xin = x + P ec on the tile and a two-point halo,
+// x1 = xin + d1 (first step, d1 = c2 Dinv (b - (A - dI) xin)) on a one-point halo, and on the tile the
+// second step xout = x1 + c1 d1 + c2 Dinv (b - (A - dI) x1), with b . xout when red asks for it.  Only
+// xout is stored.  x is read through a TB_HALO2 map, ec through a TB_CPRO2 map of the coarse level, b
+// through a TB_HALO map.
+cudaError_t tma_post2(const TmaGeo& g, int nsm, const CUtensorMap& mx_halo2, const CUtensorMap& mec_cpro2,
+                      const CUtensorMap& mb_halo, float* xout, ChebStepT<float> cs0, ChebStepT<float> cs1,
+                      const float* dsh, const Red& red, cudaStream_t s);
 // CG update x += alpha p, r -= alpha q with r.r (RED_CONV) from TMA-staged tiles of x, r, p, q (pointwise);
 // the direction is pa or pb by the Scal parity, as in the grid kernel.  False from tma_cg_fits when the
 // ring of at least two stages does not fit.

@@ -192,6 +192,30 @@ def test_mixed_solve_within_tolerance(lib, shape, alpha, k, tol, sweeps):
     assert err <= tol, (err, st)
 
 
+@pytest.mark.parametrize("shape,alpha,k", [((1023, 1023), 0.5, 7), ((255, 255), 0.25, 3), ((511, 255), 0.75, 10),
+                                           ((127, 63), 0.5, 12), ((383, 129), 0.9, 7)])
+def test_fused_post_smoothing_matches_two_sweeps(lib, shape, alpha, k):
+    """The prolongation and both post-smoothing steps as one TMA sweep (the first step recomputed on a
+    one-point halo of every tile) against the same as two sweeps.  Every point gets the same operations,
+    but r.z is summed by a sweep with another CTA count, so its FP32 partial sums group differently;
+    beta reaches the kernels as an FP32 copy, which mostly absorbs that, not always.  A preconditioner
+    fault would change the iteration counts or the iterates at the solve tolerance: both must agree,
+    the solutions to 1e-8 (observed: bit-identical or within 1e-9), and both meet the oracle.  k = 3, 7,
+    10, 12 give 4, 8, 12 and 16 FP32 values per point (16 on 3-D tensor maps); every grid has ragged
+    last tiles."""
+    nps = _np_shape(shape)
+    f = W.rhs_uniform(nps, 5)
+    tol = 1e-6
+    u1, st1, rc1, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED, post_smooth_split=0)
+    u2, st2, rc2, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED, post_smooth_split=1)
+    assert rc1 == lib.BURA_OK and rc2 == lib.BURA_OK
+    assert st1["iters"] == st2["iters"] and st1["outer"] == st2["outer"]
+    assert _rel(u1, u2) <= 1e-8
+    ref = tables.entry(alpha, k)
+    ur = exact.bura_value(nps, f, ref["c"], ref["d"])
+    assert _rel(u1, ur) <= tol and _rel(u2, ur) <= tol
+
+
 def test_mixed_variable_3d_within_tolerance(lib):
     shape = (31, 31, 31)
     nps = _np_shape(shape)
