@@ -17,8 +17,9 @@ __global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const 
     for (int q = 0; q < W; ++q) d[q] = dsh[off + q];
     Accum<double> acc;
     if constexpr (!VAR) {
-        // constant coefficients: (A - d_j I) v = (diag - d_j) v_c - wx (v_w + v_e) - wy (v_s + v_n) [- wz (...)],
-        // 6 (2-D) FP64 operations per value instead of 7 (GB300's FP64 rate bounds this kernel)
+        // constant coefficients: r = f - (diag - d_j) v_c + wx (v_w + v_e) + wy (v_s + v_n) [+ wz (...)] as
+        // three fused multiply-adds on f after the two pair sums: 5 (2-D) FP64 operations per value, plus
+        // one for ||r_j||^2 (GB300's FP64 rate bounds this kernel)
         const double diag = 2.0 * (L.wx + L.wy + (DIM == 3 ? L.wz : 0.0));
         double c0[W];
         for (int q = 0; q < W; ++q) c0[q] = diag - d[q];
@@ -45,11 +46,11 @@ __global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const 
             [&](int P, St& st) {
                 double rv[W];
                 for (int q = 0; q < W; ++q) {
-                    double t = c0[q] * st.xc[q];
-                    t = fma(-L.wx, st.sx[q], t);
-                    t = fma(-L.wy, st.sy[q], t);
-                    if (DIM == 3) t = fma(-L.wz, st.sz[q], t);
-                    rv[q] = st.fv - t;
+                    double t = fma(-c0[q], st.xc[q], st.fv);
+                    t = fma(L.wx, st.sx[q], t);
+                    t = fma(L.wy, st.sy[q], t);
+                    if (DIM == 3) t = fma(L.wz, st.sz[q], t);
+                    rv[q] = t;
                 }
                 vst(r + (size_t)P * Kp + off, rv);
                 acc.add(rv, rv);

@@ -69,6 +69,8 @@ constexpr size_t kSmemPerSM = 228 * 1024;    // shared memory of an SM
 constexpr size_t kSmemPerCTA = 226 * 1024;   // largest dynamic allocation of one CTA (the 227 KB opt-in limit
                                              // covers static shared memory too: keep 1 KB for it)
 constexpr size_t kSmemReserved = 1024;       // per CTA, by the system
+constexpr int kPost2CtasPerSM = 2;           // the fused post-smoothing ring + scratch: 2 CTAs per SM (FP32,
+                                             // 8 values per point), so its registers may be more
 
 // The tile pipeline.  issue(stage, tile, bar) is called by thread 0 only; compute(stage, tile) by
 // every thread.  Returns false (after draining the copies in flight and flagging the fault) when a
@@ -575,7 +577,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
 // hold zero (Dirichlet).  Traffic per tile: x, ec, b in, xout out, against x, ec, b in and x1, d1 out,
 // then x1, d1, b in and xout out for the two-kernel form.
 template <int C>
-__global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
+__global__ void __launch_bounds__(kTmaThreads, kPost2CtasPerSM)
     k_post2_tma(const __grid_constant__ TmaMaps3 mp, TmaGeo g, float* __restrict__ xout, ChebStepT<float> cs0,
                 ChebStepT<float> cs1, const float* __restrict__ dsh, Red red) {
     pdl_wait();
@@ -648,48 +650,98 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMaxCtasPerSM)
             }
             fence_proxy_async_smem();  // the x stage is refilled by TMA after the tile
             __syncthreads();
-            // (2) first step on the one-point halo region
-            for (int p = threadIdx.y; p < kHaloPts; p += blockDim.y) {
-                const int hy = p / (kTX + 2), hx = p - hy * (kTX + 2);
-                const int fi = x0 - 1 + hx, fj = y0 - 1 + hy;
-                float xo[4] = {0.f, 0.f, 0.f, 0.f};
-                if (fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny) {
-                    const int hidx = ((hy + 1) * kH2X + hx + 1) * Kp + off;
-                    float xc[4], Ax[4], bv[4], dv[4];
-                    stencil_tile<kH2X>(g, hidx, [&](int h, float (&o)[4]) { ld4(X + h, o); }, xc, Ax);
-                    ld4(B + p * Kp + off, bv);
-                    for (int v = 0; v < 4; ++v) {
-                        const float res = bv[v] - fmaf(-d[v], xc[v], Ax[v]);
-                        const float gg = c20[v] * res;
-                        dv[v] = fmaf(0.f, 0.f, gg);
-                        xo[v] = xc[v] + dv[v];
+            // (2) first step on the one-point halo region, by vertical pairs of points (rows 2m, 2m + 1 of
+            // the region): the pair shares its column of four values and its index arithmetic
+            for (int q = threadIdx.y; q < (kTX + 2) * ((kTY + 2) / 2); q += blockDim.y) {
+                const int pr = q / (kTX + 2), hx = q - pr * (kTX + 2);
+                const int hy0 = 2 * pr;
+                const int fi = x0 - 1 + hx, fj0 = y0 - 1 + hy0;
+                // x at 2-halo rows hy0 .. hy0 + 3 of column hx + 1, and the left / right neighbours of the pair
+                const int c0 = (hy0 * kH2X + hx + 1) * Kp + off;
+                float up[4], m0[4], m1[4], dn[4], l0[4], r0[4], l1[4], r1[4];
+                ld4(X + c0, up);
+                ld4(X + c0 + kH2X * Kp, m0);
+                ld4(X + c0 + 2 * kH2X * Kp, m1);
+                ld4(X + c0 + 3 * kH2X * Kp, dn);
+                ld4(X + c0 + kH2X * Kp - Kp, l0);
+                ld4(X + c0 + kH2X * Kp + Kp, r0);
+                ld4(X + c0 + 2 * kH2X * Kp - Kp, l1);
+                ld4(X + c0 + 2 * kH2X * Kp + Kp, r1);
+                const bool in_x = fi >= 0 && fi < g.nx;
+                for (int j = 0; j < 2; ++j) {
+                    const int hy = hy0 + j, fj = fj0 + j;
+                    const float(&xc)[4] = j ? m1 : m0;
+                    const float(&xl)[4] = j ? l1 : l0;
+                    const float(&xr)[4] = j ? r1 : r0;
+                    const float(&xu)[4] = j ? m0 : up;
+                    const float(&xd)[4] = j ? dn : m1;
+                    float xo[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (in_x && fj >= 0 && fj < g.ny) {
+                        const float diag = g.wx + g.wx + g.wy + g.wy;
+                        float bv[4], dv[4];
+                        ld4(B + (hy * (kTX + 2) + hx) * Kp + off, bv);
+                        for (int v = 0; v < 4; ++v) {
+                            float a = diag * xc[v];
+                            a = fmaf(-g.wx, xl[v], a);
+                            a = fmaf(-g.wx, xr[v], a);
+                            a = fmaf(-g.wy, xu[v], a);
+                            a = fmaf(-g.wy, xd[v], a);
+                            const float res = bv[v] - fmaf(-d[v], xc[v], a);
+                            const float gg = c20[v] * res;
+                            dv[v] = fmaf(0.f, 0.f, gg);
+                            xo[v] = xc[v] + dv[v];
+                        }
+                        if (hx >= 1 && hx <= kTX && hy >= 1 && hy <= kTY)
+                            st4(D1 + ((hy - 1) * kTX + hx - 1) * Kp + off, dv);
                     }
-                    if (hx >= 1 && hx <= kTX && hy >= 1 && hy <= kTY)
-                        st4(D1 + ((hy - 1) * kTX + hx - 1) * Kp + off, dv);
+                    st4(X1 + (hy * (kTX + 2) + hx) * Kp + off, xo);
                 }
-                st4(X1 + p * Kp + off, xo);
             }
             __syncthreads();
-            // (3) second step on the tile
-            for (int p = threadIdx.y; p < kTilePts; p += blockDim.y) {
-                const int ly = p / kTX, lx = p - ly * kTX;
-                const int gx = x0 + lx, gy = y0 + ly;
-                if (gx >= g.nx || gy >= g.ny) continue;
-                const int hidx = ((ly + 1) * (kTX + 2) + lx + 1) * Kp + off;
-                float xc[4], Ax[4], bv[4], dv[4];
-                stencil_tile(g, hidx, [&](int h, float (&o)[4]) { ld4(X1 + h, o); }, xc, Ax);
-                ld4(B + hidx, bv);
-                ld4(D1 + p * Kp + off, dv);
-                float xo[4];
-                for (int v = 0; v < 4; ++v) {
-                    const float res = bv[v] - fmaf(-d[v], xc[v], Ax[v]);
-                    const float gg = c21[v] * res;
-                    dv[v] = fmaf(c11[v], dv[v], gg);
-                    xo[v] = xc[v] + dv[v];
+            // (3) second step on the tile, by vertical pairs of points
+            for (int q = threadIdx.y; q < kTX * (kTY / 2); q += blockDim.y) {
+                const int pr = q / kTX, lx = q - pr * kTX;
+                const int ly0 = 2 * pr;
+                const int gx = x0 + lx, gy0 = y0 + ly0;
+                if (gx >= g.nx || gy0 >= g.ny) continue;
+                // x1 at 1-halo rows ly0 .. ly0 + 3 of column lx + 1, and the neighbours of the pair
+                const int c0 = (ly0 * (kTX + 2) + lx + 1) * Kp + off;
+                const int sy = (kTX + 2) * Kp;
+                float up[4], m0[4], m1[4], dn[4], l0[4], r0[4], l1[4], r1[4];
+                ld4(X1 + c0, up);
+                ld4(X1 + c0 + sy, m0);
+                ld4(X1 + c0 + 2 * sy, m1);
+                ld4(X1 + c0 + 3 * sy, dn);
+                ld4(X1 + c0 + sy - Kp, l0);
+                ld4(X1 + c0 + sy + Kp, r0);
+                ld4(X1 + c0 + 2 * sy - Kp, l1);
+                ld4(X1 + c0 + 2 * sy + Kp, r1);
+                for (int j = 0; j < 2; ++j) {
+                    const int gy = gy0 + j;
+                    if (gy >= g.ny) break;
+                    const float(&xc)[4] = j ? m1 : m0;
+                    const float(&xl)[4] = j ? l1 : l0;
+                    const float(&xr)[4] = j ? r1 : r0;
+                    const float(&xu)[4] = j ? m0 : up;
+                    const float(&xd)[4] = j ? dn : m1;
+                    const float diag = g.wx + g.wx + g.wy + g.wy;
+                    float bv[4], dv[4], xo[4];
+                    ld4(B + c0 + (1 + j) * sy, bv);
+                    ld4(D1 + ((ly0 + j) * kTX + lx) * Kp + off, dv);
+                    for (int v = 0; v < 4; ++v) {
+                        float a = diag * xc[v];
+                        a = fmaf(-g.wx, xl[v], a);
+                        a = fmaf(-g.wx, xr[v], a);
+                        a = fmaf(-g.wy, xu[v], a);
+                        a = fmaf(-g.wy, xd[v], a);
+                        const float res = bv[v] - fmaf(-d[v], xc[v], a);
+                        const float gg = c21[v] * res;
+                        dv[v] = fmaf(c11[v], dv[v], gg);
+                        xo[v] = xc[v] + dv[v];
+                    }
+                    st4(xout + ((size_t)gy * g.nx + gx) * Kp + off, xo);
+                    if (dot) acc.add(bv, xo);
                 }
-                const size_t gidx = ((size_t)gy * g.nx + gx) * Kp + off;
-                st4(xout + gidx, xo);
-                if (dot) acc.add(bv, xo);
             }
         });
     pdl_trigger();
@@ -875,11 +927,13 @@ int ring_stages(const TmaGeo& g, int kind) {
     return S;
 }
 
-// Persistent grid: as many CTAs per SM as their rings fit in shared memory (at most kTmaMaxCtasPerSM).
+// Persistent grid: as many CTAs per SM as their rings fit in shared memory (at most kTmaMaxCtasPerSM, or
+// kPost2CtasPerSM for the fused post-smoothing, whose launch bounds allow more registers).
 int tma_blocks(const TmaGeo& g, int Kp, int nsm, int kind, int S) {
     const size_t smem = dyn_smem(kind, Kp, S) + kRingSlack + kSmemReserved + 64;  // + static
     int per_sm = (int)(kSmemPerSM / smem);
-    per_sm = per_sm < 1 ? 1 : (per_sm > kTmaMaxCtasPerSM ? kTmaMaxCtasPerSM : per_sm);
+    const int cap = kind == TK_POST2 ? kPost2CtasPerSM : kTmaMaxCtasPerSM;  // the launch bounds' registers
+    per_sm = per_sm < 1 ? 1 : (per_sm > cap ? cap : per_sm);
     const int nt = kind == TK_PRE2R ? g.nctiles : g.ntiles;
     return nt < nsm * per_sm ? nt : nsm * per_sm;
 }
