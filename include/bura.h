@@ -28,6 +28,8 @@
 #ifndef BURA_H
 #define BURA_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -125,6 +127,7 @@ typedef struct {
     double err_bound;                /* sum_j c_j ||r_j|| / ((lambda_lo - d_j) ||f||): bound on ||u - u_r|| / ||f|| */
     double lambda_lo;                /* lower bound on lambda_min(A) used by the stopping test */
     long long launches;              /* CUDA kernels launched by the last solve */
+    size_t device_bytes;             /* device memory the plan holds (all its allocations) */
 } bura_stats;
 
 /* Per-kernel timing of the fine-level kernels (see bura_set_profiling). */
@@ -239,6 +242,20 @@ int bura_get_profile(const bura_plan* plan, int max_entries, bura_kernel_prof* o
 int bura_residual_norms_noalloc(const bura_grid* grid, int nsys, const double* d, const double* f,
                                 const double* V, double* rr, void* stream);
 
+/*
+ * Move the plan to another fractional power alpha in (0, 1), keeping its grid, operator, k and
+ * options: recomputes the 1-BURA coefficients (Algorithm 1's best approximation, eq. (simplified)
+ * partial fractions) and every table that depends on the shifts d_j (smoother coefficients, coarse
+ * inverses, weights c_j), in the plan's existing device buffers.  The multigrid hierarchy, the
+ * tensor maps and the captured PCG graph are kept, so this costs a host Remez solve and a few small
+ * copies instead of a setup.  The result of a later solve equals that of a plan set up at alpha.
+ * Waits for the plan's last solve to finish on the device; the caller must not run a solve of
+ * the same plan concurrently.
+ * Errors: BURA_EINVAL, BURA_EREMEZ, BURA_ECUDA (the plan keeps its previous alpha unless the
+ * error is BURA_ECUDA from a copy).
+ */
+int bura_retarget(bura_plan* plan, double alpha);
+
 /* Frees every device and host resource of the plan (NULL is accepted). */
 int bura_destroy(bura_plan* plan);
 
@@ -259,6 +276,68 @@ int bura_destroy(bura_plan* plan);
  * other error of any problem, or BURA_EINVAL (null pointers, n < 0, a plan listed twice). */
 int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
                      int nworkers, int* status);
+
+/*
+ * Solve server: a continuous-batching front end for many independent requests (grids, coefficient
+ * fields, alpha, k of their own) arriving over time.  Worker threads, each with its own CUDA stream,
+ * take requests in arrival order and serve each from a pool of resident plans: a plan of the same
+ * class (grid, coefficient field, k) that is idle is reused, moved to the request's alpha with
+ * bura_retarget if needed; otherwise a plan is set up, after evicting idle plans (least recently
+ * used first) while the resident plans would exceed the device-memory budget, or after waiting for
+ * one to become idle.  Requests of one class run concurrently on separate plans.  f and u are HOST
+ * arrays owned by the caller until bura_server_wait has reported the request done; the copies and
+ * the solve are stream-ordered on the worker's stream.  All functions are thread-safe.
+ */
+typedef struct bura_server bura_server;
+
+typedef struct {
+    int workers;          /* worker threads (streams); 0 = 8 */
+    size_t mem_budget;    /* device bytes the resident plans may hold; 0 = 80 % of the free memory at creation */
+    bura_options plan;    /* options of every plan the server sets up */
+} bura_server_options;
+
+typedef struct {
+    bura_grid grid;
+    const double* const* faces;  /* BURA_COEF_FACES: dim face arrays as for bura_setup (caller-owned until done) */
+    unsigned long long field;    /* caller's id of the coefficient field: requests with the same grid and field
+                                    share plans (ignored for BURA_COEF_CONSTANT) */
+    double alpha;                /* in (0, 1) */
+    int k;                       /* 1 .. BURA_MAX_K */
+    double tol;                  /* as for bura_solve */
+    const double* f;             /* HOST, N doubles */
+    double* u;                   /* HOST, N doubles, written when the request is done */
+} bura_request;
+
+typedef struct {
+    int status;          /* the solve's status (BURA_OK, BURA_ENOCONV, ...) */
+    int built;           /* 1: a plan was set up for this request */
+    int retargeted;      /* 1: a resident plan was moved to this request's alpha */
+    int iters, outer;    /* PCG iterations and refinement steps of the solve */
+    double err_bound;    /* as in bura_stats */
+    double queue_ms;     /* submission -> a worker took the request */
+    double service_ms;   /* worker took it -> u written (plan setup or retarget, copies, solve) */
+    double total_ms;     /* submission -> done */
+} bura_request_info;
+
+typedef struct {
+    long long submitted, completed, builds, retargets, reuses, evictions;
+    int resident_plans;
+    size_t resident_bytes;
+    size_t mem_budget;
+} bura_server_stats;
+
+void bura_server_default_options(bura_server_options* opt);
+/* Errors: BURA_EINVAL, BURA_ECUDA (no device), BURA_ENOMEM. */
+int bura_server_create(const bura_server_options* opt, bura_server** out);
+/* Queue one request; *id identifies it for bura_server_wait.  Errors: BURA_EINVAL (checked here:
+ * grid, alpha, k, tol, pointers), BURA_ENOMEM. */
+int bura_server_submit(bura_server* srv, const bura_request* req, unsigned long long* id);
+/* Wait up to timeout_s seconds (< 0: no limit) for request id.  BURA_OK: done, *info filled and the
+ * request forgotten; BURA_ETIMEOUT: not done yet; BURA_EINVAL: unknown id. */
+int bura_server_wait(bura_server* srv, unsigned long long id, double timeout_s, bura_request_info* info);
+int bura_server_get_stats(bura_server* srv, bura_server_stats* stats);
+/* Serves every queued request, joins the workers and frees every plan (NULL is accepted). */
+int bura_server_destroy(bura_server* srv);
 
 /* Static description of a status code. */
 const char* bura_strerror(int status);

@@ -42,14 +42,42 @@ class bura_stats(C.Structure):
     _fields_ = [("Lambda", C.c_double), ("E", C.c_double), ("k", C.c_int), ("levels", C.c_int),
                 ("iters", C.c_int), ("outer", C.c_int), ("shift_iters", C.c_int * (BURA_MAX_K + 1)),
                 ("rel_res", C.c_double * (BURA_MAX_K + 1)), ("err_bound", C.c_double),
-                ("lambda_lo", C.c_double), ("launches", C.c_longlong)]
+                ("lambda_lo", C.c_double), ("launches", C.c_longlong), ("device_bytes", C.c_size_t)]
 
     def to_dict(self):
         k = self.k
         return {"Lambda": self.Lambda, "E": self.E, "k": k, "levels": self.levels, "iters": self.iters,
                 "outer": self.outer, "shift_iters": list(self.shift_iters)[: k + 1],
                 "rel_res": list(self.rel_res)[: k + 1], "err_bound": self.err_bound, "lambda_lo": self.lambda_lo,
-                "launches": self.launches}
+                "launches": self.launches, "device_bytes": self.device_bytes}
+
+
+class bura_server_options(C.Structure):
+    _fields_ = [("workers", C.c_int), ("mem_budget", C.c_size_t), ("plan", bura_options)]
+
+
+class bura_request(C.Structure):
+    _fields_ = [("grid", bura_grid), ("faces", C.POINTER(C.POINTER(C.c_double))), ("field", C.c_ulonglong),
+                ("alpha", C.c_double), ("k", C.c_int), ("tol", C.c_double), ("f", C.POINTER(C.c_double)),
+                ("u", C.POINTER(C.c_double))]
+
+
+class bura_request_info(C.Structure):
+    _fields_ = [("status", C.c_int), ("built", C.c_int), ("retargeted", C.c_int), ("iters", C.c_int),
+                ("outer", C.c_int), ("err_bound", C.c_double), ("queue_ms", C.c_double), ("service_ms", C.c_double),
+                ("total_ms", C.c_double)]
+
+    def to_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class bura_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("completed", C.c_longlong), ("builds", C.c_longlong),
+                ("retargets", C.c_longlong), ("reuses", C.c_longlong), ("evictions", C.c_longlong),
+                ("resident_plans", C.c_int), ("resident_bytes", C.c_size_t), ("mem_budget", C.c_size_t)]
+
+    def to_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class bura_kernel_prof(C.Structure):
@@ -94,6 +122,14 @@ def _lib():
         L.bura_solve_batch.argtypes = [C.POINTER(P), C.POINTER(P), C.POINTER(P), I, D, I, C.POINTER(I)]
         L.bura_set_profiling.argtypes = [P, I]
         L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
+        L.bura_retarget.argtypes = [P, D]
+        L.bura_server_default_options.argtypes = [C.POINTER(bura_server_options)]
+        L.bura_server_default_options.restype = None
+        L.bura_server_create.argtypes = [C.POINTER(bura_server_options), C.POINTER(P)]
+        L.bura_server_submit.argtypes = [P, C.POINTER(bura_request), C.POINTER(C.c_ulonglong)]
+        L.bura_server_wait.argtypes = [P, C.c_ulonglong, D, C.POINTER(bura_request_info)]
+        L.bura_server_get_stats.argtypes = [P, C.POINTER(bura_server_stats)]
+        L.bura_server_destroy.argtypes = [P]
         L.bura_strerror.argtypes = [I]
         L.bura_strerror.restype = C.c_char_p
         L.bura_last_cuda_error.argtypes = []
@@ -101,7 +137,8 @@ def _lib():
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
                      "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-                     "bura_solve_batch"):
+                     "bura_solve_batch", "bura_retarget", "bura_server_create", "bura_server_submit",
+                     "bura_server_wait", "bura_server_get_stats", "bura_server_destroy"):
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -201,6 +238,109 @@ def bura_solve_batch(plans, fs, us, tol, nworkers=0):
     return list(st)[:n]
 
 
+def bura_retarget(plan, alpha):
+    """Move the plan to another alpha (new rational approximation and shift tables, same hierarchy)."""
+    return _check(_lib().bura_retarget(plan, float(alpha)), "bura_retarget")
+
+
+def _grid_of(shape, faces):
+    g = bura_grid()
+    g.dim = len(shape)
+    for i, n in enumerate(shape[:3]):
+        g.n[i] = int(n)
+    g.coef_kind = BURA_COEF_CONSTANT if faces is None else BURA_COEF_FACES
+    return g
+
+
+def bura_server_default_options():
+    o = bura_server_options()
+    _lib().bura_server_default_options(C.byref(o))
+    return o
+
+
+def bura_server_create(options=None):
+    opt = options if options is not None else bura_server_default_options()
+    srv = C.c_void_p()
+    _check(_lib().bura_server_create(C.byref(opt), C.byref(srv)), "bura_server_create")
+    return srv
+
+
+def bura_server_submit(srv, req):
+    """Queue a filled bura_request; returns its id.  The arrays it points to must stay alive until
+    bura_server_wait reports it done (BuraServer keeps them)."""
+    rid = C.c_ulonglong()
+    _check(_lib().bura_server_submit(srv, C.byref(req), C.byref(rid)), "bura_server_submit")
+    return rid.value
+
+
+def bura_server_wait(srv, rid, timeout=-1.0):
+    """The request's bura_request_info as a dict once done; None if not done within timeout seconds."""
+    info = bura_request_info()
+    rc = _check(_lib().bura_server_wait(srv, C.c_ulonglong(rid), float(timeout), C.byref(info)),
+                "bura_server_wait", allow=(BURA_ETIMEOUT,))
+    return None if rc == BURA_ETIMEOUT else info.to_dict()
+
+
+def bura_server_get_stats(srv):
+    st = bura_server_stats()
+    _check(_lib().bura_server_get_stats(srv, C.byref(st)), "bura_server_get_stats")
+    return st.to_dict()
+
+
+def bura_server_destroy(srv):
+    return _check(_lib().bura_server_destroy(srv), "bura_server_destroy")
+
+
+class BuraServer:
+    """The solve server with host numpy arrays: submit() keeps f, u and the faces alive until wait()."""
+
+    def __init__(self, workers=0, mem_budget=0, options=None):
+        o = bura_server_default_options()
+        o.workers = int(workers)
+        o.mem_budget = int(mem_budget)
+        if options is not None:
+            o.plan = options
+        self.srv = bura_server_create(o)
+        self._keep = {}
+
+    def submit(self, shape, alpha, k, f, u, tol, faces=None, field=0):
+        req = bura_request()
+        req.grid = _grid_of(shape, faces)
+        keep = [f, u]
+        if faces is not None:
+            arr = (C.POINTER(C.c_double) * len(faces))()
+            for i, a in enumerate(faces):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                arr[i] = _hptr(a)
+            keep.append(arr)
+            req.faces = C.cast(arr, C.POINTER(C.POINTER(C.c_double)))
+        req.field = int(field)
+        req.alpha = float(alpha)
+        req.k = int(k)
+        req.tol = float(tol)
+        req.f = _hptr(f)
+        req.u = _hptr(u)
+        rid = bura_server_submit(self.srv, req)
+        self._keep[rid] = (keep, req)
+        return rid
+
+    def wait(self, rid, timeout=-1.0):
+        info = bura_server_wait(self.srv, rid, timeout)
+        if info is not None:
+            self._keep.pop(rid, None)
+        return info
+
+    def stats(self):
+        return bura_server_get_stats(self.srv)
+
+    def close(self):
+        if self.srv is not None:
+            bura_server_destroy(self.srv)
+            self.srv = None
+            self._keep.clear()
+
+
 def bura_solve_host(plan, f, u, tol, stream=None):
     """Same with host numpy arrays (copies inside the call)."""
     return _check(_lib().bura_solve_host(plan, _hptr(f), _hptr(u), float(tol), _stream(stream)),
@@ -267,4 +407,6 @@ def bura_destroy(plan):
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
             "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-            "bura_last_cuda_error", "bura_solve_batch"]
+            "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_server_default_options",
+            "bura_server_create", "bura_server_submit", "bura_server_wait", "bura_server_get_stats",
+            "bura_server_destroy"]

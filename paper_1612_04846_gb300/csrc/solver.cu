@@ -157,6 +157,8 @@ struct bura_plan {
     double* fdev = nullptr;     // host-solve staging
     double* udev = nullptr;
     std::vector<void*> allocs;
+    size_t dbytes = 0;           // sum of the allocations
+    cudaEvent_t done = nullptr;  // recorded after the last kernel of every solve (bura_retarget waits on it)
     bura_stats st{};
     Tracer tr;
     cudaStream_t cap = nullptr;  // private stream used only to capture the PCG loop graphs
@@ -189,6 +191,7 @@ int dalloc(bura_plan* p, P** ptr, size_t bytes) {
         return e == cudaErrorMemoryAllocation ? BURA_ENOMEM : BURA_ECUDA;
     }
     p->allocs.push_back(q);
+    p->dbytes += bytes > 0 ? bytes : 16;
     *ptr = reinterpret_cast<P*>(q);
     return BURA_OK;
 }
@@ -514,6 +517,45 @@ int build_tma(bura_plan* p, Work<T>& w) {
     return BURA_OK;
 }
 
+// The shift-dependent tables of a work set, written into its existing buffers: per level the Chebyshev
+// coefficients c1, c2 (deg x Kp), the shifts, and the dense inverses of the exact level.  Their sizes
+// do not depend on the shifts (the coarsest degree depends on d_0 = 0 only), so a plan can be moved
+// to another alpha without reallocating and without recapturing its PCG graph, whose kernels read
+// these buffers.
+template <class T>
+int upload_tables(bura_plan* p, Work<T>& w) {
+    const int nlev = (int)p->hl.size();
+    for (int l = 0; l < (int)w.c1.size(); ++l) {
+        if (!w.c1[l]) continue;
+        const HostLevel& h = p->hl[l];
+        const bool coarsest = (l == nlev - 1);
+        const int deg = w.deg[l];
+        std::vector<std::vector<double>> C1, C2;
+        cheb_tables(h, p->var, p->d, p->K, w.Kp, deg, p->opt.smoother_ratio, coarsest, C1, C2);
+        if (coarsest && h.N == 1) {  // exact solve of the 1x1 system: x = b / (diag - d)
+            for (int s = 0; s < p->K; ++s) C2[0][s] = p->var ? 1.0 : 1.0 / (h.amax - p->d[s]);
+        }
+        std::vector<T> t1((size_t)deg * w.Kp), t2((size_t)deg * w.Kp);
+        for (int m = 0; m < deg; ++m)
+            for (int s = 0; s < w.Kp; ++s) {
+                t1[(size_t)m * w.Kp + s] = (T)C1[m][s];
+                t2[(size_t)m * w.Kp + s] = (T)C2[m][s];
+            }
+        CK(cudaMemcpy(w.c1[l], t1.data(), t1.size() * sizeof(T), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(w.c2[l], t2.data(), t2.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    std::vector<T> dsht(KMAXP, T(0));
+    for (int s = 0; s < p->K; ++s) dsht[s] = (T)p->d[s];
+    CK(cudaMemcpy(w.dsh, dsht.data(), KMAXP * sizeof(T), cudaMemcpyHostToDevice));
+    if (w.minv) {
+        std::vector<double> inv;
+        dense_inverses(p->hl[w.le], p->dim, p->var, p->d, p->K, w.Kp, inv);
+        const std::vector<T> tv(inv.begin(), inv.end());
+        CK(cudaMemcpy(w.minv, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    return BURA_OK;
+}
+
 // full = false: only what the mixed path's FP64 refinement and bura_apply_shifted use of the FP64 work
 // (level-0 launch shape, geometry and face coefficients, the shifts); no hierarchy, no PCG buffers.
 template <class T>
@@ -569,28 +611,13 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
         int deg = p->opt.smoother_degree;
         if (coarsest) deg = h.N == 1 ? 1 : (p->opt.coarse_degree > 0 ? p->opt.coarse_degree : coarse_degree_auto(h, p->d[0]));
         w.deg[l] = deg;
-        std::vector<std::vector<double>> C1, C2;
-        cheb_tables(h, p->var, p->d, p->K, w.Kp, deg, p->opt.smoother_ratio, coarsest, C1, C2);
-        if (coarsest && h.N == 1) {  // exact solve of the 1x1 system: x = b / (diag - d)
-            for (int s = 0; s < p->K; ++s) C2[0][s] = p->var ? 1.0 : 1.0 / (h.amax - p->d[s]);
-        }
-        std::vector<double> f1((size_t)deg * w.Kp), f2((size_t)deg * w.Kp);
-        for (int m = 0; m < deg; ++m)
-            for (int s = 0; s < w.Kp; ++s) {
-                f1[(size_t)m * w.Kp + s] = C1[m][s];
-                f2[(size_t)m * w.Kp + s] = C2[m][s];
-            }
-        const std::vector<T> t1(f1.begin(), f1.end()), t2(f2.begin(), f2.end());
-        CA(dalloc(p, &w.c1[l], t1.size() * sizeof(T)));
-        CA(dalloc(p, &w.c2[l], t2.size() * sizeof(T)));
-        CK(cudaMemcpy(w.c1[l], t1.data(), t1.size() * sizeof(T), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(w.c2[l], t2.data(), t2.size() * sizeof(T), cudaMemcpyHostToDevice));
+        // the Chebyshev tables (deg x Kp each) depend on the shifts: filled by upload_tables
+        CA(dalloc(p, &w.c1[l], (size_t)deg * w.Kp * sizeof(T)));
+        CA(dalloc(p, &w.c2[l], (size_t)deg * w.Kp * sizeof(T)));
     }
     if (!full) {
-        std::vector<T> dsht(KMAXP, T(0));
-        for (int s = 0; s < p->K; ++s) dsht[s] = (T)p->d[s];
         CA(dalloc(p, &w.dsh, KMAXP * sizeof(T)));
-        CK(cudaMemcpy(w.dsh, dsht.data(), KMAXP * sizeof(T), cudaMemcpyHostToDevice));
+        CA(upload_tables<T>(p, w));
         return BURA_OK;  // w.ready stays false: this work never runs a PCG
     }
     // the first level with at most kExactPoints points is solved exactly (dense inverses); the levels
@@ -628,12 +655,9 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
         }
     }
     if (w.lc < 0) w.le = -1;  // the dense solve lives in the coarse kernel only
-    if (w.le >= 0) {
-        std::vector<double> inv;
-        dense_inverses(p->hl[w.le], p->dim, p->var, p->d, p->K, w.Kp, inv);
-        std::vector<T> tv(inv.begin(), inv.end());
-        CA(dalloc(p, &w.minv, tv.size() * sizeof(T)));
-        CK(cudaMemcpy(w.minv, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (w.le >= 0) {  // [row][col][Kp] dense inverses of the exact level, filled by upload_tables
+        const size_t n = (size_t)p->hl[w.le].N;
+        CA(dalloc(p, &w.minv, n * n * w.Kp * sizeof(T)));
     }
     w.gc.Kp = w.Kp;
     w.gc.C = w.C;
@@ -654,11 +678,8 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
     CA(dalloc(p, &w.pa, vb0));
     CA(dalloc(p, &w.pb, vb0));
     CA(dalloc(p, &w.q, vb0));
-    std::vector<double> dsh(KMAXP, 0.0);
-    for (int s = 0; s < p->K; ++s) dsh[s] = p->d[s];
-    const std::vector<T> dsht(dsh.begin(), dsh.end());
     CA(dalloc(p, &w.dsh, KMAXP * sizeof(T)));
-    CK(cudaMemcpy(w.dsh, dsht.data(), KMAXP * sizeof(T), cudaMemcpyHostToDevice));
+    CA(upload_tables<T>(p, w));
     CA(dalloc(p, &w.scal, sizeof(Scal)));
     CK(cudaMemset(w.scal, 0, sizeof(Scal)));
     CA(build_tma(p, w));
@@ -1312,6 +1333,21 @@ void split_df(double x, float* hi, float* lo) {
 }
 
 // Buffers and coefficient tables of the double-float refinement of the mixed path.
+// The double-float refinement's per-system tables (KMAXP entries each, zero in the padding): diag - d_j,
+// d_j, c_j as (hi, lo) pairs, written into the buffer that starts at dfop.ch.
+int upload_df_tables(bura_plan* p) {
+    const HostLevel& h = p->hl[0];
+    std::vector<float> t(6 * KMAXP, 0.f);
+    const double diag = 2.0 * (h.w[0] + h.w[1] + (p->dim == 3 ? h.w[2] : 0.0));
+    for (int j = 0; j < p->K; ++j) {
+        split_df(diag - p->d[j], &t[j], &t[KMAXP + j]);
+        split_df(p->d[j], &t[2 * KMAXP + j], &t[3 * KMAXP + j]);
+        split_df(p->c[j], &t[4 * KMAXP + j], &t[5 * KMAXP + j]);
+    }
+    CK(cudaMemcpy(const_cast<float*>(p->dfop.ch), t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return BURA_OK;
+}
+
 int build_df(bura_plan* p) {
     const long long N = p->hl[0].N;
     const int Kp = p->w32.Kp;
@@ -1325,23 +1361,15 @@ int build_df(bura_plan* p) {
     const HostLevel& h = p->hl[0];
     DfOpHost& op = p->dfop;
     for (int a = 0; a < 3; ++a) split_df(a < p->dim ? h.w[a] : 0.0, &op.w[a][0], &op.w[a][1]);
-    // per-system tables (KMAXP entries, zero in the padding): diag - d_j, d_j, c_j
-    std::vector<float> t(6 * KMAXP, 0.f);
-    const double diag = 2.0 * (h.w[0] + h.w[1] + (p->dim == 3 ? h.w[2] : 0.0));
-    for (int j = 0; j < p->K; ++j) {
-        split_df(diag - p->d[j], &t[j], &t[KMAXP + j]);
-        split_df(p->d[j], &t[2 * KMAXP + j], &t[3 * KMAXP + j]);
-        split_df(p->c[j], &t[4 * KMAXP + j], &t[5 * KMAXP + j]);
-    }
     float* dt = nullptr;
-    CA(dalloc(p, &dt, t.size() * sizeof(float)));
-    CK(cudaMemcpy(dt, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CA(dalloc(p, &dt, 6 * KMAXP * sizeof(float)));
     op.ch = dt;
     op.cl = dt + KMAXP;
     op.dh = dt + 2 * KMAXP;
     op.dl = dt + 3 * KMAXP;
     p->cwh = dt + 4 * KMAXP;
     p->cwl = dt + 5 * KMAXP;
+    CA(upload_df_tables(p));
     if (p->var) {
         for (int a = 0; a < p->dim; ++a) {
             std::vector<float> fh(h.a[a].size()), fl(h.a[a].size());
@@ -1381,6 +1409,18 @@ void bura_default_options(bura_options* opt) {
     opt->max_outer = 12;
     opt->inner_rtol = 1e-5;
     opt->coarse_degree = 0;
+}
+
+// The weights c_j of the output sum and the shifts of the outer (refinement) CG state record.
+int upload_outer(bura_plan* p) {
+    std::vector<double> cc(KMAXP, 0.0);
+    for (int j = 0; j < p->K; ++j) cc[j] = p->c[j];
+    CK(cudaMemcpy(p->cdev, cc.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice));
+    Scal so;
+    std::memset(&so, 0, sizeof(so));
+    for (int j = 0; j < p->K; ++j) so.dsh[j] = p->d[j];
+    CK(cudaMemcpy(p->scal_outer, &so, sizeof(Scal), cudaMemcpyHostToDevice));
+    return BURA_OK;
 }
 
 int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, int k, const bura_options* opt,
@@ -1499,15 +1539,10 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if (o.precision == BURA_PREC_MIXED && o.refine == BURA_REFINE_DF && (rc = build_df(p)) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    {
-        std::vector<double> cc(KMAXP, 0.0);
-        for (int j = 0; j < p->K; ++j) cc[j] = p->c[j];
-        if (cudaMemcpy(p->cdev, cc.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(BURA_ECUDA);
-        Scal so;
-        std::memset(&so, 0, sizeof(so));
-        for (int j = 0; j < p->K; ++j) so.dsh[j] = p->d[j];
-        if (cudaMemcpy(p->scal_outer, &so, sizeof(Scal), cudaMemcpyHostToDevice) != cudaSuccess) return fail(BURA_ECUDA);
+    if ((rc = upload_outer(p)) != BURA_OK) return fail(rc);
+    if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
+        p->done = nullptr;
+        return fail(BURA_ECUDA);
     }
     if (cudaMallocHost(&p->hscal, sizeof(Scal)) != cudaSuccess) { p->hscal = nullptr; return fail(BURA_ENOMEM); }
     if (cudaMallocHost(&p->hbuf, 4 * KMAXP * sizeof(double)) != cudaSuccess) { p->hbuf = nullptr; return fail(BURA_ENOMEM); }
@@ -1535,6 +1570,7 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
         traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s,
                [&] { launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), p->cdev, u, s); });
     CKL();
+    CK(cudaEventRecord(p->done, s));
     p->st.launches = p->tr.launches;
     if (p->tr.on) {
         CK(cudaStreamSynchronize(s));
@@ -1570,6 +1606,7 @@ int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, voi
         else launch_gather_systems(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), V, s);
     });
     CKL();
+    CK(cudaEventRecord(p->done, s));
     p->st.launches = p->tr.launches;
     if (p->tr.on) {
         CK(cudaStreamSynchronize(s));
@@ -1666,6 +1703,7 @@ int bura_get_rational(const bura_plan* p, double* c, double* d, double* E) {
 int bura_get_stats(const bura_plan* p, bura_stats* st) {
     if (!p || !st) return BURA_EINVAL;
     *st = p->st;
+    st->device_bytes = p->dbytes;
     return BURA_OK;
 }
 
@@ -1706,6 +1744,7 @@ int bura_destroy(bura_plan* p) {
     if (!p) return BURA_OK;
     cudaSetDevice(p->dev);
     for (auto& e : p->tr.ev) cudaEventDestroy(e);
+    if (p->done) cudaEventDestroy(p->done);
     if (p->w64.exec) cudaGraphExecDestroy(p->w64.exec);
     if (p->w64.graph) cudaGraphDestroy(p->w64.graph);
     if (p->w32.exec) cudaGraphExecDestroy(p->w32.exec);
@@ -1715,6 +1754,27 @@ int bura_destroy(bura_plan* p) {
     if (p->hscal) cudaFreeHost(p->hscal);
     if (p->hbuf) cudaFreeHost(p->hbuf);
     delete p;
+    return BURA_OK;
+}
+
+int bura_retarget(bura_plan* p, double alpha) {
+    if (!p || !(alpha > 0 && alpha < 1)) return BURA_EINVAL;
+    std::vector<double> c(p->K, 0.0), d(p->K, 0.0);
+    double E = 0.0;
+    int rc = bura_rational(alpha, p->k, c.data(), d.data(), &E);
+    if (rc != BURA_OK) return rc;
+    if (d[0] != p->d[0]) return BURA_EREMEZ;  // d_0 = 0 fixes the coarsest smoothing degree
+    CK(cudaSetDevice(p->dev));
+    CK(cudaEventSynchronize(p->done));  // the last solve's kernels read the tables being replaced
+    p->alpha = alpha;
+    p->c = c;
+    p->d = d;
+    p->E = E;
+    CA(upload_tables<double>(p, p->w64));
+    if (p->opt.precision == BURA_PREC_MIXED) CA(upload_tables<float>(p, p->w32));
+    if (p->dfop.ch) CA(upload_df_tables(p));
+    CA(upload_outer(p));
+    p->st.E = E;
     return BURA_OK;
 }
 

@@ -79,6 +79,28 @@ def test_batch_arguments_on_the_host(lib):
     assert L.bura_solve_batch(nulls, nulls, nulls, 1, 1e-6, 1, st) == lib.BURA_EINVAL
 
 
+def test_server_and_retarget_arguments_on_the_host(lib):
+    """Defaults of the solve server and the argument checks that return before any CUDA call."""
+    import ctypes as C
+    o = lib.bura_server_default_options()
+    assert o.workers == 8 and o.mem_budget == 0
+    assert o.plan.precision == lib.BURA_PREC_MIXED and o.plan.smoother_degree == 2
+    L = lib._lib()
+    srv = C.c_void_p()
+    assert L.bura_server_create(C.byref(o), None) == lib.BURA_EINVAL
+    o.workers = -1
+    assert L.bura_server_create(C.byref(o), C.byref(srv)) == lib.BURA_EINVAL
+    req = lib.bura_request()
+    rid = C.c_ulonglong()
+    assert L.bura_server_submit(None, C.byref(req), C.byref(rid)) == lib.BURA_EINVAL
+    info = lib.bura_request_info()
+    assert L.bura_server_wait(None, 1, 0.0, C.byref(info)) == lib.BURA_EINVAL
+    st = lib.bura_server_stats()
+    assert L.bura_server_get_stats(None, C.byref(st)) == lib.BURA_EINVAL
+    assert L.bura_server_destroy(None) == lib.BURA_OK
+    assert L.bura_retarget(None, 0.5) == lib.BURA_EINVAL
+
+
 def test_setup_rejects_nonpositive_coefficients(lib):
     from paper_1612_04846_gb300 import workloads as W
     faces = list(W.constant_faces((4, 5)))
