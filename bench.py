@@ -47,6 +47,10 @@ def parse_args(argv=None):
     ap.add_argument("--profile-steps", type=int, default=6, help="solves timed kernel by kernel for the roofline")
     ap.add_argument("--skip-3d", action="store_true", help="skip the 3D variable-coefficient workload")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched 256-problem workload")
+    ap.add_argument("--skip-serve", action="store_true", help="skip the serving workload (Poisson arrivals)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s of the serving workload")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured arrival window of the serving workload")
+    ap.add_argument("--serve-warmup", type=float, default=2.0, help="warm-up arrival window of the serving workload")
     return ap.parse_args(argv)
 
 
@@ -295,6 +299,125 @@ def bench_batch(bura, W, np, torch, dev, rank, reps):
             "timing": "host wall clock around the blocking bura_solve_batch call"}
 
 
+SERVE_GRIDS = [(127, 127), (255, 255), (511, 511), (1023, 1023), (31, 31, 31), (63, 63, 63), (127, 127, 127)]
+SERVE_CAP = 64
+
+
+def serve_workload(rate, seconds, warm):
+    return ("serving: Poisson arrivals at %g/s (seed 5) for %g s after a %g s warm-up; grids uniform from "
+            "{127^2,255^2,511^2,1023^2} (2-D 5-point) and {31^3,63^3,127^3} (3-D 7-point); coefficients constant "
+            "or block log-uniform in [1e-2,1] on 8^d blocks (50/50, one field per grid); alpha ~ U(0.1,0.9), "
+            "k ~ U{5..9}, tol 1e-6; f ~ U[-1,1] (2 vectors per grid, pinned host memory); bura_server, 8 workers, "
+            "at most %d requests in flight (later arrivals are shed and counted); latency from the scheduled "
+            "arrival to u written to host memory" % (rate, seconds, warm, SERVE_CAP))
+
+
+def serve_pass(bura, np, torch, srv, data, upool, rate, seconds, warm, seed):
+    """One open-loop pass: Poisson arrivals on a fixed schedule, a collector thread waiting in order."""
+    import queue
+    rng = np.random.default_rng(seed)
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= warm + seconds:
+            break
+        gi = int(rng.integers(len(SERVE_GRIDS)))
+        arrivals.append((t, gi, bool(rng.integers(2)), float(rng.uniform(0.1, 0.9)), int(rng.integers(5, 10)),
+                         int(rng.integers(2))))
+    lock = threading.Lock()
+    free = {gi: list(upool[gi]) for gi in range(len(SERVE_GRIDS))}  # pinned before the pass: no CUDA
+                                                                      # allocation beside the server's work
+    state = {"in_flight": 0}
+    lat, done_t, per = [], [], {}
+    state["shed"] = 0
+    q = queue.Queue()
+
+    def submit_all(arrivals, t0):
+        for (ta, gi, var, alpha, k, fi) in arrivals:
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            measured = ta >= warm
+            with lock:
+                full = state["in_flight"] >= SERVE_CAP
+                if not full:
+                    state["in_flight"] += 1
+                    u = free[gi].pop()
+            if full:
+                state["shed"] += int(measured)
+                continue
+            f, faces = data[gi][0][fi], data[gi][1] if var else None
+            rid = srv.submit(SERVE_GRIDS[gi], alpha, k, f, u, TOL, faces=faces, field=gi + 1 if var else 0)
+            q.put((rid, gi, u, t0 + ta, time.perf_counter(), measured))
+
+    def collect():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            rid, gi, u, t_sched, t_sub, measured = item
+            try:
+                info = srv.wait(rid)
+            except Exception as e:  # reported by the caller after the join
+                state["error"] = repr(e)
+                info = {"status": -1, "total_ms": 0.0, "service_ms": 0.0}
+            t_done = time.perf_counter()
+            with lock:
+                free[gi].append(u)
+                state["in_flight"] -= 1
+                if measured:
+                    if info["status"] not in (bura.BURA_OK, bura.BURA_ENOCONV):
+                        state["error"] = "serving request failed: %s" % info
+                    lat.append(info["total_ms"] + 1e3 * (t_sub - t_sched))
+                    done_t.append(t_done)
+                    per.setdefault(gi, []).append(info["service_ms"])
+
+    th = threading.Thread(target=collect, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    try:
+        submit_all(arrivals, t0)
+    finally:  # the collector is always stopped and joined before the server can be destroyed
+        q.put(None)
+        th.join()
+    if "error" in state:
+        raise RuntimeError(state["error"])
+    n_meas = sum(1 for a in arrivals if a[0] >= warm)
+    span = (max(done_t) - (t0 + warm)) if done_t else float("nan")
+    lat.sort()
+    pct = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))] if lat else float("nan")
+    return {"offered_per_s": rate, "arrivals_measured": n_meas, "completed": len(lat), "shed": state["shed"],
+            "solves_per_s": len(lat) / span if lat else 0.0, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
+            "mean_service_ms_per_grid": {"x".join(map(str, SERVE_GRIDS[g])): float(np.mean(v)) for g, v in sorted(per.items())}}
+
+
+def bench_serve(bura, W, np, torch, rate, seconds, warm):
+    """The serving workload through bura_server: one pass at the offered rate, one at 70 % of the
+    throughput that pass sustained."""
+    data = {}
+    for gi, shp in enumerate(SERVE_GRIDS):
+        nps = tuple(reversed(shp))
+        fs = []
+        for j in range(2):
+            t = torch.empty(int(np.prod(shp)), dtype=torch.float64, pin_memory=True)
+            t.copy_(torch.from_numpy(W.rhs_uniform(nps, 500 + 10 * gi + j)))
+            fs.append(t.numpy())
+        data[gi] = (fs, W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 600 + gi))
+    upool = {gi: [torch.empty(int(np.prod(shp)), dtype=torch.float64, pin_memory=True).numpy()
+                  for _ in range(SERVE_CAP)] for gi, shp in enumerate(SERVE_GRIDS)}
+    srv = bura.BuraServer(workers=8)
+    try:
+        first = serve_pass(bura, np, torch, srv, data, upool, rate, seconds, warm, 5)
+        cap_rate = max(1.0, 0.7 * first["solves_per_s"])
+        second = serve_pass(bura, np, torch, srv, data, upool, cap_rate, seconds, warm, 6)
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"workload": serve_workload(rate, seconds, warm), "at_offered_rate": first,
+            "at_70pct_of_sustained": second, "server": st,
+            "timing": "host wall clock; latency = scheduled arrival -> u in host memory"}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -476,6 +599,9 @@ def main(argv=None):
     wb = None
     if not args.skip_batch:
         wb = bench_batch(bura, W, np, torch, dev, rank, 2)
+    wsv = None
+    if not args.skip_serve:
+        wsv = bench_serve(bura, W, np, torch, args.serve_rate, args.serve_seconds, args.serve_warmup)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -490,7 +616,8 @@ def main(argv=None):
                 "fp64_path_solves_per_s": fp64_solves,
                 "df_refine_solves_per_s": df_solves,
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "batch_256_mixed_2d": wb}}
+                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "batch_256_mixed_2d": wb,
+                                                               "serve_poisson_mixed": wsv}}
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
         dist.destroy_process_group()

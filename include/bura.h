@@ -336,7 +336,9 @@ int bura_server_submit(bura_server* srv, const bura_request* req, unsigned long 
  * request forgotten; BURA_ETIMEOUT: not done yet; BURA_EINVAL: unknown id. */
 int bura_server_wait(bura_server* srv, unsigned long long id, double timeout_s, bura_request_info* info);
 int bura_server_get_stats(bura_server* srv, bura_server_stats* stats);
-/* Serves every queued request, joins the workers and frees every plan (NULL is accepted). */
+/* Serves every queued request, joins the workers and frees every plan and request record (NULL is
+ * accepted).  No other call on srv may be in progress or follow (a thread blocked in
+ * bura_server_wait must have returned first). */
 int bura_server_destroy(bura_server* srv);
 
 /* Static description of a status code. */

@@ -17,6 +17,10 @@
 //   * Start: the k = 1 problem at alpha = 1/2 from a fixed guess, continuation in k at alpha = 1/2
 //     (one new zero/pole pair and two reference points extrapolated below the smallest ones),
 //     then continuation in alpha with an adaptive step to the requested alpha.
+//   * Warm start: the converged states on a fixed grid of alpha (steps of kGridStep) are kept per k,
+//     each reached from the alpha = 1/2 anchor exactly as a cold start; a requested alpha continues
+//     from the nearest grid state.  The result is a function of (alpha, k) alone, whatever was
+//     solved before in the process.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -242,10 +246,8 @@ bool anchor(int k, Rat& out) {
     return true;
 }
 
-bool solve_bura(double alpha, int k, Rat& out) {
-    Rat R;
-    if (!anchor(k, R)) return false;
-    double a = 0.5;
+// Continuation in alpha from the state R at alpha a to the requested alpha (adaptive step).
+bool continue_to(Rat R, double a, double alpha, Rat& out) {
     double step = alpha > a ? 0.05 : -0.05;
     int guard = 0;
     while (a != alpha && guard++ < 10000) {
@@ -266,13 +268,50 @@ bool solve_bura(double alpha, int k, Rat& out) {
     return true;
 }
 
+bool solve_bura(double alpha, int k, Rat& out) {
+    Rat R;
+    if (!anchor(k, R)) return false;
+    return continue_to(R, 0.5, alpha, out);
+}
+
+constexpr double kGridStep = 0.05;
+std::mutex g_state_mu;
+std::map<std::pair<int, int>, Rat> g_states;  // (k, grid index) -> converged state at kGridStep * index
+
+bool solve_warm(double alpha, int k, Rat& out) {
+    int gi = (int)std::lround(alpha / kGridStep);
+    gi = std::max(1, std::min(gi, (int)std::lround(1.0 / kGridStep) - 1));
+    const double ag = kGridStep * gi;
+    Rat G;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lk(g_state_mu);
+        auto it = g_states.find({k, gi});
+        if (it != g_states.end()) {
+            G = it->second;
+            have = true;
+        }
+    }
+    if (!have) {
+        if (!solve_bura(ag, k, G)) return solve_bura(alpha, k, out);
+        std::lock_guard<std::mutex> lk(g_state_mu);
+        g_states[{k, gi}] = G;
+    }
+    if (alpha == ag) {
+        out = G;
+        return true;
+    }
+    return continue_to(G, ag, alpha, out) || solve_bura(alpha, k, out);
+}
+
 struct Coeffs {
     std::vector<double> c, d;
     double E;
 };
 
 std::mutex g_mu;
-std::map<std::pair<double, int>, Coeffs> g_cache;
+std::map<std::pair<double, int>, Coeffs> g_cache;  // results by (alpha, k); cleared when it grows past
+constexpr size_t kCacheMax = 1u << 16;             // kCacheMax entries (a continuous stream of alphas)
 
 }  // namespace
 
@@ -289,7 +328,7 @@ extern "C" int bura_rational(double alpha, int k, double* c, double* d, double* 
         }
     }
     Rat R;
-    if (!solve_bura(alpha, k, R)) return BURA_EREMEZ;
+    if (!solve_warm(alpha, k, R)) return BURA_EREMEZ;
     // Partial fractions of t^{-1} r(t): c_0 = r(0); c_j = residue of r(t)/t at d_j = -e^{w_j}.
     std::vector<double> zu(k), zw(k);
     for (int j = 0; j < k; ++j) { zu[j] = std::exp(R.th[1 + j]); zw[j] = std::exp(R.th[1 + k + j]); }
@@ -316,6 +355,7 @@ extern "C" int bura_rational(double alpha, int k, double* c, double* d, double* 
         if (!(out.c[j] > 0) || !std::isfinite(out.c[j])) return BURA_EREMEZ;
     {
         std::lock_guard<std::mutex> lk(g_mu);
+        if (g_cache.size() >= kCacheMax) g_cache.clear();
         g_cache[{alpha, k}] = out;
     }
     std::memcpy(c, out.c.data(), sizeof(double) * (k + 1));

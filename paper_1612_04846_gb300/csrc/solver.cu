@@ -10,6 +10,7 @@
 #include <new>
 #include <atomic>
 #include <mutex>
+#include <shared_mutex>
 #include <thread>
 #include <vector>
 
@@ -166,7 +167,11 @@ struct bura_plan {
 
 namespace {
 
-thread_local cudaError_t g_last = cudaSuccess;  // per calling thread (batch workers run in parallel)
+thread_local cudaError_t g_last = cudaSuccess;
+// Stream capture of a PCG graph is invalidated by a device-synchronising call of another thread (a
+// device-wide synchronisation, a free, a synchronous copy or memset).  The library's own such calls
+// (plan setup, retargeting, destruction) hold this guard shared; a capture holds it exclusively.
+std::shared_mutex g_capture_guard;  // per calling thread (batch workers run in parallel)
 #define CK(call)                                  \
     do {                                          \
         cudaError_t e_ = (call);                  \
@@ -990,10 +995,9 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
 template <class T>
 int build_graph(bura_plan* p, Work<T>& w) {
     if (w.exec) return BURA_OK;
-    // capture and instantiation happen once per plan; plans solved concurrently by batch workers build
-    // their graphs one at a time
-    static std::mutex build_mutex;
-    std::lock_guard<std::mutex> lock(build_mutex);
+    // capture and instantiation happen once per plan, one plan at a time, and never beside the library's
+    // own device-synchronising calls in other threads
+    std::unique_lock<std::shared_mutex> lock(g_capture_guard);
     CK(cudaGraphCreate(&w.graph, 0));
     CK(cudaGraphConditionalHandleCreate(&w.cond, w.graph, 1u, cudaGraphCondAssignDefault));
     // the parameter struct holds a union with no default constructor: start from zeroed storage
@@ -1018,8 +1022,9 @@ int build_graph(bura_plan* p, Work<T>& w) {
     cudaError_t e = cudaStreamEndCapture(p->cap, &captured);
     if (rc == BURA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&w.exec, w.graph, 0);
     if (rc != BURA_OK || e != cudaSuccess) {
-        // drop the partial graph, so that the plan stays destroyable and a later solve captures afresh
-        cudaGraphDestroy(w.graph);
+        // a capture that another thread invalidated leaves a graph the driver cannot always destroy
+        // (observed: a crash in cudaGraphDestroy); it is left allocated and the next solve captures afresh
+        cudaGetLastError();
         w.graph = nullptr;
         w.exec = nullptr;
         if (rc != BURA_OK) return rc;
@@ -1042,7 +1047,9 @@ int pcg(bura_plan* p, Work<T>& w, int* iters_out, cudaStream_t s) {
             if (h.breakdown || h.fault || h.nactive == 0 || h.it >= h.max_it) break;
         }
     } else {
-        CA(build_graph<T>(p, w));
+        int brc = build_graph<T>(p, w);
+        for (int attempt = 1; brc == BURA_ECUDA && attempt < 3; ++attempt) brc = build_graph<T>(p, w);
+        CA(brc);
         CK(cudaGraphLaunch(w.exec, s));
         CK(cudaMemcpyAsync(p->hscal, w.scal, sizeof(Scal), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1395,6 +1402,23 @@ const double* solution_vectors(const bura_plan* p) {
     return p->opt.precision == BURA_PREC_FP64 ? p->w64.x : p->v64;
 }
 
+// Frees every device and host resource of the plan (the body of bura_destroy, without its guard).
+int destroy_plan(bura_plan* p) {
+    cudaSetDevice(p->dev);
+    for (auto& e : p->tr.ev) cudaEventDestroy(e);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->w64.exec) cudaGraphExecDestroy(p->w64.exec);
+    if (p->w64.graph) cudaGraphDestroy(p->w64.graph);
+    if (p->w32.exec) cudaGraphExecDestroy(p->w32.exec);
+    if (p->w32.graph) cudaGraphDestroy(p->w32.graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    for (void* q : p->allocs) cudaFree(q);
+    if (p->hscal) cudaFreeHost(p->hscal);
+    if (p->hbuf) cudaFreeHost(p->hbuf);
+    delete p;
+    return BURA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1454,9 +1478,10 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
         o.post_smooth_split > 1)
         return BURA_EINVAL;
 
+    std::shared_lock<std::shared_mutex> guard(g_capture_guard);
     bura_plan* p = new (std::nothrow) bura_plan();
     if (!p) return BURA_ENOMEM;
-    auto fail = [&](int rc) { bura_destroy(p); return rc; };
+    auto fail = [&](int rc) { destroy_plan(p); return rc; };
     p->dim = dim;
     p->var = var;
     p->k = k;
@@ -1585,6 +1610,7 @@ int bura_solve_host(bura_plan* p, const double* f, double* u, double tol, void* 
     const size_t nb = (size_t)p->hl[0].N * sizeof(double);
     CK(cudaSetDevice(p->dev));
     if (!p->fdev) {
+        std::shared_lock<std::shared_mutex> guard(g_capture_guard);
         CA(dalloc(p, &p->fdev, nb));
         CA(dalloc(p, &p->udev, nb));
     }
@@ -1742,20 +1768,10 @@ int bura_get_profile(const bura_plan* p, int max_entries, bura_kernel_prof* out,
 
 int bura_destroy(bura_plan* p) {
     if (!p) return BURA_OK;
-    cudaSetDevice(p->dev);
-    for (auto& e : p->tr.ev) cudaEventDestroy(e);
-    if (p->done) cudaEventDestroy(p->done);
-    if (p->w64.exec) cudaGraphExecDestroy(p->w64.exec);
-    if (p->w64.graph) cudaGraphDestroy(p->w64.graph);
-    if (p->w32.exec) cudaGraphExecDestroy(p->w32.exec);
-    if (p->w32.graph) cudaGraphDestroy(p->w32.graph);
-    if (p->cap) cudaStreamDestroy(p->cap);
-    for (void* q : p->allocs) cudaFree(q);
-    if (p->hscal) cudaFreeHost(p->hscal);
-    if (p->hbuf) cudaFreeHost(p->hbuf);
-    delete p;
-    return BURA_OK;
+    std::shared_lock<std::shared_mutex> guard(g_capture_guard);
+    return destroy_plan(p);
 }
+
 
 int bura_retarget(bura_plan* p, double alpha) {
     if (!p || !(alpha > 0 && alpha < 1)) return BURA_EINVAL;
@@ -1764,6 +1780,7 @@ int bura_retarget(bura_plan* p, double alpha) {
     int rc = bura_rational(alpha, p->k, c.data(), d.data(), &E);
     if (rc != BURA_OK) return rc;
     if (d[0] != p->d[0]) return BURA_EREMEZ;  // d_0 = 0 fixes the coarsest smoothing degree
+    std::shared_lock<std::shared_mutex> guard(g_capture_guard);
     CK(cudaSetDevice(p->dev));
     CK(cudaEventSynchronize(p->done));  // the last solve's kernels read the tables being replaced
     p->alpha = alpha;
