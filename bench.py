@@ -144,9 +144,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "noalloc.cu",
+                  "kernels.cuh", "kernels_impl.cuh", "tma.cuh")
+
+
 def sources_sha():
+    """Hash of the kernel sources (device code and the headers it includes), whose per-launch DRAM
+    traffic profiles/ncu_traffic.json records; host-only files do not change it."""
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(CSRC)):
+    for fn in KERNEL_SOURCES:
         with open(os.path.join(CSRC, fn), "rb") as fh:
             h.update(fn.encode() + fh.read())
     return h.hexdigest()[:16]
