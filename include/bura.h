@@ -256,6 +256,17 @@ int bura_residual_norms_noalloc(const bura_grid* grid, int nsys, const double* d
  */
 int bura_retarget(bura_plan* plan, double alpha);
 
+/*
+ * Multi-step BURA (Sec. "Multi-step BURA approximation"): with plans of one grid and operator at
+ * alpha_1..alpha_n, u = r_{alpha_n}(A) A^{-1} ... r_{alpha_1}(A) A^{-1} f, the approximation of
+ * A^{-(alpha_1+...+alpha_n)} f by successive BURA solves (plans[0] first).  f and u are DEVICE arrays
+ * of N doubles (they may alias); each step runs in place in u, stream-ordered on `stream`.  Each step
+ * meets tol relative to its own input, as bura_solve; a step's error is carried through the later
+ * steps, whose operators r_j(A) A^{-1} have norms up to about lambda_min(A)^{-alpha_j}.
+ * Errors: BURA_EINVAL (n < 1, a null plan, plans of different grids), those of bura_solve.
+ */
+int bura_solve_chain(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream);
+
 /* Frees every device and host resource of the plan (NULL is accepted). */
 int bura_destroy(bura_plan* plan);
 

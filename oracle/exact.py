@@ -17,7 +17,8 @@ from __future__ import annotations
 import numpy as np
 import scipy.fft as sfft
 
-__all__ = ["gershgorin", "eigenvalues", "apply_function", "fractional", "bura_value", "bura_components"]
+__all__ = ["gershgorin", "eigenvalues", "apply_function", "fractional", "bura_value", "bura_components",
+           "multistep_value", "multistep_error", "energy_ratio"]
 
 
 def gershgorin(shape):
@@ -67,3 +68,32 @@ def bura_value(shape, f, c, d):
 def bura_components(shape, f, d):
     """The k+1 exact solutions v_j = (A - d_j I)^{-1} f, shape (k+1, N)."""
     return np.stack([apply_function(shape, f, lambda lam, dj=float(dj): 1.0 / (lam - dj)) for dj in d])
+
+
+def multistep_value(shape, f, steps):
+    """Multi-step BURA value (Sec. "Multi-step BURA approximation"): u_0 = f and
+    u_i = r_{alpha_i}(A) A^{-1} u_{i-1}, each step the exact BURA value of its (c, d), steps in order of
+    application; approximates A^{-(alpha_1 + ... + alpha_n)} f."""
+    u = np.asarray(f, dtype=np.float64)
+    for c, d in steps:
+        u = bura_value(shape, u, c, d)
+    return u
+
+
+def multistep_error(shape, steps, alpha):
+    """E_{alpha_1..alpha_n}(k,k;1) of eq. (multi-step error): the largest |prod_i r_i(t) / t^(n-1) -
+    t^(1-alpha)| over the eigenvalues t of A, with r_i(t) = t sum_j c_j/(t - d_j) (eq. (simplified))."""
+    lam = eigenvalues(shape).ravel()
+    prod = np.ones_like(lam)
+    for c, d in steps:
+        prod *= lam * sum(float(cj) / (lam - float(dj)) for cj, dj in zip(c, d))
+    n = len(steps)
+    return float(np.max(np.abs(prod / lam ** (n - 1) - lam ** (1.0 - float(alpha)))))
+
+
+def energy_ratio(shape, f, u, alpha):
+    """||u - A^{-alpha} f||_A / ||f||_{A^{-1}}, the error measure of eq. (errorU)."""
+    e = np.asarray(u, dtype=np.float64) - fractional(shape, f, alpha)
+    ea = float(e @ apply_function(shape, e, lambda lam: lam))
+    fa = float(np.asarray(f) @ apply_function(shape, f, lambda lam: 1.0 / lam))
+    return (ea / fa) ** 0.5

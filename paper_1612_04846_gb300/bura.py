@@ -123,6 +123,7 @@ def _lib():
         L.bura_set_profiling.argtypes = [P, I]
         L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
         L.bura_retarget.argtypes = [P, D]
+        L.bura_solve_chain.argtypes = [C.POINTER(P), I, P, P, D, P]
         L.bura_server_default_options.argtypes = [C.POINTER(bura_server_options)]
         L.bura_server_default_options.restype = None
         L.bura_server_create.argtypes = [C.POINTER(bura_server_options), C.POINTER(P)]
@@ -137,7 +138,7 @@ def _lib():
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
                      "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-                     "bura_solve_batch", "bura_retarget", "bura_server_create", "bura_server_submit",
+                     "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_server_create", "bura_server_submit",
                      "bura_server_wait", "bura_server_get_stats", "bura_server_destroy"):
             getattr(L, name).restype = I
         _LIB = L
@@ -236,6 +237,14 @@ def bura_solve_batch(plans, fs, us, tol, nworkers=0):
     _check(_lib().bura_solve_batch(pa, fa, ua, int(n), float(tol), int(nworkers), st), "bura_solve_batch",
            allow=(BURA_ENOCONV,))
     return list(st)[:n]
+
+
+def bura_solve_chain(plans, f, u, tol, stream=None):
+    """Multi-step BURA: the plans' BURA solves applied in order to f (device float64 tensors f, u)."""
+    P = C.c_void_p
+    pa = (P * max(len(plans), 1))(*[C.cast(p, P) for p in plans])
+    return _check(_lib().bura_solve_chain(pa, int(len(plans)), _dptr(f), _dptr(u), float(tol), _stream(stream)),
+                  "bura_solve_chain", allow=(BURA_ENOCONV,))
 
 
 def bura_retarget(plan, alpha):
@@ -407,6 +416,6 @@ def bura_destroy(plan):
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
             "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-            "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_server_default_options",
+            "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_server_default_options",
             "bura_server_create", "bura_server_submit", "bura_server_wait", "bura_server_get_stats",
             "bura_server_destroy"]

@@ -1604,6 +1604,27 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
     return rc;
 }
 
+int bura_solve_chain(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream) {
+    if (!plans || n < 1 || !f || !u || !(tol > 0)) return BURA_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return BURA_EINVAL;
+        const bura_plan* a = plans[i];
+        const bura_plan* b = plans[0];
+        if (a->dim != b->dim || a->var != b->var || a->hl[0].n[0] != b->hl[0].n[0] || a->hl[0].n[1] != b->hl[0].n[1] ||
+            a->hl[0].n[2] != b->hl[0].n[2] || a->dev != b->dev)
+            return BURA_EINVAL;
+    }
+    int out = BURA_OK;
+    const double* in = f;
+    for (int i = 0; i < n; ++i) {
+        const int rc = bura_solve(plans[i], in, u, tol, stream);  // bura_solve reads f before writing u
+        if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
+        if (rc == BURA_ENOCONV) out = BURA_ENOCONV;
+        in = u;
+    }
+    return out;
+}
+
 int bura_solve_host(bura_plan* p, const double* f, double* u, double tol, void* stream) {
     if (!p || !f || !u) return BURA_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

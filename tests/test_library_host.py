@@ -99,6 +99,9 @@ def test_server_and_retarget_arguments_on_the_host(lib):
     assert L.bura_server_get_stats(None, C.byref(st)) == lib.BURA_EINVAL
     assert L.bura_server_destroy(None) == lib.BURA_OK
     assert L.bura_retarget(None, 0.5) == lib.BURA_EINVAL
+    nulls = (C.c_void_p * 2)()
+    assert L.bura_solve_chain(nulls, 2, None, None, 1e-6, None) == lib.BURA_EINVAL
+    assert L.bura_solve_chain(nulls, 0, None, None, 1e-6, None) == lib.BURA_EINVAL
 
 
 def test_setup_rejects_nonpositive_coefficients(lib):
