@@ -18,7 +18,8 @@ import numpy as np
 import scipy.fft as sfft
 
 __all__ = ["gershgorin", "eigenvalues", "apply_function", "fractional", "bura_value", "bura_components",
-           "multistep_value", "multistep_error", "energy_ratio"]
+           "multistep_value", "multistep_error", "energy_ratio", "product_error_on_interval",
+           "reconstruction_ratio"]
 
 
 def gershgorin(shape):
@@ -97,3 +98,29 @@ def energy_ratio(shape, f, u, alpha):
     ea = float(e @ apply_function(shape, e, lambda lam: lam))
     fa = float(np.asarray(f) @ apply_function(shape, f, lambda lam: 1.0 / lam))
     return (ea / fa) ** 0.5
+
+
+def _r_of_t(c, d, t):
+    """r(t) = t sum_j c_j/(t - d_j) (eq. (simplified)), continued by r(0) = c_0 where d_0 = 0."""
+    t = np.asarray(t, dtype=np.float64)
+    out = np.zeros_like(t)
+    for cj, dj in zip(c, d):
+        cj, dj = float(cj), float(dj)
+        out += cj if dj == 0.0 else cj * t / (t - dj)
+    return out
+
+
+def product_error_on_interval(steps, t):
+    """|r_1(t) r_2(t) ... - t| on the points t of [0, 1]: the two-step residual of the f-reconstruction
+    (Sec. "1D and 3D numerical tests", E_{1-alpha,alpha}(k,k;2) is its maximum over [0, 1])."""
+    prod = np.ones_like(np.asarray(t, dtype=np.float64))
+    for c, d in steps:
+        prod = prod * _r_of_t(c, d, t)
+    return np.abs(prod - np.asarray(t))
+
+
+def reconstruction_ratio(shape, f, steps):
+    """||f_r - f|| / ||A^{-1} f|| with f_r = A u_2, u_2 the two-step value of steps (eq. (3D error))."""
+    u2 = multistep_value(shape, f, steps)
+    fr = apply_function(shape, u2, lambda lam: lam)
+    return float(np.linalg.norm(fr - f) / np.linalg.norm(apply_function(shape, f, lambda lam: 1.0 / lam)))

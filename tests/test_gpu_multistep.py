@@ -56,3 +56,36 @@ def test_chain_matches_the_multistep_oracle(lib, shape, alphas, precision, tol):
     assert err <= bound, (err, bound)
     ratio = exact.energy_ratio(nps, f, u, alpha)
     assert ratio <= exact.multistep_error(nps, steps, alpha) * (1 + 1e-6) + bound
+
+
+def test_f_reconstruction_on_a_variable_3d_operator(lib):
+    """Sec. "1D and 3D numerical tests": with no exact solution, f_r = A u_2 (u_2 the two-step chain at
+    alpha and 1 - alpha) must satisfy ||f_r - f|| / ||A^{-1} f|| <= E_{1-alpha} + E_alpha - E_{1-alpha} E_alpha
+    (eq. (3D error final)).  A u_2 comes from the plan's shifted operator (system 0, d_0 = 0) and A^{-1} f
+    from system 0 of bura_solve_systems, all through the library."""
+    shape, alpha, k, tol = (31, 31, 31), 0.25, 7, 1e-11
+    nps = tuple(reversed(shape))
+    faces = W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 2)
+    f = W.rhs_normal(nps, 3)
+    o = lib.bura_default_options()
+    o.precision = lib.BURA_PREC_FP64
+    plans = [lib.bura_setup(shape, a, k, faces=faces, options=o) for a in (alpha, 1.0 - alpha)]
+    try:
+        N = f.size
+        fd = torch.from_numpy(f).cuda()
+        u = torch.zeros_like(fd)
+        assert lib.bura_solve_chain(plans, fd, u, tol) == lib.BURA_OK
+        X = torch.zeros((k + 1, N), dtype=torch.float64, device="cuda")
+        X[0] = u
+        Y = torch.zeros_like(X)
+        lib.bura_apply_shifted(plans[0], X, Y)
+        V = torch.zeros_like(X)
+        lib.bura_solve_systems(plans[0], fd, V, tol)
+        torch.cuda.synchronize()
+        fr, v0 = Y[0].cpu().numpy(), V[0].cpu().numpy()
+    finally:
+        for p in plans:
+            lib.bura_destroy(p)
+    ratio = float(np.linalg.norm(fr - f) / np.linalg.norm(v0))
+    E1, E2 = tables.entry(alpha, k)["E"], tables.entry(1.0 - alpha, k)["E"]
+    assert 0 < ratio <= (E1 + E2 - E1 * E2) * (1 + 1e-6), (ratio, E1 + E2 - E1 * E2, E1 * E2)

@@ -6,6 +6,9 @@
     -E_{ai} at t = 1, Lemma BURA_caracter), because Lambda_N is close to 1;
   * for any f the ratio ||u_n - A^{-alpha} f||_A / ||f||_{A^{-1}} is at most E_{a1..an} (the argument of
     Lemma l:BURAerror with the multi-step error function).
+  * the f-reconstruction (Sec. "1D and 3D numerical tests"): |r_{1-alpha}(t) r_alpha(t) - t| on [0, 1]
+    reaches its largest value E_{1-alpha} + E_alpha - E_{1-alpha} E_alpha at t = 1 only (eq. (3D error final),
+    stated sharp for k = 5, 7), and ||f_r - f|| / ||A^{-1} f|| stays below it.
 A dropped cross term, a wrong power of t or a sign slip breaks one of these.
 """
 import numpy as np
@@ -61,3 +64,25 @@ def test_one_step_is_the_bura_value():
     ref = tables.entry(0.5, k)
     assert np.array_equal(exact.multistep_value(shape, f, [(ref["c"], ref["d"])]),
                           exact.bura_value(shape, f, ref["c"], ref["d"]))
+
+
+@pytest.mark.parametrize("alpha", [0.25, 0.5, 0.75])
+@pytest.mark.parametrize("k", [5, 7])
+def test_reconstruction_residual_peaks_at_one(alpha, k):
+    steps = _steps((alpha, 1.0 - alpha), k)
+    t = np.concatenate([[0.0], np.logspace(-14, 0, 20001)])
+    res = exact.product_error_on_interval(steps, t)
+    E1, E2 = tables.entry(alpha, k)["E"], tables.entry(1.0 - alpha, k)["E"]
+    assert abs(res[-1] - (E1 + E2 - E1 * E2)) <= 1e-9 * (E1 + E2)
+    assert int(np.argmax(res)) == len(t) - 1
+    assert np.max(res[t < 0.8]) < res[-1]
+
+
+@pytest.mark.parametrize("shape", [(63, 63), (15, 15, 15)])
+def test_reconstruction_ratio_within_the_paper_bound(shape):
+    alpha, k = 0.25, 7
+    steps = _steps((alpha, 1.0 - alpha), k)
+    f = W.rhs_uniform(shape, 41)
+    ratio = exact.reconstruction_ratio(shape, f, steps)
+    E1, E2 = tables.entry(alpha, k)["E"], tables.entry(1.0 - alpha, k)["E"]
+    assert 0 < ratio <= E1 + E2 - E1 * E2
