@@ -147,6 +147,25 @@ def test_library_rational_matches_oracle(lib, alpha, k):
     assert np.max(np.abs(r(c, d) - r(ref["c"], ref["d"]))) <= 2e-15
 
 
+@pytest.mark.parametrize("alpha", [0.37, 0.13])
+def test_library_rational_off_the_warm_start_grid_matches_live_oracle(lib, alpha):
+    """alpha off the library's warm-start grid (multiples of 0.05) goes through the continuation from the
+    nearest grid state; r(t) must still agree with the oracle's multi-precision Algorithm 1 (run live)
+    to 2e-15 on [0, 1]."""
+    pytest.importorskip("mpmath")
+    from oracle.remez import bura
+    k = 5
+    ref = bura(alpha, k).floats()
+    c, d, E = lib.bura_rational(alpha, k)
+    assert abs(E - ref["E"]) <= 1e-11 * ref["E"]
+    t = np.concatenate([np.logspace(-40, 0, 2000), np.linspace(0.001, 1, 1000)])
+
+    def r(cc, dd):
+        return t * sum(cj / (t - dj) for cj, dj in zip(cc, dd))
+
+    assert np.max(np.abs(r(c, d) - r(ref["c"], ref["d"]))) <= 2e-15
+
+
 def test_library_rational_edge_alphas(lib):
     """Outside the tabulated alphas: positivity, ordering, c_0 = E and the Stahl asymptotics."""
     import math
