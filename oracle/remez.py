@@ -30,8 +30,8 @@ How (Algorithm 1, Sec. 3.2, taken step by step)
   t = (1+s)/2, and c_0 = P(0)/Q(0), c_j = P(d_j) / (d_j Q'(d_j)) (eq. (simplified);
   c_0 = E by eq. (c0,beta), Sec. 4.1).
 
-Readings where the paper leaves a choice (each also listed in the design doc)
------------------------------------------------------------------------
+Readings where the paper leaves a choice
+----------------------------------------
 * Arithmetic: mpmath with max(60, 40 + 4 |log10 eta_2|) decimal digits.  Table
   (tabLastS) shows that quad precision stops converging at k = 7..11; the extreme
   points cluster at 0 (eta_2 ~ 1e-25 for alpha = 0.9, k = 9) and the Step 3 matrix
