@@ -112,6 +112,16 @@ typedef struct {
                              step).  Every point gets the same operations either way; r.z is summed by
                              a sweep with another CTA count, so the iterates may differ in the last
                              bits of the FP32 beta. */
+    int unscaled;         /* 0 (default): u solves the scaled problem A^alpha u = f.  1: f is the right-hand
+                             side ftilde of the unscaled problem Atilde^alpha utilde = ftilde and u = utilde =
+                             Lambda^-alpha (A^-alpha ftilde), since Atilde = Lambda A (eq. (algebraic), Sec. 1.4;
+                             Corollary c:BURAerror is stated for the scaled pair).  The stopping rule and
+                             bura_stats refer to the scaled solution; the relative error is the same.  Not
+                             accepted by bura_setup_shifts (no alpha). */
+    long long tma_wait_cycles; /* SM clocks a TMA-staged sweep waits for one stage of its shared-memory ring
+                             before it gives up, records a fault and the solve returns BURA_ETIMEOUT; 0 = the
+                             default (about 2 s).  Copies still in flight are always drained under the
+                             default budget before a kernel exits.  See bura_set_tma_wait_cycles. */
 } bura_options;
 
 /* Statistics of the last bura_solve*/
@@ -171,6 +181,44 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
                const bura_options* opt, bura_plan** out);
 
 /*
+ * A plan for a partial-fraction sum with caller-given weights and shifts instead of the BURA:
+ *     u = sum_{j=0}^{nsys-1} c[j] (A - d[j] I)^{-1} f,    c[j] > 0, d[j] <= 0,
+ * on the same multi-shift multigrid-PCG solve.  This is the form of the sinc quadrature of [BP15] that the
+ * paper compares the BURA with (eq. (BonitoPasciak), Sec. 5.3): with A = Atilde / Lambda its nodes are
+ * d_l = -e^{-2 l k'} / Lambda with weights c_l = (2 k' sin(pi alpha) / pi) e^{2 (alpha - 1) l k'} Lambda^(alpha - 1)
+ * (every term a positive diagonal shift of Atilde).  A quadrature with more than BURA_MAX_K + 1 nodes is
+ * split over several plans whose results bura_solve_sum adds.
+ *   c, d: HOST arrays of nsys doubles (copied).  The plan stores the systems sorted by descending d;
+ *         bura_get_rational returns them in that order with E = 0.
+ *   grid, faces, opt: as for bura_setup (opt->unscaled must be 0).
+ * Errors: BURA_EINVAL (bad grid, null c/d, nsys < 1, c[j] <= 0, d[j] > 0, non-finite values, unscaled),
+ *         BURA_ERANGE (nsys > BURA_MAX_K + 1, or N too large), BURA_ENOMEM, BURA_ECUDA.
+ *         bura_retarget rejects such a plan with BURA_EINVAL.
+ */
+int bura_setup_shifts(const bura_grid* grid, const double* const* faces, int nsys, const double* c, const double* d,
+                      const bura_options* opt, bura_plan** out);
+
+/*
+ * The scale Lambda of eq. (algebraic) (Sec. 1.4) for a grid and its coefficients, host only: the Gershgorin
+ * bound max_P sum_Q |Atilde_PQ| of the unscaled matrix, which every plan of the grid uses (A = Atilde / Lambda).
+ * grid and faces as for bura_setup.  Errors: BURA_EINVAL (bad grid or faces, null Lambda), BURA_ERANGE.
+ */
+int bura_scale(const bura_grid* grid, const double* const* faces, double* Lambda);
+
+/*
+ * Nodes of the sinc quadrature of [BP15] in the paper's comparison (eq. (BonitoPasciak), Sec. 5.3) for the
+ * scaled operator A = Atilde / Lambda, host only:
+ *     Atilde^{-alpha} ftilde ~ (2 k' sin(pi alpha) / pi) sum_{l=-m}^{M} e^{2 (alpha-1) l k'} (e^{-2 l k'} I + Atilde)^{-1} ftilde,
+ *     m = ceil(pi^2 / (4 alpha k'^2)), M = ceil(pi^2 / (4 (1 - alpha) k'^2)),
+ * returned as the partial-fraction form of A^{-alpha} f:  c[l+m] = (2 k' sin(pi alpha)/pi) e^{2(alpha-1) l k'}
+ * Lambda^(alpha-1) > 0 and d[l+m] = -e^{-2 l k'} / Lambda < 0, l = -m..M, for bura_setup_shifts.
+ *   cap: capacity of the caller's HOST arrays c, d; *n receives m + M + 1 (also when it exceeds cap).
+ * Errors: BURA_EINVAL (alpha not in (0,1), kprime <= 0, Lambda <= 0, null n, null c/d with cap > 0),
+ *         BURA_ERANGE (m + M + 1 > cap; nothing written to c, d).
+ */
+int bura_quadrature_bp15(double alpha, double kprime, double Lambda, int cap, double* c, double* d, int* n);
+
+/*
  * u = sum_j c_j (A - d_j I)^{-1} f, stream-ordered on `stream` (a cudaStream_t; NULL = the
  * legacy default stream).  f and u are DEVICE arrays of N doubles owned by the caller (they
  * may alias each other).  The call returns once the solve has converged; u is complete when
@@ -199,10 +247,20 @@ int bura_solve_systems(bura_plan* plan, const double* f, double* V, double tol, 
  */
 int bura_apply_shifted(bura_plan* plan, const double* x, double* y, void* stream);
 
-/* c[0..k], d[0..k] (host arrays of k+1 doubles) and E of the plan's rational approximation. */
+/*
+ * The partial-fraction form of the plan's rational approximation, t^{-1} r(t) = sum_j c_j / (t - d_j)
+ * (eq. (simplified), Sec. 2.2): c[0..k] and d[0..k] are caller-owned HOST arrays of k+1 doubles,
+ * d[0] = 0 > d[1] > ... > d[k]; E (may be NULL) receives the error E_alpha(k,k;1) of Definition def-BURA
+ * (for plans set up with bura_setup_shifts: the caller's weights and shifts, and E = 0).
+ * Errors: BURA_EINVAL (null plan, c or d).
+ */
 int bura_get_rational(const bura_plan* plan, double* c, double* d, double* E);
 
-/* Statistics of the last solve (host struct). */
+/*
+ * Statistics of the last solve, copied into the caller's HOST struct: the scale Lambda of eq. (algebraic)
+ * (Sec. 1.4), E, the iteration counts and the residual-based bound on ||u - u_r|| / ||f|| of the partial-
+ * fraction value u_r of eq. (Rgeneral).  Errors: BURA_EINVAL (null plan or stats).
+ */
 int bura_get_stats(const bura_plan* plan, bura_stats* stats);
 
 /*
@@ -220,8 +278,8 @@ int bura_get_profile(const bura_plan* plan, int max_entries, bura_kernel_prof* o
 
 /*
  * Allocation-free residual norms (no counterpart in the paper; a service for callers that cannot
- * allocate device memory, e.g. inside a stream capture that must not allocate, under a caller-owned
- * memory pool, or in a loop that must never enter the allocator).
+ * allocate device memory: code that runs under a caller-owned memory pool or a fixed device-memory
+ * budget, or a loop that must never enter the allocator because an allocation there can block or fail).
  *   rr[j] = || f - (A - d[j] I) V_j ||_2^2 for j = 0..nsys-1, A the scaled constant-coefficient
  *   operator of `grid` (coef_kind must be BURA_COEF_CONSTANT), computed in FP64.
  *   d: HOST array of nsys shifts.  f: DEVICE array of N doubles.  V: DEVICE array of nsys*N doubles,
@@ -267,11 +325,37 @@ int bura_retarget(bura_plan* plan, double alpha);
  */
 int bura_solve_chain(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream);
 
-/* Frees every device and host resource of the plan (NULL is accepted). */
+/*
+ * Sum of the partial-fraction solves of several plans of one grid and operator:
+ *     u = sum_i sum_j c_{i,j} (A - d_{i,j} I)^{-1} f,
+ * each plan's weighted sum added into u in FP64 on the device (plans[0] writes u, the others add).  This
+ * runs a quadrature whose nodes are spread over several plans of bura_setup_shifts (eq. (BonitoPasciak),
+ * Sec. 5.3), or any sum of BURA solves.  f and u are DEVICE arrays of N doubles and must not alias when
+ * n > 1; stream-ordered on `stream`.  Each plan meets tol for its own term as bura_solve does.
+ * Errors: BURA_EINVAL (n < 1, a null plan, plans of different grids or devices, f == u with n > 1,
+ * tol <= 0), those of bura_solve.
+ */
+int bura_solve_sum(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream);
+
+/*
+ * Failure detection of the TMA-staged sweeps: set the budget (SM clocks, >= 0; 0 = the default of about 2 s)
+ * of their waits on the shared-memory ring for the later solves of this plan.  A budget shorter than a
+ * copy's latency makes the first waits give up: the kernel drains its copies in flight under the default
+ * budget, records the fault in the plan's CG state, and the solve returns BURA_ETIMEOUT; the plan stays
+ * usable.  Errors: BURA_EINVAL (null plan, cycles < 0).
+ */
+int bura_set_tma_wait_cycles(bura_plan* plan, long long cycles);
+
+/*
+ * Frees every device and host resource of the plan (NULL is accepted): the multigrid hierarchy, the
+ * shifted-system workspaces of eq. (Rgeneral) and the plan record.  The caller must not use the plan
+ * afterwards, and no solve of it may still be running on the device.  Always returns BURA_OK.
+ */
 int bura_destroy(bura_plan* plan);
 
-/* Batched solves: n independent problems, one per plan, solved concurrently on this GPU (the first row
- * of the "next" list of the build: many systems x shifts x right-hand sides in flight together).
+/* Batched solves: n independent problems, one per plan, solved concurrently on this GPU; every problem
+ * is one BURA solve of eq. (Rgeneral) (its k+1 shifted systems are independent), so many systems x shifts
+ * x right-hand sides are in flight together.
  *   plans[i]  plan of problem i (grid, coefficients, alpha, k, options of its own); a plan may appear
  *             only once in the list (its buffers serve one solve at a time);
  *   f[i]      device FP64 right-hand side of plan i's grid (N_i values, lexicographic, x fastest);

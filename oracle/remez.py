@@ -62,7 +62,7 @@ import functools
 
 import mpmath as mp
 
-__all__ = ["bura", "remez_bura", "partial_fractions", "error_at", "BuraResult"]
+__all__ = ["bura", "remez_bura", "partial_fractions", "BuraResult"]
 
 
 def _cheb(s, n):
@@ -420,8 +420,3 @@ def _continue_alpha(alpha, k, alpha0, pts0, dps, depth=0):
     _, _, _, pmid = _continue_alpha(mid, k, alpha0, pts0, dps, depth + 1)
     return _continue_alpha(alpha, k, mid, list(pmid), dps, depth + 1)
 
-
-def error_at(res, t):
-    """t^(1-alpha) - r(t) for a BuraResult (multi-precision)."""
-    t = mp.mpf(t)
-    return (t ** (1 - mp.mpf(res.alpha)) if t > 0 else mp.mpf(0)) - res.r(t)

@@ -35,7 +35,8 @@ class bura_options(C.Structure):
                 ("max_iters", C.c_int), ("max_outer", C.c_int), ("inner_rtol", C.c_double),
                 ("coarse_degree", C.c_int), ("block_points", C.c_int), ("blocks_per_sm", C.c_int),
                 ("coarse_kernel", C.c_int), ("cluster_size", C.c_int), ("sweeps", C.c_int),
-                ("refine", C.c_int), ("tma_stages", C.c_int), ("post_smooth_split", C.c_int)]
+                ("refine", C.c_int), ("tma_stages", C.c_int), ("post_smooth_split", C.c_int),
+                ("unscaled", C.c_int), ("tma_wait_cycles", C.c_longlong)]
 
 
 class bura_stats(C.Structure):
@@ -124,6 +125,12 @@ def _lib():
         L.bura_get_profile.argtypes = [P, I, C.POINTER(bura_kernel_prof), C.POINTER(I)]
         L.bura_retarget.argtypes = [P, D]
         L.bura_solve_chain.argtypes = [C.POINTER(P), I, P, P, D, P]
+        L.bura_setup_shifts.argtypes = [C.POINTER(bura_grid), C.POINTER(dp), I, dp, dp, C.POINTER(bura_options),
+                                        C.POINTER(P)]
+        L.bura_solve_sum.argtypes = [C.POINTER(P), I, P, P, D, P]
+        L.bura_scale.argtypes = [C.POINTER(bura_grid), C.POINTER(dp), dp]
+        L.bura_quadrature_bp15.argtypes = [D, D, D, I, dp, dp, C.POINTER(I)]
+        L.bura_set_tma_wait_cycles.argtypes = [P, C.c_longlong]
         L.bura_server_default_options.argtypes = [C.POINTER(bura_server_options)]
         L.bura_server_default_options.restype = None
         L.bura_server_create.argtypes = [C.POINTER(bura_server_options), C.POINTER(P)]
@@ -138,7 +145,8 @@ def _lib():
         for name in ("bura_rational", "bura_setup", "bura_solve", "bura_solve_host", "bura_solve_systems",
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
                      "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-                     "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_server_create", "bura_server_submit",
+                     "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts", "bura_solve_sum",
+                     "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_server_create", "bura_server_submit",
                      "bura_server_wait", "bura_server_get_stats", "bura_server_destroy"):
             getattr(L, name).restype = I
         _LIB = L
@@ -191,30 +199,83 @@ def bura_rational(alpha, k):
     return c, d, E.value
 
 
+def _faces_arg(faces, keep):
+    if faces is None:
+        return None
+    arr = (C.POINTER(C.c_double) * len(faces))()
+    for i, a in enumerate(faces):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        arr[i] = _hptr(a)
+    keep.append(arr)
+    return C.cast(arr, C.POINTER(C.POINTER(C.c_double)))
+
+
 def bura_setup(shape, alpha, k, faces=None, options=None):
     """Plan for an interior grid ``shape`` = (nx, ny) or (nx, ny, nz).
 
     faces: None (a = 1) or a tuple of float64 arrays (ax, ay[, az]) with the shapes of
     include/bura.h (numpy C order (nz, ny, nx+1) etc.).  Returns an opaque plan handle.
     """
-    g = bura_grid()
-    g.dim = len(shape)
-    for i, n in enumerate(shape[:3]):
-        g.n[i] = int(n)
-    g.coef_kind = BURA_COEF_CONSTANT if faces is None else BURA_COEF_FACES
+    g = _grid_of(shape, faces)
     keep = []
-    fptr = None
-    if faces is not None:
-        arr = (C.POINTER(C.c_double) * len(faces))()
-        for i, a in enumerate(faces):
-            a = np.ascontiguousarray(a, dtype=np.float64)
-            keep.append(a)
-            arr[i] = _hptr(a)
-        fptr = C.cast(arr, C.POINTER(C.POINTER(C.c_double)))
+    fptr = _faces_arg(faces, keep)
     opt = options if options is not None else bura_default_options()
     plan = C.c_void_p()
     _check(_lib().bura_setup(C.byref(g), fptr, float(alpha), int(k), C.byref(opt), C.byref(plan)), "bura_setup")
     return plan
+
+
+def bura_setup_shifts(shape, c, d, faces=None, options=None):
+    """Plan for u = sum_j c[j] (A - d[j] I)^{-1} f with caller-given weights c > 0 and shifts d <= 0."""
+    g = _grid_of(shape, faces)
+    keep = []
+    fptr = _faces_arg(faces, keep)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    if c.shape != d.shape or c.ndim != 1:
+        raise ValueError("c and d must be 1-D arrays of one length")
+    opt = options if options is not None else bura_default_options()
+    plan = C.c_void_p()
+    _check(_lib().bura_setup_shifts(C.byref(g), fptr, int(c.size), _hptr(c), _hptr(d), C.byref(opt), C.byref(plan)),
+           "bura_setup_shifts")
+    return plan
+
+
+def bura_scale(shape, faces=None):
+    """Lambda of the grid's operator (host only)."""
+    g = _grid_of(shape, faces)
+    keep = []
+    fptr = _faces_arg(faces, keep)
+    lam = C.c_double()
+    _check(_lib().bura_scale(C.byref(g), fptr, C.byref(lam)), "bura_scale")
+    return lam.value
+
+
+def bura_quadrature_bp15(alpha, kprime, Lam):
+    """(c, d) of the [BP15] sinc quadrature for the scaled operator (host only)."""
+    n = C.c_int()
+    rc = _lib().bura_quadrature_bp15(float(alpha), float(kprime), float(Lam), 0, None, None, C.byref(n))
+    if rc not in (BURA_OK, BURA_ERANGE):
+        raise BuraError(rc, "bura_quadrature_bp15")
+    c = np.zeros(n.value)
+    d = np.zeros(n.value)
+    _check(_lib().bura_quadrature_bp15(float(alpha), float(kprime), float(Lam), n.value, _hptr(c), _hptr(d),
+                                       C.byref(n)), "bura_quadrature_bp15")
+    return c, d
+
+
+def bura_solve_sum(plans, f, u, tol, stream=None):
+    """u = the sum of the plans' partial-fraction solves of f (device float64 tensors f, u)."""
+    P = C.c_void_p
+    pa = (P * max(len(plans), 1))(*[C.cast(p, P) for p in plans])
+    return _check(_lib().bura_solve_sum(pa, int(len(plans)), _dptr(f), _dptr(u), float(tol), _stream(stream)),
+                  "bura_solve_sum", allow=(BURA_ENOCONV,))
+
+
+def bura_set_tma_wait_cycles(plan, cycles):
+    """Budget of the TMA ring waits of later solves of the plan (0: the default)."""
+    return _check(_lib().bura_set_tma_wait_cycles(plan, int(cycles)), "bura_set_tma_wait_cycles")
 
 
 def bura_solve(plan, f, u, tol, stream=None):
@@ -416,6 +477,7 @@ def bura_destroy(plan):
 EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve", "bura_solve_host",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
             "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
-            "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_server_default_options",
+            "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts",
+            "bura_solve_sum", "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_server_default_options",
             "bura_server_create", "bura_server_submit", "bura_server_wait", "bura_server_get_stats",
             "bura_server_destroy"]

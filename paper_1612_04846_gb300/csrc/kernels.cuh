@@ -59,6 +59,7 @@ struct Scal {
     int max_it;           // cap on it (device-side loop control)
     int parity;           // which of the two direction buffers holds the current p
     int fault;            // set by a kernel whose bounded wait on its own copies gave up
+    long long wait_cycles;  // SM clocks a TMA kernel waits for one stage of its ring before giving up
 };
 
 // Chebyshev step coefficients of one level: d_m = c1 d_{m-1} + c2 Dinv res (c2 includes 1/(diag - d)
@@ -224,7 +225,9 @@ void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, 
                       const double* scale, cudaStream_t s);
 void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const double* invscale, float* r32,
                    float* x32, float* p32, cudaStream_t s);
-void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s);
+// u = sum_j c_j v_j (accumulate = 0) or u += sum_j c_j v_j (accumulate = 1), j = 0..K-1 in order.
+void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, int accumulate,
+                         cudaStream_t s);
 void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s);
 void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s);
 void launch_scatter_systems(long long N, int Kp, int K, const double* X, double* x, cudaStream_t s);
@@ -247,7 +250,7 @@ void launch_update_residual_df(const Launch& g, const Lev& L, int dim, bool var,
 void launch_cast_f_df(const Launch& g32, long long N, int K, const double* f, double sf, float* r32, float* x32,
                       float* p32, float* fh, float* fl, cudaStream_t s);
 void launch_weighted_sum_df(long long N, int Kp, int K, const float* vh, const float* vl, const float* ch,
-                            const float* cl, double* u, cudaStream_t s);
+                            const float* cl, double* u, int accumulate, cudaStream_t s);
 void launch_gather_df(long long N, int Kp, int K, const float* vh, const float* vl, double* V, cudaStream_t s);
 
 }  // namespace bura

@@ -185,7 +185,8 @@ __global__ void k_cast_f_df(int N, int Kp, int K, const double* __restrict__ f, 
 
 // u = sum_j c_j v_j in df, converted to FP64 once per point.
 __global__ void k_weighted_sum_df(int N, int Kp, int K, const float* __restrict__ vh, const float* __restrict__ vl,
-                                  const float* __restrict__ ch, const float* __restrict__ cl, double* __restrict__ u) {
+                                  const float* __restrict__ ch, const float* __restrict__ cl, double* __restrict__ u,
+                                  int accumulate) {
     __shared__ float sh[KMAXP], sl[KMAXP];
     if (threadIdx.x < KMAXP) {
         sh[threadIdx.x] = threadIdx.x < K ? ch[threadIdx.x] : 0.f;
@@ -205,7 +206,8 @@ __global__ void k_weighted_sum_df(int N, int Kp, int K, const float* __restrict_
                 s = df_add(s, df_mul(dfv{sh[j], sl[j]}, dfv{ah[v], bl[v]}));
             }
         }
-        u[P] = (double)s.hi + (double)s.lo;
+        const double w = (double)s.hi + (double)s.lo;
+        u[P] = accumulate ? u[P] + w : w;
     }
 }
 
@@ -260,10 +262,10 @@ void launch_cast_f_df(const Launch& g32, long long N, int K, const double* f, do
 }
 
 void launch_weighted_sum_df(long long N, int Kp, int K, const float* vh, const float* vl, const float* ch,
-                            const float* cl, double* u, cudaStream_t s) {
+                            const float* cl, double* u, int accumulate, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (int)std::min<long long>((N + threads - 1) / threads, 152LL * 16);
-    k_weighted_sum_df<<<blocks, threads, 0, s>>>((int)N, Kp, K, vh, vl, ch, cl, u);
+    k_weighted_sum_df<<<blocks, threads, 0, s>>>((int)N, Kp, K, vh, vl, ch, cl, u, accumulate);
 }
 
 void launch_gather_df(long long N, int Kp, int K, const float* vh, const float* vl, double* V, cudaStream_t s) {

@@ -218,7 +218,7 @@ void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const
 
 // u = sum_j c_j v_j (FP64, fixed order j = 0..K-1); one thread per point.
 __global__ void k_weighted_sum(int N, int Kp, int K, const double* __restrict__ v, const double* __restrict__ c,
-                               double* __restrict__ u) {
+                               double* __restrict__ u, int accumulate) {
     __shared__ double cs[KMAXP];
     if (threadIdx.x < KMAXP) cs[threadIdx.x] = threadIdx.x < K ? c[threadIdx.x] : 0.0;
     __syncthreads();
@@ -230,7 +230,7 @@ __global__ void k_weighted_sum(int N, int Kp, int K, const double* __restrict__ 
             s = fma(cs[2 * q], a.x, s);
             s = fma(cs[2 * q + 1], a.y, s);
         }
-        u[P] = s;
+        u[P] = accumulate ? u[P] + s : s;
     }
 }
 
@@ -239,8 +239,9 @@ static int grid1(long long N, int bs) {
     return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
 }
 
-void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, cudaStream_t s) {
-    k_weighted_sum<<<grid1(N, 256), 256, 0, s>>>((int)N, Kp, K, v, c, u);
+void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, int accumulate,
+                         cudaStream_t s) {
+    k_weighted_sum<<<grid1(N, 256), 256, 0, s>>>((int)N, Kp, K, v, c, u, accumulate);
 }
 
 __global__ void k_gather(int N, int Kp, int K, const double* __restrict__ v, double* __restrict__ V) {

@@ -97,9 +97,10 @@ __device__ __forceinline__ bool tile_loop(int ntiles, int S, unsigned char* smem
             issue(smem + s * sbytes, (int)blockIdx.x + s * (int)gridDim.x, &bars[s]);
     int k = 0;
     bool ok = true;
+    const long long budget = scal->wait_cycles > 0 ? scal->wait_cycles : kTmaWaitCycles;
     for (; k < nmine; ++k) {
         const int s = k % S;
-        const bool got = mbar_wait_bounded(&bars[s], (unsigned)(k / S) & 1u);
+        const bool got = mbar_wait_bounded(&bars[s], (unsigned)(k / S) & 1u, budget);
         if constexpr (SYNC_COMPUTE) {
             if (__syncthreads_or(!got)) { ok = false; break; }
             compute(smem + s * sbytes, (int)blockIdx.x + k * (int)gridDim.x);
@@ -114,9 +115,10 @@ __device__ __forceinline__ bool tile_loop(int ntiles, int S, unsigned char* smem
             issue(smem + s * sbytes, (int)blockIdx.x + (k + S) * (int)gridDim.x, &bars[s]);
     }
     if (!ok) {
-        // tiles k .. k+S-1 may still have copies in flight into this CTA's shared memory
+        // tiles k .. k+S-1 may still have copies in flight into this CTA's shared memory: drained under
+        // the full budget, so no CTA exits while a copy can still write its shared memory
         for (int j = k; j < nmine && j < k + S; ++j)
-            (void)mbar_wait_bounded(&bars[j % S], (unsigned)(j / S) & 1u);
+            (void)mbar_wait_bounded(&bars[j % S], (unsigned)(j / S) & 1u, kTmaWaitCycles);
         if (tid == 0) atomicExch(&scal->fault, 1);
         __syncthreads();
     }

@@ -128,6 +128,9 @@ struct bura_plan {
     bool var = false;
     int k = 0, K = 0;
     double alpha = 0, E = 0, Lambda = 0, lambda_lo = 0;
+    bool shifts_only = false;  // set up by bura_setup_shifts: caller-given weights and shifts, no alpha
+    double out_scale = 1.0;    // factor of the weights in the output sum (Lambda^-alpha with opt.unscaled)
+    long long wait_cycles = 0; // budget of the TMA ring waits (0: the kernels' default)
     std::vector<double> c, d;
     bura_options opt{};
     std::vector<HostLevel> hl;
@@ -1081,6 +1084,7 @@ int init_scal(bura_plan* p, Scal* dev, const double* thr, const int* active, cud
     h.it = 0;
     h.max_it = p->opt.max_iters;
     h.parity = 0;
+    h.wait_cycles = p->wait_cycles;
     *p->hscal = h;
     CK(cudaMemcpyAsync(dev, p->hscal, sizeof(Scal), cudaMemcpyHostToDevice, s));
     return BURA_OK;
@@ -1212,7 +1216,7 @@ int solve_mixed_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) 
         CA(init_scal(p, w.scal, thr, act, s));
         int it = 0;
         int irc = pcg<float>(p, w, &it, s);
-        if (irc == BURA_ENOTSPD) return irc;
+        if (irc == BURA_ENOTSPD || irc == BURA_ETIMEOUT) return irc;
         for (int j = 0; j < p->K; ++j) siters[j] += p->hscal->iters[j];
         total_it += it;
         traced(p, K_CORR64, false, true, vbytes<double>(p, 0, 2.0, false) + vbytes<float>(p, 0, 1.0, false), s,
@@ -1349,7 +1353,7 @@ int upload_df_tables(bura_plan* p) {
     for (int j = 0; j < p->K; ++j) {
         split_df(diag - p->d[j], &t[j], &t[KMAXP + j]);
         split_df(p->d[j], &t[2 * KMAXP + j], &t[3 * KMAXP + j]);
-        split_df(p->c[j], &t[4 * KMAXP + j], &t[5 * KMAXP + j]);
+        split_df(p->c[j] * p->out_scale, &t[4 * KMAXP + j], &t[5 * KMAXP + j]);
     }
     CK(cudaMemcpy(const_cast<float*>(p->dfop.ch), t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
     return BURA_OK;
@@ -1393,6 +1397,18 @@ int build_df(bura_plan* p) {
     return BURA_OK;
 }
 
+// The weights c_j (times the output scale) of the output sum and the shifts of the outer (refinement) CG state record.
+int upload_outer(bura_plan* p) {
+    std::vector<double> cc(KMAXP, 0.0);
+    for (int j = 0; j < p->K; ++j) cc[j] = p->c[j] * p->out_scale;
+    CK(cudaMemcpy(p->cdev, cc.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice));
+    Scal so;
+    std::memset(&so, 0, sizeof(so));
+    for (int j = 0; j < p->K; ++j) so.dsh[j] = p->d[j];
+    CK(cudaMemcpy(p->scal_outer, &so, sizeof(Scal), cudaMemcpyHostToDevice));
+    return BURA_OK;
+}
+
 // Where the solutions are: FP64 path w64.x, mixed path with FP64 refinement v64 (both Kp64 layout),
 // mixed path with double-float refinement the FP32 pairs vh/vl[vcur] (Kp32 layout).
 bool df_solution(const bura_plan* p) {
@@ -1433,39 +1449,32 @@ void bura_default_options(bura_options* opt) {
     opt->max_outer = 12;
     opt->inner_rtol = 1e-5;
     opt->coarse_degree = 0;
+    opt->unscaled = 0;
+    opt->tma_wait_cycles = 0;
 }
 
-// The weights c_j of the output sum and the shifts of the outer (refinement) CG state record.
-int upload_outer(bura_plan* p) {
-    std::vector<double> cc(KMAXP, 0.0);
-    for (int j = 0; j < p->K; ++j) cc[j] = p->c[j];
-    CK(cudaMemcpy(p->cdev, cc.data(), KMAXP * sizeof(double), cudaMemcpyHostToDevice));
-    Scal so;
-    std::memset(&so, 0, sizeof(so));
-    for (int j = 0; j < p->K; ++j) so.dsh[j] = p->d[j];
-    CK(cudaMemcpy(p->scal_outer, &so, sizeof(Scal), cudaMemcpyHostToDevice));
+
+}  // extern "C"
+
+namespace {
+
+// Grid and coefficient checks shared by the setup entry points; *N receives the number of points.
+int check_grid(const bura_grid* grid, const double* const* faces, long long* N) {
+    if (!grid) return BURA_EINVAL;
+    if (grid->dim != 2 && grid->dim != 3) return BURA_EINVAL;
+    if (grid->coef_kind != BURA_COEF_CONSTANT && grid->coef_kind != BURA_COEF_FACES) return BURA_EINVAL;
+    long long n = 1;
+    for (int a = 0; a < grid->dim; ++a) {
+        if (grid->n[a] < 1) return BURA_EINVAL;
+        n *= grid->n[a];
+    }
+    if (grid->coef_kind == BURA_COEF_FACES && !faces) return BURA_EINVAL;
+    if (n * 16 >= (1LL << 31)) return BURA_ERANGE;
+    *N = n;
     return BURA_OK;
 }
 
-int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, int k, const bura_options* opt,
-               bura_plan** out) {
-    if (!grid || !out) return BURA_EINVAL;
-    *out = nullptr;
-    if (grid->dim != 2 && grid->dim != 3) return BURA_EINVAL;
-    if (grid->coef_kind != BURA_COEF_CONSTANT && grid->coef_kind != BURA_COEF_FACES) return BURA_EINVAL;
-    if (!(alpha > 0 && alpha < 1) || k < 1 || k > BURA_MAX_K) return BURA_EINVAL;
-    const int dim = grid->dim;
-    long long N = 1;
-    for (int a = 0; a < dim; ++a) {
-        if (grid->n[a] < 1) return BURA_EINVAL;
-        N *= grid->n[a];
-    }
-    const bool var = grid->coef_kind == BURA_COEF_FACES;
-    if (var && !faces) return BURA_EINVAL;
-    if ((long long)N * 16 >= (1LL << 31)) return BURA_ERANGE;
-    bura_options o;
-    bura_default_options(&o);
-    if (opt) o = *opt;
+int check_options(const bura_options& o) {
     if (o.precision != BURA_PREC_FP64 && o.precision != BURA_PREC_MIXED) return BURA_EINVAL;
     if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio > 1) || o.max_iters < 1 ||
         o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000 ||
@@ -1475,24 +1484,33 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
           o.cluster_size == 16) ||
         o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
         o.refine > BURA_REFINE_DF || o.tma_stages < 0 || o.tma_stages > 4 || o.post_smooth_split < 0 ||
-        o.post_smooth_split > 1)
+        o.post_smooth_split > 1 || o.unscaled < 0 || o.unscaled > 1 || o.tma_wait_cycles < 0)
         return BURA_EINVAL;
+    return BURA_OK;
+}
 
+// A plan for the K weights c and shifts d (d[0] >= d[1] >= ... , all <= 0, c > 0) of a partial-fraction
+// sum u = sum_j c_j (A - d_j I)^{-1} f on the grid: scaling, multigrid hierarchy, tables, workspaces.
+int setup_plan(const bura_grid* grid, const double* const* faces, long long N, int K, const double* c,
+               const double* d, double E, double alpha, bool shifts_only, const bura_options& o, bura_plan** out) {
+    const int dim = grid->dim;
+    const bool var = grid->coef_kind == BURA_COEF_FACES;
     std::shared_lock<std::shared_mutex> guard(g_capture_guard);
     bura_plan* p = new (std::nothrow) bura_plan();
     if (!p) return BURA_ENOMEM;
     auto fail = [&](int rc) { destroy_plan(p); return rc; };
     p->dim = dim;
     p->var = var;
-    p->k = k;
-    p->K = k + 1;
+    p->k = K - 1;
+    p->K = K;
     p->alpha = alpha;
+    p->shifts_only = shifts_only;
     p->opt = o;
-    p->c.assign(p->K, 0.0);
-    p->d.assign(p->K, 0.0);
-    int rc = bura_rational(alpha, k, p->c.data(), p->d.data(), &p->E);
-    if (rc != BURA_OK) return fail(rc);
-
+    p->wait_cycles = o.tma_wait_cycles;
+    p->c.assign(c, c + K);
+    p->d.assign(d, d + K);
+    p->E = E;
+    int rc = BURA_OK;
     // fine level
     HostLevel h0;
     h0.n[0] = grid->n[0];
@@ -1529,6 +1547,7 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
         level_bounds(h, dim, var, p->Lambda);
     }
     p->lambda_lo = p->hl[0].lmin * (1.0 - 1e-12);
+    p->out_scale = o.unscaled ? std::pow(p->Lambda, -alpha) : 1.0;
 
     if (cudaGetDevice(&p->dev) != cudaSuccess) return fail(BURA_ECUDA);
     if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1574,26 +1593,127 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(BURA_ECUDA);
     p->st.Lambda = p->Lambda;
     p->st.E = p->E;
-    p->st.k = k;
+    p->st.k = K - 1;
     p->st.levels = (int)p->hl.size();
     p->st.lambda_lo = p->lambda_lo;
     *out = p;
     return BURA_OK;
 }
 
-int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* stream) {
-    if (!p || !f || !u) return BURA_EINVAL;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+}  // namespace
+
+extern "C" {
+
+int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, int k, const bura_options* opt,
+               bura_plan** out) {
+    if (!out) return BURA_EINVAL;
+    *out = nullptr;
+    long long N = 0;
+    CA(check_grid(grid, faces, &N));
+    if (!(alpha > 0 && alpha < 1) || k < 1 || k > BURA_MAX_K) return BURA_EINVAL;
+    bura_options o;
+    bura_default_options(&o);
+    if (opt) o = *opt;
+    CA(check_options(o));
+    std::vector<double> c(k + 1, 0.0), d(k + 1, 0.0);
+    double E = 0.0;
+    CA(bura_rational(alpha, k, c.data(), d.data(), &E));
+    return setup_plan(grid, faces, N, k + 1, c.data(), d.data(), E, alpha, false, o, out);
+}
+
+int bura_scale(const bura_grid* grid, const double* const* faces, double* Lambda) {
+    long long N = 0;
+    if (!Lambda) return BURA_EINVAL;
+    CA(check_grid(grid, faces, &N));
+    const int dim = grid->dim;
+    const bool var = grid->coef_kind == BURA_COEF_FACES;
+    HostLevel h0;
+    h0.n[0] = grid->n[0];
+    h0.n[1] = grid->n[1];
+    h0.n[2] = dim == 3 ? grid->n[2] : 1;
+    h0.N = N;
+    for (int a = 0; a < 3; ++a) h0.h[a] = 1.0 / (h0.n[a] + 1);
+    if (var) {
+        const size_t sz[3] = {(size_t)h0.n[2] * h0.n[1] * (h0.n[0] + 1), (size_t)h0.n[2] * (h0.n[1] + 1) * h0.n[0],
+                              (size_t)(h0.n[2] + 1) * h0.n[1] * h0.n[0]};
+        for (int a = 0; a < dim; ++a) {
+            if (!faces[a]) return BURA_EINVAL;
+            h0.a[a].assign(faces[a], faces[a] + sz[a]);
+            for (double v : h0.a[a])
+                if (!(v > 0) || !std::isfinite(v)) return BURA_EINVAL;
+        }
+    }
+    *Lambda = gershgorin(h0, dim, var);
+    return BURA_OK;
+}
+
+int bura_quadrature_bp15(double alpha, double kprime, double Lambda, int cap, double* c, double* d, int* n) {
+    if (!n || !(alpha > 0 && alpha < 1) || !(kprime > 0) || !std::isfinite(kprime) || !(Lambda > 0) ||
+        !std::isfinite(Lambda) || cap < 0 || (cap > 0 && (!c || !d)))
+        return BURA_EINVAL;
+    // node counts below and above l = 0 that balance the three error terms of the quadrature
+    const double lo = std::ceil(M_PI * M_PI / (4.0 * alpha * kprime * kprime));
+    const double hi = std::ceil(M_PI * M_PI / (4.0 * (1.0 - alpha) * kprime * kprime));
+    if (lo + hi + 1 > 1e6) return BURA_ERANGE;
+    const int m = (int)lo, M = (int)hi;
+    *n = m + M + 1;
+    if (*n > cap) return BURA_ERANGE;
+    const double pre = 2.0 * kprime * std::sin(M_PI * alpha) / M_PI * std::pow(Lambda, alpha - 1.0);
+    for (int l = -m; l <= M; ++l) {
+        // (e^{-2lk'} I + Atilde)^{-1} = Lambda^{-1} (A - d_l I)^{-1} with d_l = -e^{-2lk'} / Lambda
+        c[l + m] = pre * std::exp(2.0 * (alpha - 1.0) * l * kprime);
+        d[l + m] = -std::exp(-2.0 * l * kprime) / Lambda;
+    }
+    return BURA_OK;
+}
+
+int bura_setup_shifts(const bura_grid* grid, const double* const* faces, int nsys, const double* c, const double* d,
+                      const bura_options* opt, bura_plan** out) {
+    if (!out) return BURA_EINVAL;
+    *out = nullptr;
+    long long N = 0;
+    CA(check_grid(grid, faces, &N));
+    if (!c || !d || nsys < 1) return BURA_EINVAL;
+    if (nsys > BURA_MAX_K + 1) return BURA_ERANGE;
+    bura_options o;
+    bura_default_options(&o);
+    if (opt) o = *opt;
+    CA(check_options(o));
+    if (o.unscaled) return BURA_EINVAL;  // no fractional power to undo the scaling with
+    std::vector<std::pair<double, double>> cd;
+    for (int j = 0; j < nsys; ++j) {
+        if (!(c[j] > 0) || !std::isfinite(c[j]) || !(d[j] <= 0) || !std::isfinite(d[j])) return BURA_EINVAL;
+        cd.push_back({d[j], c[j]});
+    }
+    // the system nearest d = 0 (the hardest) first, as the BURA poles d_0 = 0 > d_1 > ...
+    std::stable_sort(cd.begin(), cd.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<double> cs(nsys), ds(nsys);
+    for (int j = 0; j < nsys; ++j) {
+        ds[j] = cd[j].first;
+        cs[j] = cd[j].second;
+    }
+    return setup_plan(grid, faces, N, nsys, cs.data(), ds.data(), 0.0, 0.0, true, o, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The solve and the output sum u = sum_j c_j v_j (accumulate = 1: u += ...), stream-ordered on s.
+int solve_into(bura_plan* p, const double* f, double* u, double tol, cudaStream_t s, int accumulate) {
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     const double N = (double)p->hl[0].N;
+    const double wbytes = N * p->K * 8.0 + N * 8.0 * (accumulate ? 2.0 : 1.0);
     if (df_solution(p))
-        traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s, [&] {
-            launch_weighted_sum_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], p->cwh, p->cwl, u, s);
+        traced(p, K_WSUM, false, true, wbytes, s, [&] {
+            launch_weighted_sum_df(p->hl[0].N, p->w32.Kp, p->K, p->vh[p->vcur], p->vl[p->vcur], p->cwh, p->cwl, u,
+                                   accumulate, s);
         });
     else
-        traced(p, K_WSUM, false, true, N * p->K * 8.0 + N * 8.0, s,
-               [&] { launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), p->cdev, u, s); });
+        traced(p, K_WSUM, false, true, wbytes, s,
+               [&] { launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), p->cdev, u, accumulate, s); });
     CKL();
     CK(cudaEventRecord(p->done, s));
     p->st.launches = p->tr.launches;
@@ -1604,16 +1724,45 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
     return rc;
 }
 
+// Plans of one grid and operator on one device (bura_solve_chain, bura_solve_sum).
+bool same_operator(const bura_plan* a, const bura_plan* b) {
+    return a->dim == b->dim && a->var == b->var && a->hl[0].n[0] == b->hl[0].n[0] && a->hl[0].n[1] == b->hl[0].n[1] &&
+           a->hl[0].n[2] == b->hl[0].n[2] && a->dev == b->dev;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* stream) {
+    if (!p || !f || !u) return BURA_EINVAL;
+    return solve_into(p, f, u, tol, reinterpret_cast<cudaStream_t>(stream), 0);
+}
+
+int bura_solve_sum(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream) {
+    if (!plans || n < 1 || !f || !u || !(tol > 0)) return BURA_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!plans[i] || !same_operator(plans[i], plans[0])) return BURA_EINVAL;
+    if (f == u && n > 1) return BURA_EINVAL;  // every term reads f after the first has written u
+    int out = BURA_OK;
+    for (int i = 0; i < n; ++i) {
+        const int rc = solve_into(plans[i], f, u, tol, reinterpret_cast<cudaStream_t>(stream), i > 0 ? 1 : 0);
+        if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
+        if (rc == BURA_ENOCONV) out = BURA_ENOCONV;
+    }
+    return out;
+}
+
+int bura_set_tma_wait_cycles(bura_plan* p, long long cycles) {
+    if (!p || cycles < 0) return BURA_EINVAL;
+    p->wait_cycles = cycles;  // read by the next solve's CG state records
+    return BURA_OK;
+}
+
 int bura_solve_chain(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream) {
     if (!plans || n < 1 || !f || !u || !(tol > 0)) return BURA_EINVAL;
-    for (int i = 0; i < n; ++i) {
-        if (!plans[i]) return BURA_EINVAL;
-        const bura_plan* a = plans[i];
-        const bura_plan* b = plans[0];
-        if (a->dim != b->dim || a->var != b->var || a->hl[0].n[0] != b->hl[0].n[0] || a->hl[0].n[1] != b->hl[0].n[1] ||
-            a->hl[0].n[2] != b->hl[0].n[2] || a->dev != b->dev)
-            return BURA_EINVAL;
-    }
+    for (int i = 0; i < n; ++i)
+        if (!plans[i] || !same_operator(plans[i], plans[0])) return BURA_EINVAL;
     int out = BURA_OK;
     const double* in = f;
     for (int i = 0; i < n; ++i) {
@@ -1795,7 +1944,7 @@ int bura_destroy(bura_plan* p) {
 
 
 int bura_retarget(bura_plan* p, double alpha) {
-    if (!p || !(alpha > 0 && alpha < 1)) return BURA_EINVAL;
+    if (!p || !(alpha > 0 && alpha < 1) || p->shifts_only) return BURA_EINVAL;
     std::vector<double> c(p->K, 0.0), d(p->K, 0.0);
     double E = 0.0;
     int rc = bura_rational(alpha, p->k, c.data(), d.data(), &E);
@@ -1808,6 +1957,7 @@ int bura_retarget(bura_plan* p, double alpha) {
     p->c = c;
     p->d = d;
     p->E = E;
+    if (p->opt.unscaled) p->out_scale = std::pow(p->Lambda, -alpha);
     CA(upload_tables<double>(p, p->w64));
     if (p->opt.precision == BURA_PREC_MIXED) CA(upload_tables<float>(p, p->w32));
     if (p->dfop.ch) CA(upload_df_tables(p));

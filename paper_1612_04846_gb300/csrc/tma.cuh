@@ -1,9 +1,10 @@
 // TMA (cp.async.bulk.tensor) and mbarrier helpers in inline PTX, and the host-side declarations of
 // the TMA-staged fine-level sweeps (kernels_tma.cu).
 //
-// Every wait on an mbarrier is bounded in time: after kTmaWaitCycles SM clocks without the phase
-// completing, the wait gives up and the kernel records a fault in its Scal record (the host returns
-// BURA_ETIMEOUT) instead of spinning forever.
+// Every wait on an mbarrier is bounded in time: after a budget of SM clocks without the phase completing
+// (kTmaWaitCycles unless the plan sets another, Scal::wait_cycles), the wait gives up and the kernel
+// records a fault in its Scal record (the host returns BURA_ETIMEOUT) instead of spinning forever.  The
+// copies still in flight are then drained under the full kTmaWaitCycles budget before the CTA exits.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -86,11 +87,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier; false if it did not complete within kTmaWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// Non-blocking test of phase `parity`.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Budgets below this many SM clocks poll with the non-blocking test (a blocking try_wait may suspend
+// the thread for longer than such a budget).
+constexpr long long kTmaShortWait = 100000;
+
+// Wait for phase `parity` of the barrier; false if it did not complete within `budget` SM clocks.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long budget) {
     const long long t0 = clock64();
+    if (budget < kTmaShortWait) {
+        while (!mbar_test_wait(bar, parity))
+            if (clock64() - t0 > budget) return false;
+        return true;
+    }
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kTmaWaitCycles) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 

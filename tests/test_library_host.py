@@ -55,7 +55,8 @@ def test_setup_rejects_bad_arguments_on_the_host(lib, shape, alpha, k):
 
 
 @pytest.mark.parametrize("field,value", [("coarse_kernel", -1), ("coarse_kernel", 4), ("cluster_size", 3),
-                                         ("cluster_size", 32), ("smoother_degree", 0), ("inner_rtol", 1.0)])
+                                         ("cluster_size", 32), ("smoother_degree", 0), ("inner_rtol", 1.0),
+                                         ("unscaled", 2), ("unscaled", -1), ("tma_wait_cycles", -1)])
 def test_setup_rejects_bad_options_on_the_host(lib, field, value):
     o = lib.bura_default_options()
     assert o.coarse_kernel == lib.BURA_COARSE_AUTO and o.cluster_size == 0
@@ -185,3 +186,63 @@ def test_library_rational_rejects_bad_input(lib):
         with pytest.raises(lib.BuraError) as ei:
             lib.bura_rational(a, k)
         assert ei.value.code == lib.BURA_EINVAL
+
+
+@pytest.mark.parametrize("c,d,code", [([1.0, 0.0], [0.0, -1.0], "EINVAL"), ([1.0, 1.0], [0.0, 0.5], "EINVAL"),
+                                      ([1.0, float("nan")], [0.0, -1.0], "EINVAL"), ([], [], "EINVAL"),
+                                      ([1.0] * 14, [-1.0] * 14, "ERANGE")])
+def test_setup_shifts_rejects_bad_weights_and_shifts_on_the_host(lib, c, d, code):
+    """bura_setup_shifts (the partial-fraction form of a quadrature, eq. (BonitoPasciak)): positive weights,
+    non-positive shifts and at most BURA_MAX_K + 1 systems, checked before any CUDA call."""
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup_shifts((31, 31), c, d)
+    assert ei.value.code == getattr(lib, "BURA_" + code)
+
+
+def test_setup_shifts_rejects_the_unscaled_option(lib):
+    o = lib.bura_default_options()
+    o.unscaled = 1
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup_shifts((31, 31), [1.0], [-0.5], options=o)
+    assert ei.value.code == lib.BURA_EINVAL
+
+
+def test_sum_and_wait_budget_arguments_on_the_host(lib):
+    import ctypes as C
+    L = lib._lib()
+    P = C.c_void_p
+    nulls = (P * 1)()
+    assert L.bura_solve_sum(None, 1, None, None, 1e-6, None) == lib.BURA_EINVAL
+    assert L.bura_solve_sum(nulls, 0, None, None, 1e-6, None) == lib.BURA_EINVAL
+    assert L.bura_solve_sum(nulls, 1, P(16), P(32), 1e-6, None) == lib.BURA_EINVAL  # a null plan
+    assert L.bura_set_tma_wait_cycles(None, 100) == lib.BURA_EINVAL
+
+
+@pytest.mark.parametrize("shape,var", [((31, 31), False), ((1023, 1023), False), ((7, 5, 3), False),
+                                       ((15, 9, 7), True), ((33, 17), True)])
+def test_scale_matches_the_oracle_gershgorin_bound(lib, shape, var):
+    """bura_scale: Lambda of eq. (algebraic) equals the oracle's max absolute row sum of Atilde."""
+    from oracle import operators
+    from paper_1612_04846_gb300 import workloads as W
+    nps = tuple(reversed(shape))
+    faces = W.block_lognormal_faces(nps, 2, 1e-2, 1.0, 3) if var else None
+    _, lam = operators.scaled_matrix(nps, faces)
+    assert lib.bura_scale(shape, faces) == pytest.approx(lam, rel=1e-14)
+
+
+@pytest.mark.parametrize("alpha,kp", [(0.25, 0.5), (0.5, 1.0 / 3.0), (0.75, 0.7), (0.5, 1.0)])
+def test_bp15_nodes_match_the_oracle(lib, alpha, kp):
+    """bura_quadrature_bp15 gives the oracle's weights and shifts of eq. (BonitoPasciak) (1e-14), in the
+    same order l = -m..M, and reports the node count when the capacity is short."""
+    from oracle import quadrature
+    lam = 8.0 * 1024 ** 2
+    c, d = lib.bura_quadrature_bp15(alpha, kp, lam)
+    co, do = quadrature.bp15_shifts(alpha, kp, lam)
+    assert len(c) == len(co)
+    np.testing.assert_allclose(c, co, rtol=1e-14)
+    np.testing.assert_allclose(d, do, rtol=1e-14)
+    import ctypes as C
+    n = C.c_int()
+    buf = np.zeros(2)
+    rc = lib._lib().bura_quadrature_bp15(alpha, kp, lam, 2, lib._hptr(buf), lib._hptr(buf.copy()), C.byref(n))
+    assert rc == lib.BURA_ERANGE and n.value == len(co)

@@ -115,3 +115,20 @@ def test_positive_coefficients_keep_the_sum_stable():
     assert np.all(terms > 0)
     val = terms.sum(axis=0)
     assert np.all(np.abs(val - lam ** -0.5) <= e["E"] / lam * (1 + 1e-12))
+
+
+@pytest.mark.parametrize("shape", [(31, 31), (7, 7, 7), (9, 6)])
+def test_dst_components_match_sparse_direct(shape):
+    """eq. (Rgeneral), eq. (exacalg): every component v_j = (A - d_j I)^{-1} f of the DST eigenbasis
+    equals the sparse LU solve of that shifted system, and sum_j c_j v_j is the exact BURA value.
+    A slip in one shift (a sign of d_j, a dropped system) fails the per-component check."""
+    e = tables.entry(0.5, 7)
+    A, _ = operators.scaled_matrix(shape)
+    f = W.rhs_uniform(shape, 5)
+    comp = exact.bura_components(shape, f, e["d"])
+    ref = direct.shifted_solves_sparse(A, f, e["d"])
+    assert comp.shape == ref.shape == (len(e["d"]), int(np.prod(shape)))
+    for j in range(len(e["d"])):
+        assert _rel(comp[j], ref[j]) < 1e-12, j
+    total = sum(float(cj) * vj for cj, vj in zip(e["c"], comp))
+    assert _rel(total, exact.bura_value(shape, f, e["c"], e["d"])) < 1e-13
