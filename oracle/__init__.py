@@ -21,6 +21,11 @@ exact      closed-form sine-transform eigenbasis solutions on constant-
 direct     the same two quantities for any operator: sparse direct solves of
            every shifted system (eq. (Rgeneral)), and dense eigendecomposition
            for tiny matrices (eq. (exacalg)).
+pcg        the same method on the CPU for any operator: every shifted system solved on its own by
+           multigrid-preconditioned CG in FP64 (C with OpenMP, oracle/cpu_pcg.c), then the
+           weighted sum of eq. (Rgeneral); the oracle of the variable-coefficient operators and
+           the timed same-method CPU baseline.
+quadrature the sinc quadrature of [BP15] of the paper's comparison (eq. (BonitoPasciak), Sec. 5.3).
 tables     lookup of the committed oracle-generated coefficient table.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
