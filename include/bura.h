@@ -90,8 +90,9 @@ typedef enum {
 typedef struct {
     int precision;        /* bura_precision; default BURA_PREC_MIXED */
     int smoother_degree;  /* Chebyshev degree of each pre/post smoothing; default 2 */
-    double smoother_ratio;/* Chebyshev interval [lmax/ratio, lmax] of D^{-1}(A - d I); default 4 (the upper
-                             quarter of the spectrum, which full coarsening leaves to the smoother) */
+    double smoother_ratio;/* Chebyshev interval [lmax/ratio, lmax] of D^{-1}(A - d I), ratio > 1; 0 (default) =
+                             auto: 4 in 2-D, 8 in 3-D (the band of the spectrum that full coarsening leaves to
+                             the smoother is wider for the 7-point operator) */
     int max_iters;        /* cap on PCG iterations per (inner) solve; default 200 */
     int max_outer;        /* cap on FP64 refinement steps (mixed precision); default 12 */
     double inner_rtol;    /* largest relative residual reduction asked of one FP32 inner solve; the FP64
@@ -122,6 +123,11 @@ typedef struct {
                              before it gives up, records a fault and the solve returns BURA_ETIMEOUT; 0 = the
                              default (about 2 s).  Copies still in flight are always drained under the
                              default budget before a kernel exits.  See bura_set_tma_wait_cycles. */
+    int smoother_bf16;    /* variable coefficients, mixed precision: 1 stores the face weights that the
+                             multigrid V-cycle (smoothing, residuals, coarse levels) reads as bfloat16 (the CG
+                             operator and the FP64 refinement keep FP32/FP64 weights, so the solution's
+                             accuracy is unchanged; only the preconditioner sees the rounded field); each
+                             level's diagonal is summed from its stored weights; default 0 */
 } bura_options;
 
 /* Statistics of the last bura_solve*/

@@ -36,7 +36,7 @@ class bura_options(C.Structure):
                 ("coarse_degree", C.c_int), ("block_points", C.c_int), ("blocks_per_sm", C.c_int),
                 ("coarse_kernel", C.c_int), ("cluster_size", C.c_int), ("sweeps", C.c_int),
                 ("refine", C.c_int), ("tma_stages", C.c_int), ("post_smooth_split", C.c_int),
-                ("unscaled", C.c_int), ("tma_wait_cycles", C.c_longlong)]
+                ("unscaled", C.c_int), ("tma_wait_cycles", C.c_longlong), ("smoother_bf16", C.c_int)]
 
 
 class bura_stats(C.Structure):

@@ -33,9 +33,12 @@ struct Lev {
     long long plane;    // nx*ny
     double wx, wy, wz;  // constant-coefficient weights 1/(h^2 Lambda) per axis (wz = 0 in 2D)
     float wxf, wyf, wzf;  // the same rounded to FP32 (read by the FP32 kernels: no FP64 conversions)
-    const void* fx;     // variable coefficients: face weights a/(h^2 Lambda), element type T
+    const void* fx;     // variable coefficients: face weights a/(h^2 Lambda), element type T (bf16 with cbf16)
     const void* fy;
     const void* fz;
+    const void* dg;     // variable coefficients: the diagonal sum of a point's face weights, element type T
+                        // (computed from the stored faces, so the operator stays consistent); null: summed
+    int cbf16;          // 1: fx, fy, fz hold bfloat16 (FP32 kernels of the V-cycle levels only)
 };
 
 // Per-system CG state shared by the kernels (device memory).
@@ -184,6 +187,10 @@ struct Ops {
                              const T* b, T* bc, const T* dsh, cudaStream_t s);
     static void prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x,
                             cudaStream_t s);
+    // r = b - (A - dI) x, then bc = R r (full weighting): the residual restriction in two sweeps
+    static void residual(const Launch& g, const Lev& L, int dim, bool var, const T* x, const T* b, T* r, const T* dsh,
+                         cudaStream_t s);
+    static void restrict_r(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, const T* r, T* bc, cudaStream_t s);
     static void coarse_cycle(const Launch& g1, int dim, bool var, const CoarseArgs& a, cudaStream_t s);
     static cudaError_t coarse_cluster(const Launch& g1, int csize, int dim, bool var, const ClusterArgs& a,
                                       cudaStream_t s);

@@ -88,22 +88,29 @@ __device__ __forceinline__ Coord coord(const Lev& L, int P) {
 template <class T>
 struct Wts { T xm, xp, ym, yp, zm, zp; };
 
+// A face weight of a variable-coefficient level: element i of the array, stored as T or, for the FP32
+// kernels of a level with cbf16, as bfloat16 (the upper 16 bits of an FP32 value).
+template <class T>
+__device__ __forceinline__ T coef(const Lev& L, const void* a, size_t i) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.cbf16) return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short*>(a) + i) << 16);
+    }
+    return __ldg(reinterpret_cast<const T*>(a) + i);
+}
+
 template <class T, int DIM, bool VAR>
 __device__ __forceinline__ Wts<T> weights(const Lev& L, int P, const Coord& c) {
     Wts<T> w;
     if (VAR) {
-        const T* fx = reinterpret_cast<const T*>(L.fx);
-        const T* fy = reinterpret_cast<const T*>(L.fy);
         const size_t row = (size_t)c.l * L.ny + c.j;  // (l, j) row of x-faces: nx+1 each
-        w.xm = __ldg(fx + row * (L.nx + 1) + c.i);
-        w.xp = __ldg(fx + row * (L.nx + 1) + c.i + 1);
+        w.xm = coef<T>(L, L.fx, row * (L.nx + 1) + c.i);
+        w.xp = coef<T>(L, L.fx, row * (L.nx + 1) + c.i + 1);
         const size_t ybase = ((size_t)c.l * (L.ny + 1) + c.j) * L.nx + c.i;
-        w.ym = __ldg(fy + ybase);
-        w.yp = __ldg(fy + ybase + L.nx);
+        w.ym = coef<T>(L, L.fy, ybase);
+        w.yp = coef<T>(L, L.fy, ybase + L.nx);
         if (DIM == 3) {
-            const T* fz = reinterpret_cast<const T*>(L.fz);
-            w.zm = __ldg(fz + P);
-            w.zp = __ldg(fz + P + L.plane);
+            w.zm = coef<T>(L, L.fz, P);
+            w.zp = coef<T>(L, L.fz, P + L.plane);
         } else {
             w.zm = w.zp = T(0);
         }
@@ -117,6 +124,7 @@ __device__ __forceinline__ Wts<T> weights(const Lev& L, int P, const Coord& c) {
 
 template <class T, int DIM, bool VAR>
 __device__ __forceinline__ T diag_at(const Lev& L, int P) {
+    if (VAR && L.dg) return __ldg(reinterpret_cast<const T*>(L.dg) + P);
     const Coord c = coord<DIM>(L, P);
     const Wts<T> w = weights<T, DIM, VAR>(L, P, c);
     T dg = w.xm + w.xp + w.ym + w.yp;
@@ -231,8 +239,12 @@ __device__ __forceinline__ void stencil(const Lev& L, int Kp, int P, int off, co
     constexpr int W = VecT<T>::W;
     const Coord c = coord<DIM>(L, P);
     const Wts<T> w = weights<T, DIM, VAR>(L, P, c);
-    diag = w.xm + w.xp + w.ym + w.yp;
-    if (DIM == 3) diag += w.zm + w.zp;
+    if (VAR && L.dg) {
+        diag = __ldg(reinterpret_cast<const T*>(L.dg) + P);
+    } else {
+        diag = w.xm + w.xp + w.ym + w.yp;
+        if (DIM == 3) diag += w.zm + w.zp;
+    }
     const size_t base = (size_t)P * Kp + off;
     ld(P, base, xc);
     T acc[W];
@@ -556,6 +568,57 @@ __device__ __forceinline__ void sw_restrict(const Lev& Lf, const Lev& Lc, int Kp
         [&](int P, St& st) { vst(bc + (size_t)P * Kp + off, st.sum); });
 }
 
+// r = b - (A - dI) x on one level (the residual that sw_restrict_r restricts).
+template <class T, int DIM, bool VAR>
+__device__ __forceinline__ void sw_residual(const Lev& L, int Kp, const T* x, const T* b, T* r, const T* dsh,
+                                            int b0, int nb) {
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    T d[W];
+    for (int v = 0; v < W; ++v) d[v] = (T)dsh[off + v];
+    LoadPlain<T> ld{x};
+    sweep_u<StencilState<T>>(
+        L.N, b0, nb,
+        [&](int P, StencilState<T>& st) {
+            stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag);
+            vld(b + (size_t)P * Kp + off, st.bv);
+        },
+        [&](int P, StencilState<T>& st) {
+            T rv[W];
+            for (int v = 0; v < W; ++v) rv[v] = st.bv[v] - fma(-d[v], st.xc[v], st.Ax[v]);
+            vst(r + (size_t)P * Kp + off, rv);
+        });
+}
+
+// bc = R r: full weighting of a stored fine-level residual (weights 1/4, 1/2, 1/4 per axis).
+template <class T, int DIM>
+__device__ __forceinline__ void sw_restrict_r(const Lev& Lf, const Lev& Lc, int Kp, const T* r, T* bc, int b0, int nb) {
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    const T w1[3] = {T(0.25), T(0.5), T(0.25)};
+    struct St { T sum[VecT<T>::W]; };
+    sweep_u<St>(
+        Lc.N, b0, nb,
+        [&](int P, St& st) {
+            const Coord cc = coord<DIM>(Lc, P);
+            const int fi = 2 * cc.i + 1, fj = 2 * cc.j + 1, fl = (DIM == 3) ? 2 * cc.l + 1 : 0;
+            for (int v = 0; v < W; ++v) st.sum[v] = T(0);
+            const int zlo = (DIM == 3) ? -1 : 0, zhi = (DIM == 3) ? 1 : 0;
+            for (int dz = zlo; dz <= zhi; ++dz)
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const size_t row = ((size_t)(fl + dz) * Lf.ny + (fj + dy)) * Lf.nx;
+                    const T wyz = w1[dy + 1] * (DIM == 3 ? w1[dz + 1] : T(1));
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        T rv[W];
+                        vld(r + (row + fi + dx) * Kp + off, rv);
+                        const T wt = w1[dx + 1] * wyz;
+                        for (int v = 0; v < W; ++v) st.sum[v] = fma(wt, rv[v], st.sum[v]);
+                    }
+                }
+        },
+        [&](int P, St& st) { vst(bc + (size_t)P * Kp + off, st.sum); });
+}
+
 // x += P ec (prolongation of the coarse correction; pointwise on the fine level).
 template <class T, int DIM>
 __device__ __forceinline__ void sw_prolong_add(const Lev& Lf, const Lev& Lc, int Kp, const T* ec, T* x, int b0,
@@ -726,6 +789,21 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_restrict_res
                                T* __restrict__ bc, const T* __restrict__ dsh) {
     pdl_wait();
     sw_restrict<T, DIM, VAR>(Lf, Lc, Kp, x, b, bc, dsh, blockIdx.x, gridDim.x);
+}
+
+template <class T, int DIM, bool VAR>
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_residual(Lev L, int Kp, const T* __restrict__ x,
+                                                                         const T* __restrict__ b, T* __restrict__ r,
+                                                                         const T* __restrict__ dsh) {
+    pdl_wait();
+    sw_residual<T, DIM, VAR>(L, Kp, x, b, r, dsh, blockIdx.x, gridDim.x);
+}
+
+template <class T, int DIM>
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_restrict_r(Lev Lf, Lev Lc, int Kp,
+                                                                           const T* __restrict__ r, T* __restrict__ bc) {
+    pdl_wait();
+    sw_restrict_r<T, DIM>(Lf, Lc, Kp, r, bc, blockIdx.x, gridDim.x);
 }
 
 template <class T, int DIM, bool VAR>
@@ -1061,6 +1139,18 @@ template <class T>
 void Ops<T>::restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, bool var, const T* x, const T* b,
                           T* bc, const T* dsh, cudaStream_t s) {
     BURA_DISPATCH_PDL(dim, var, k_restrict_res, dim3(gc.blocks), blk(gc), 0, s, Lf, Lc, gc.Kp, x, b, bc, dsh);
+}
+
+template <class T>
+void Ops<T>::residual(const Launch& g, const Lev& L, int dim, bool var, const T* x, const T* b, T* r, const T* dsh,
+                      cudaStream_t s) {
+    BURA_DISPATCH_PDL(dim, var, k_residual, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, b, r, dsh);
+}
+
+template <class T>
+void Ops<T>::restrict_r(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim, const T* r, T* bc, cudaStream_t s) {
+    if (dim == 2) launch_pdl(k_restrict_r<T, 2>, dim3(gc.blocks), blk(gc), 0, s, Lf, Lc, gc.Kp, r, bc);
+    else launch_pdl(k_restrict_r<T, 3>, dim3(gc.blocks), blk(gc), 0, s, Lf, Lc, gc.Kp, r, bc);
 }
 
 template <class T>

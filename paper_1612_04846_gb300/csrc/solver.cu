@@ -35,7 +35,7 @@ struct HostLevel {
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
            K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_REDFIN,
-           K_POST2, K_NK };
+           K_POST2, K_RESID, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -60,7 +60,8 @@ const char* const kNames[K_NK][2][2] = {
     {{"update_residual_df", "update_residual_df"}, {"update_residual_df", "update_residual_df"}},
     {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}},
     {{"red_finish_f64", "red_finish_f64"}, {"red_finish_f32", "red_finish_f32"}},
-    {{"post2_f64", "post2_f64@coarse"}, {"post2_f32", "post2_f32@coarse"}}};
+    {{"post2_f64", "post2_f64@coarse"}, {"post2_f32", "post2_f32@coarse"}},
+    {{"residual_f64", "residual_f64@coarse"}, {"residual_f32", "residual_f32@coarse"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -80,6 +81,7 @@ struct Work {
     int Kp = 0, W = 0, C = 0;
     std::vector<Launch> g;
     std::vector<Lev> L;
+    Lev Lop{};                    // level 0 as the CG operator (FP32/FP64 faces even when L[0]'s are bf16)
     T *x = nullptr, *r = nullptr, *pa = nullptr, *pb = nullptr, *q = nullptr;
     std::vector<T*> b, xa, xb, dd;
     std::vector<T*> c1, c2;       // [level] -> deg rows of Kp coefficients, in the kernels' precision
@@ -117,6 +119,20 @@ struct Work {
 };
 
 int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
+
+// FP32 -> bfloat16 bits, rounded to nearest even (finite values).
+unsigned short to_bf16(float f) {
+    unsigned u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (unsigned short)(u >> 16);
+}
+float from_bf16(unsigned short h) {
+    const unsigned u = (unsigned)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
 
 
 }  // namespace
@@ -525,6 +541,15 @@ int build_tma(bura_plan* p, Work<T>& w) {
     return BURA_OK;
 }
 
+// Chebyshev interval [lmax / ratio, lmax] of the smoother: the option, or (0 = auto) the upper quarter of
+// the spectrum in 2-D and the upper eighth in 3-D, where full coarsening leaves a wider high-frequency
+// band (the eigenvalues of D^-1 A over the modes that are oscillatory in at least one direction reach
+// down to 1/dim of their maximum for the 7-point operator).
+double smoother_ratio(const bura_plan* p) {
+    if (p->opt.smoother_ratio > 0) return p->opt.smoother_ratio;
+    return p->dim == 3 ? 8.0 : 4.0;
+}
+
 // The shift-dependent tables of a work set, written into its existing buffers: per level the Chebyshev
 // coefficients c1, c2 (deg x Kp), the shifts, and the dense inverses of the exact level.  Their sizes
 // do not depend on the shifts (the coarsest degree depends on d_0 = 0 only), so a plan can be moved
@@ -539,7 +564,7 @@ int upload_tables(bura_plan* p, Work<T>& w) {
         const bool coarsest = (l == nlev - 1);
         const int deg = w.deg[l];
         std::vector<std::vector<double>> C1, C2;
-        cheb_tables(h, p->var, p->d, p->K, w.Kp, deg, p->opt.smoother_ratio, coarsest, C1, C2);
+        cheb_tables(h, p->var, p->d, p->K, w.Kp, deg, smoother_ratio(p), coarsest, C1, C2);
         if (coarsest && h.N == 1) {  // exact solve of the 1x1 system: x = b / (diag - d)
             for (int s = 0; s < p->K; ++s) C2[0][s] = p->var ? 1.0 : 1.0 / (h.amax - p->d[s]);
         }
@@ -561,6 +586,55 @@ int upload_tables(bura_plan* p, Work<T>& w) {
         const std::vector<T> tv(inv.begin(), inv.end());
         CK(cudaMemcpy(w.minv, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice));
     }
+    return BURA_OK;
+}
+
+// Face weights a / (h^2 Lambda) of a variable-coefficient level and its diagonal (the sum of a point's
+// six stored weights, in FP64, rounded to T), as T or as bf16.
+template <class T>
+int upload_faces(bura_plan* p, const HostLevel& h, Lev& L, bool bf16) {
+    const int nx = h.n[0], ny = h.n[1], nz = h.n[2];
+    std::vector<double> stored[3];
+    for (int a = 0; a < p->dim; ++a) {
+        const size_t n = h.a[a].size();
+        stored[a].resize(n);
+        void* dptr = nullptr;
+        if (bf16) {
+            std::vector<unsigned short> v(n);
+            for (size_t i = 0; i < n; ++i) {
+                v[i] = to_bf16((float)(h.a[a][i] * h.w[a]));
+                stored[a][i] = from_bf16(v[i]);
+            }
+            CA(dalloc(p, &dptr, n * sizeof(unsigned short)));
+            CK(cudaMemcpy(dptr, v.data(), n * sizeof(unsigned short), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<T> v(n);
+            for (size_t i = 0; i < n; ++i) {
+                v[i] = (T)(h.a[a][i] * h.w[a]);
+                stored[a][i] = (double)v[i];
+            }
+            CA(dalloc(p, &dptr, n * sizeof(T)));
+            CK(cudaMemcpy(dptr, v.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+        }
+        if (a == 0) L.fx = dptr;
+        else if (a == 1) L.fy = dptr;
+        else L.fz = dptr;
+    }
+    std::vector<T> dg((size_t)h.N);
+    for (int l = 0; l < nz; ++l)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double s = stored[0][((size_t)l * ny + j) * (nx + 1) + i] + stored[0][((size_t)l * ny + j) * (nx + 1) + i + 1];
+                s += stored[1][((size_t)l * (ny + 1) + j) * nx + i] + stored[1][((size_t)l * (ny + 1) + j + 1) * nx + i];
+                if (p->dim == 3)
+                    s += stored[2][((size_t)l * ny + j) * nx + i] + stored[2][((size_t)(l + 1) * ny + j) * nx + i];
+                dg[((size_t)l * ny + j) * nx + i] = (T)s;
+            }
+    T* dptr = nullptr;
+    CA(dalloc(p, &dptr, dg.size() * sizeof(T)));
+    CK(cudaMemcpy(dptr, dg.data(), dg.size() * sizeof(T), cudaMemcpyHostToDevice));
+    L.dg = dptr;
+    L.cbf16 = bf16 ? 1 : 0;
     return BURA_OK;
 }
 
@@ -596,19 +670,17 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
         L.wxf = (float)L.wx;
         L.wyf = (float)L.wy;
         L.wzf = (float)L.wz;
-        L.fx = L.fy = L.fz = nullptr;
+        L.fx = L.fy = L.fz = L.dg = nullptr;
+        L.cbf16 = 0;
         if (p->var) {
-            for (int a = 0; a < p->dim; ++a) {
-                std::vector<T> sc(h.a[a].size());
-                for (size_t i = 0; i < sc.size(); ++i) sc[i] = (T)(h.a[a][i] * h.w[a]);
-                T* dptr = nullptr;
-                CA(dalloc(p, &dptr, sc.size() * sizeof(T)));
-                CK(cudaMemcpy(dptr, sc.data(), sc.size() * sizeof(T), cudaMemcpyHostToDevice));
-                if (a == 0) L.fx = dptr;
-                else if (a == 1) L.fy = dptr;
-                else L.fz = dptr;
-            }
+            // the CG operator's faces in T; the V-cycle's in bf16 when asked (FP32 path), with the diagonal
+            // summed from the stored values so each level operator is the M-matrix of its stored faces
+            const bool bf = sizeof(T) == 4 && p->opt.smoother_bf16;
+            if (!bf || l == 0) CA(upload_faces<T>(p, h, L, false));
+            if (l == 0) w.Lop = L;
+            if (bf) CA(upload_faces<T>(p, h, L, true));
         }
+        if (l == 0 && !p->var) w.Lop = L;
         if (!full) break;
         const size_t vb = (size_t)h.N * w.Kp * sizeof(T);
         CA(dalloc(p, &w.b[l], vb));  // level 0 uses the CG residual instead; kept for the coarse CTA
@@ -931,10 +1003,19 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
         }
         return cur;
     }
-    // coarse-grid correction: residual + restriction, then the coarser levels
-    traced(p, K_RESTRICT, f32, fine, vbytes<T>(p, l, 2.0, true) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
-        Ops<T>::restrict_res(w.g[l + 1], L, w.L[l + 1], dim, var, cur, b, w.b[l + 1], w.dsh, s);
-    });
+    // coarse-grid correction: residual + restriction, then the coarser levels.  In 3-D and with variable
+    // coefficients the residual is stored (in D, free between pre- and post-smoothing) and restricted by a
+    // second sweep: 27 (3-D) stencil evaluations per coarse point cost more than the extra vector pass.
+    if (dim == 3 || var) {
+        traced(p, K_RESID, f32, fine, vbytes<T>(p, l, 3.0, true), s,
+               [&] { Ops<T>::residual(g, L, dim, var, cur, b, D, w.dsh, s); });
+        traced(p, K_RESTRICT, f32, fine, vbytes<T>(p, l, 1.0, false) + vbytes<T>(p, l + 1, 1.0, false), s,
+               [&] { Ops<T>::restrict_r(w.g[l + 1], L, w.L[l + 1], dim, D, w.b[l + 1], s); });
+    } else {
+        traced(p, K_RESTRICT, f32, fine, vbytes<T>(p, l, 2.0, true) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
+            Ops<T>::restrict_res(w.g[l + 1], L, w.L[l + 1], dim, var, cur, b, w.b[l + 1], w.dsh, s);
+        });
+    }
     T* ec = vcycle<T>(p, w, l + 1, w.b[l + 1], false, s);
     traced(p, K_PROLONG, f32, fine, vbytes<T>(p, l, 2.0, false) + vbytes<T>(p, l + 1, 1.0, false), s,
            [&] { Ops<T>::prolong_add(g, L, w.L[l + 1], dim, ec, cur, s); });
@@ -957,7 +1038,7 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
 template <class T>
 int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) {
     const Launch& g = w.g[0];
-    const Lev& L = w.L[0];
+    const Lev& L = w.Lop;  // the CG operator (its faces never bf16)
     const bool f32 = sizeof(T) == 4;
     const Red ralpha = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_ALPHA, 0});
     const Red rconv = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_CONV, cond});
@@ -1444,13 +1525,14 @@ void bura_default_options(bura_options* opt) {
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = BURA_PREC_MIXED;
     opt->smoother_degree = 2;
-    opt->smoother_ratio = 4.0;
+    opt->smoother_ratio = 0.0;
     opt->max_iters = 200;
     opt->max_outer = 12;
     opt->inner_rtol = 1e-5;
     opt->coarse_degree = 0;
     opt->unscaled = 0;
     opt->tma_wait_cycles = 0;
+    opt->smoother_bf16 = 0;
 }
 
 
@@ -1476,7 +1558,7 @@ int check_grid(const bura_grid* grid, const double* const* faces, long long* N) 
 
 int check_options(const bura_options& o) {
     if (o.precision != BURA_PREC_FP64 && o.precision != BURA_PREC_MIXED) return BURA_EINVAL;
-    if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio > 1) || o.max_iters < 1 ||
+    if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio == 0 || o.smoother_ratio > 1) || o.max_iters < 1 ||
         o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000 ||
         o.block_points < 0 || o.block_points > 1024 || o.blocks_per_sm < 0 || o.blocks_per_sm > 64 ||
         o.coarse_kernel < BURA_COARSE_AUTO || o.coarse_kernel > BURA_COARSE_NONE ||
@@ -1484,7 +1566,8 @@ int check_options(const bura_options& o) {
           o.cluster_size == 16) ||
         o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
         o.refine > BURA_REFINE_DF || o.tma_stages < 0 || o.tma_stages > 4 || o.post_smooth_split < 0 ||
-        o.post_smooth_split > 1 || o.unscaled < 0 || o.unscaled > 1 || o.tma_wait_cycles < 0)
+        o.post_smooth_split > 1 || o.unscaled < 0 || o.unscaled > 1 || o.tma_wait_cycles < 0 ||
+        o.smoother_bf16 < 0 || o.smoother_bf16 > 1)
         return BURA_EINVAL;
     return BURA_OK;
 }
