@@ -205,6 +205,39 @@ int bura_setup_shifts(const bura_grid* grid, const double* const* faces, int nsy
                       const bura_options* opt, bura_plan** out);
 
 /*
+ * An assembled SPD matrix Atilde in compressed sparse rows (host arrays, 0-based), for instance the
+ * stiffness matrix of conforming P1 finite elements that the paper's 3-D tests use (Sec. 5.4): row i holds
+ * its entries val[row_ptr[i] .. row_ptr[i+1]-1] in columns col[...], the diagonal included, in any order.
+ */
+typedef struct {
+    int n;                /* rows = columns */
+    long long nnz;        /* entries, row_ptr[n] */
+    const int* row_ptr;   /* n + 1 offsets */
+    const int* col;       /* nnz column indices */
+    const double* val;    /* nnz values */
+    double lambda_min;    /* a lower bound (> 0) on the smallest eigenvalue of Atilde, or 0 if none is known */
+} bura_csr;
+
+/*
+ * A plan for the BURA solve of A^alpha u = f with the sparse matrix A = Atilde / Lambda, Lambda the largest
+ * absolute row sum of Atilde (eq. (algebraic), Sec. 1.4), u = sum_j c_j (A - d_j I)^{-1} f (eq. (Rgeneral)).
+ * The k+1 shifted systems run as one multi-shift CG on the GPU: the sparse product reads each entry's value
+ * and column once for all systems (vectors interleaved by system, as on grids), and the preconditioner is a
+ * Chebyshev polynomial in Dinv (A - d_j I) per system (degree opt->coarse_degree, 0 = 8, on the interval
+ * [lambda_lo_j, Gershgorin bound of the scaled rows]; lambda_lo_j from lambda_min, else the upper bound /
+ * opt->smoother_ratio, 0 = 30): geometric multigrid needs a grid.
+ * Stopping rule: with lambda_min > 0 that of bura_solve; with lambda_min = 0 every system stops at
+ * ||f - (A - d_j I) v_j|| <= tol ||f|| (the relative residual criterion of the paper's PCG runs) and
+ * bura_stats.err_bound is -1.  The arrays are copied (the caller keeps ownership); bura_solve* and
+ * bura_apply_shifted then take vectors of n entries.  Not with opt->refine = BURA_REFINE_DF.
+ * Errors: BURA_EINVAL (null pointers, n < 1, offsets not from 0 to nnz or decreasing, a column out of range,
+ *         a non-finite value, a row without a positive diagonal, an unsymmetric matrix, lambda_min < 0,
+ *         alpha, k or options out of range), BURA_ERANGE (n * 16 or nnz >= 2^31), BURA_EREMEZ, BURA_ENOMEM,
+ *         BURA_ECUDA.
+ */
+int bura_setup_csr(const bura_csr* A, double alpha, int k, const bura_options* opt, bura_plan** out);
+
+/*
  * The scale Lambda of eq. (algebraic) (Sec. 1.4) for a grid and its coefficients, host only: the Gershgorin
  * bound max_P sum_Q |Atilde_PQ| of the unscaled matrix, which every plan of the grid uses (A = Atilde / Lambda).
  * grid and faces as for bura_setup.  Errors: BURA_EINVAL (bad grid or faces, null Lambda), BURA_ERANGE.

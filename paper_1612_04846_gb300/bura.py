@@ -39,6 +39,11 @@ class bura_options(C.Structure):
                 ("unscaled", C.c_int), ("tma_wait_cycles", C.c_longlong), ("smoother_bf16", C.c_int)]
 
 
+class bura_csr(C.Structure):
+    _fields_ = [("n", C.c_int), ("nnz", C.c_longlong), ("row_ptr", C.POINTER(C.c_int)), ("col", C.POINTER(C.c_int)),
+                ("val", C.POINTER(C.c_double)), ("lambda_min", C.c_double)]
+
+
 class bura_stats(C.Structure):
     _fields_ = [("Lambda", C.c_double), ("E", C.c_double), ("k", C.c_int), ("levels", C.c_int),
                 ("iters", C.c_int), ("outer", C.c_int), ("shift_iters", C.c_int * (BURA_MAX_K + 1)),
@@ -129,6 +134,7 @@ def _lib():
                                         C.POINTER(P)]
         L.bura_solve_sum.argtypes = [C.POINTER(P), I, P, P, D, P]
         L.bura_scale.argtypes = [C.POINTER(bura_grid), C.POINTER(dp), dp]
+        L.bura_setup_csr.argtypes = [C.POINTER(bura_csr), D, I, C.POINTER(bura_options), C.POINTER(P)]
         L.bura_quadrature_bp15.argtypes = [D, D, D, I, dp, dp, C.POINTER(I)]
         L.bura_set_tma_wait_cycles.argtypes = [P, C.c_longlong]
         L.bura_server_default_options.argtypes = [C.POINTER(bura_server_options)]
@@ -146,7 +152,7 @@ def _lib():
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
                      "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
                      "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts", "bura_solve_sum",
-                     "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_server_create", "bura_server_submit",
+                     "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr", "bura_server_create", "bura_server_submit",
                      "bura_server_wait", "bura_server_get_stats", "bura_server_destroy"):
             getattr(L, name).restype = I
         _LIB = L
@@ -239,6 +245,26 @@ def bura_setup_shifts(shape, c, d, faces=None, options=None):
     plan = C.c_void_p()
     _check(_lib().bura_setup_shifts(C.byref(g), fptr, int(c.size), _hptr(c), _hptr(d), C.byref(opt), C.byref(plan)),
            "bura_setup_shifts")
+    return plan
+
+
+def bura_setup_csr(indptr, indices, data, alpha, k, lambda_min=0.0, options=None):
+    """Plan for the sparse SPD matrix Atilde given by its CSR arrays (row offsets, columns, values; e.g. a
+    scipy.sparse.csr_matrix's indptr, indices, data).  lambda_min: a lower bound on its smallest
+    eigenvalue, or 0."""
+    rp = np.ascontiguousarray(indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(indices, dtype=np.int32)
+    va = np.ascontiguousarray(data, dtype=np.float64)
+    A = bura_csr()
+    A.n = int(rp.size - 1)
+    A.nnz = int(ci.size)
+    A.row_ptr = rp.ctypes.data_as(C.POINTER(C.c_int))
+    A.col = ci.ctypes.data_as(C.POINTER(C.c_int))
+    A.val = _hptr(va)
+    A.lambda_min = float(lambda_min)
+    opt = options if options is not None else bura_default_options()
+    plan = C.c_void_p()
+    _check(_lib().bura_setup_csr(C.byref(A), float(alpha), int(k), C.byref(opt), C.byref(plan)), "bura_setup_csr")
     return plan
 
 
@@ -478,6 +504,6 @@ EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
             "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
             "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts",
-            "bura_solve_sum", "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_server_default_options",
+            "bura_solve_sum", "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr", "bura_server_default_options",
             "bura_server_create", "bura_server_submit", "bura_server_wait", "bura_server_get_stats",
             "bura_server_destroy"]

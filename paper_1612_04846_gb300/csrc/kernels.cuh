@@ -39,6 +39,11 @@ struct Lev {
     const void* dg;     // variable coefficients: the diagonal sum of a point's face weights, element type T
                         // (computed from the stored faces, so the operator stays consistent); null: summed
     int cbf16;          // 1: fx, fy, fz hold bfloat16 (FP32 kernels of the V-cycle levels only)
+    // sparse operator (kernels instantiated with DIM = 0): row offsets, column indices and values of the
+    // scaled matrix A, all entries of a row including its diagonal (which dg also holds), element type T
+    const int* rowptr;
+    const int* col;
+    const void* val;
 };
 
 // Per-system CG state shared by the kernels (device memory).

@@ -79,7 +79,8 @@ void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const d
     const size_t sh = (size_t)g.C * g.PPB * 2 * sizeof(double);
     // the shifts live in the device Scal record (address arithmetic only, no host dereference)
     const double* dsh = reinterpret_cast<const double*>(reinterpret_cast<const char*>(red.scal) + offsetof(Scal, dsh));
-    if (dim == 2 && !var) k_residual64<2, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    if (dim == 0) k_residual64<0, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    else if (dim == 2 && !var) k_residual64<2, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
     else if (dim == 2) k_residual64<2, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
     else if (!var) k_residual64<3, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
     else k_residual64<3, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);

@@ -124,7 +124,7 @@ __device__ __forceinline__ Wts<T> weights(const Lev& L, int P, const Coord& c) {
 
 template <class T, int DIM, bool VAR>
 __device__ __forceinline__ T diag_at(const Lev& L, int P) {
-    if (VAR && L.dg) return __ldg(reinterpret_cast<const T*>(L.dg) + P);
+    if (DIM == 0 || (VAR && L.dg)) return __ldg(reinterpret_cast<const T*>(L.dg) + P);
     const Coord c = coord<DIM>(L, P);
     const Wts<T> w = weights<T, DIM, VAR>(L, P, c);
     T dg = w.xm + w.xp + w.ym + w.yp;
@@ -233,10 +233,29 @@ struct LoadProlong {
 };
 
 // A x at point P (no shift term) for the W systems of chunk `off`; xc = x(P), diag = A_PP.
+// DIM = 0: a sparse row of the operator (CSR): every entry's value and column are loaded once for the
+// W systems of the chunk, and the values of x at the columns come from the loader.
 template <class T, int DIM, bool VAR, class LD>
 __device__ __forceinline__ void stencil(const Lev& L, int Kp, int P, int off, const LD& ld,
                                         T (&xc)[VecT<T>::W], T (&Ax)[VecT<T>::W], T& diag) {
     constexpr int W = VecT<T>::W;
+    if constexpr (DIM == 0) {
+        diag = __ldg(reinterpret_cast<const T*>(L.dg) + P);
+        ld(P, (size_t)P * Kp + off, xc);
+        T acc[W];
+        for (int v = 0; v < W; ++v) acc[v] = T(0);
+        const int e = __ldg(L.rowptr + P + 1);
+        const T* __restrict__ val = reinterpret_cast<const T*>(L.val);
+        for (int q = __ldg(L.rowptr + P); q < e; ++q) {
+            const int cq = __ldg(L.col + q);
+            const T a = __ldg(val + q);
+            T n[W];
+            ld(cq, (size_t)cq * Kp + off, n);
+            for (int v = 0; v < W; ++v) acc[v] = fma(a, n[v], acc[v]);
+        }
+        for (int v = 0; v < W; ++v) Ax[v] = acc[v];
+        return;
+    } else {
     const Coord c = coord<DIM>(L, P);
     const Wts<T> w = weights<T, DIM, VAR>(L, P, c);
     if (VAR && L.dg) {
@@ -262,6 +281,7 @@ __device__ __forceinline__ void stencil(const Lev& L, int Kp, int P, int off, co
         if (c.l < L.nz - 1) { ld(P + pz, base + sz, n); for (int v = 0; v < W; ++v) acc[v] = fma(-w.zp, n[v], acc[v]); }
     }
     for (int v = 0; v < W; ++v) Ax[v] = acc[v];
+    }
 }
 
 // ------------------------------------------------------------------ reductions
@@ -1081,6 +1101,13 @@ inline size_t shm(const Launch& g, int W) { return (size_t)g.C * g.PPB * W * siz
         else KERNEL<T, 3, true>__VA_ARGS__;                                          \
     } while (0)
 
+// dim 0: the sparse (CSR) operator, for the kernels a one-level operator uses (no grid transfers)
+#define BURA_DISPATCH_PDL0(dim, var, KERNEL, GRID, BLOCK, SMEM, S, ...)                                \
+    do {                                                                                             \
+        if (dim == 0) launch_pdl(KERNEL<T, 0, true>, GRID, BLOCK, SMEM, S, __VA_ARGS__);             \
+        else BURA_DISPATCH_PDL(dim, var, KERNEL, GRID, BLOCK, SMEM, S, __VA_ARGS__);                  \
+    } while (0)
+
 #define BURA_DISPATCH_PDL(dim, var, KERNEL, GRID, BLOCK, SMEM, S, ...)                                 \
     do {                                                                                             \
         if (dim == 2 && !var) launch_pdl(KERNEL<T, 2, false>, GRID, BLOCK, SMEM, S, __VA_ARGS__);    \
@@ -1097,7 +1124,7 @@ void Ops<T>::broadcast(const Launch& g, const double* f, long long N, int K, T* 
 template <class T>
 void Ops<T>::spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, T* pa, T* pb, T* q,
                     const Red& red, cudaStream_t s) {
-    BURA_DISPATCH_PDL(dim, var, k_spmv_p, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, L, g.Kp, z, pa, pb, q, red);
+    BURA_DISPATCH_PDL0(dim, var, k_spmv_p, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, L, g.Kp, z, pa, pb, q, red);
 }
 
 template <class T>
@@ -1109,21 +1136,21 @@ void Ops<T>::cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, co
 template <class T>
 void Ops<T>::cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStepT<T> cs,
                        const T* dsh, cudaStream_t s) {
-    BURA_DISPATCH_PDL(dim, var, k_cheb_zero, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, x, cs, dsh);
+    BURA_DISPATCH_PDL0(dim, var, k_cheb_zero, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, x, cs, dsh);
 }
 
 template <class T>
 void Ops<T>::cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,
                        T* xout, T* dout, ChebStepT<T> cs, const T* dsh, const Red& red, cudaStream_t s) {
     const size_t sh = red.op != RED_NONE ? shm(g, VecT<T>::W) : 0;
-    BURA_DISPATCH_PDL(dim, var, k_cheb_step, dim3(g.blocks), blk(g), sh, s, L, g.Kp, xin, din, b, xout, dout, cs, dsh,
+    BURA_DISPATCH_PDL0(dim, var, k_cheb_step, dim3(g.blocks), blk(g), sh, s, L, g.Kp, xin, din, b, xout, dout, cs, dsh,
                       red);
 }
 
 template <class T>
 void Ops<T>::cheb_pre2(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* xout, T* dout, ChebStepT<T> cs0,
                        ChebStepT<T> cs1, const T* dsh, cudaStream_t s) {
-    BURA_DISPATCH_PDL(dim, var, k_cheb_pre2, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, xout, dout, cs0, cs1, dsh);
+    BURA_DISPATCH_PDL0(dim, var, k_cheb_pre2, dim3(g.blocks), blk(g), 0, s, L, g.Kp, b, xout, dout, cs0, cs1, dsh);
 }
 
 template <class T>
@@ -1144,7 +1171,7 @@ void Ops<T>::restrict_res(const Launch& gc, const Lev& Lf, const Lev& Lc, int di
 template <class T>
 void Ops<T>::residual(const Launch& g, const Lev& L, int dim, bool var, const T* x, const T* b, T* r, const T* dsh,
                       cudaStream_t s) {
-    BURA_DISPATCH_PDL(dim, var, k_residual, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, b, r, dsh);
+    BURA_DISPATCH_PDL0(dim, var, k_residual, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, b, r, dsh);
 }
 
 template <class T>
@@ -1250,7 +1277,7 @@ cudaError_t Ops<T>::cluster_prepare(int dim, bool var, int threads, int want, in
 template <class T>
 void Ops<T>::apply_shifted(const Launch& g, const Lev& L, int dim, bool var, const T* x, T* y, const T* dsh,
                            cudaStream_t s) {
-    BURA_DISPATCH_PDL(dim, var, k_apply_shifted, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, y, dsh);
+    BURA_DISPATCH_PDL0(dim, var, k_apply_shifted, dim3(g.blocks), blk(g), 0, s, L, g.Kp, x, y, dsh);
 }
 
 template <class T>

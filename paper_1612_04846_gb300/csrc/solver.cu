@@ -30,6 +30,10 @@ struct HostLevel {
     std::vector<double> a[3];  // unscaled face coefficients (variable coefficients only)
     double amax;         // max diagonal of the scaled level operator
     double lmin;         // lower bound on lambda_min of the scaled level operator
+    // sparse operator (plan dim 0): the scaled matrix's rows (all entries, diagonal included), its diagonal
+    // and absolute row sums; lmin = 0 when no lower bound on lambda_min is known
+    std::vector<int> rowptr, col;
+    std::vector<double> val, diag, rowsum;
 };
 
 // Kernel types for launch counting and per-kernel timing (fine level only).
@@ -120,6 +124,9 @@ struct Work {
 
 int ceil_to(int v, int m) { return (v + m - 1) / m * m; }
 
+// Degree of the Chebyshev polynomial preconditioner of a sparse operator (one level, no coarse grids).
+constexpr int kCsrDegree = 8;
+
 // FP32 -> bfloat16 bits, rounded to nearest even (finite values).
 unsigned short to_bf16(float f) {
     unsigned u;
@@ -148,6 +155,8 @@ struct bura_plan {
     double out_scale = 1.0;    // factor of the weights in the output sum (Lambda^-alpha with opt.unscaled)
     long long wait_cycles = 0; // budget of the TMA ring waits (0: the kernels' default)
     std::vector<double> c, d;
+    const int* csr_rowptr = nullptr;  // device copies of the sparse operator's row offsets and columns
+    const int* csr_col = nullptr;
     bura_options opt{};
     std::vector<HostLevel> hl;
     Work<double> w64;
@@ -388,9 +397,13 @@ void cheb_tables(const HostLevel& h, bool var, const std::vector<double>& d, int
     C2.assign(deg, std::vector<double>(Kp, 0.0));
     for (int s = 0; s < K; ++s) {
         const double mds = -d[s];  // >= 0
-        const double hi = 1.0 + h.amax / (h.amax + mds);
+        double hi = 1.0 + h.amax / (h.amax + mds);
+        if (!h.rowsum.empty()) {  // sparse operator: Gershgorin bound of Dinv (A - dI) row by row
+            hi = 0.0;
+            for (size_t i = 0; i < h.rowsum.size(); ++i) hi = std::max(hi, (h.rowsum[i] + mds) / (h.diag[i] + mds));
+        }
         double lo;
-        if (coarse_solve) lo = (h.lmin + mds) / (h.amax + mds);
+        if (coarse_solve && !(h.rowsum.size() && h.lmin <= 0)) lo = (h.lmin + mds) / (h.amax + mds);
         else lo = std::max(hi / ratio, mds / (h.amax + mds));
         lo = std::min(lo, hi * (1.0 - 1e-12));
         const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
@@ -547,6 +560,7 @@ int build_tma(bura_plan* p, Work<T>& w) {
 // down to 1/dim of their maximum for the 7-point operator).
 double smoother_ratio(const bura_plan* p) {
     if (p->opt.smoother_ratio > 0) return p->opt.smoother_ratio;
+    if (p->dim == 0) return 30.0;  // sparse operator without a lambda_min bound: the polynomial preconditioner
     return p->dim == 3 ? 8.0 : 4.0;
 }
 
@@ -672,7 +686,24 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
         L.wzf = (float)L.wz;
         L.fx = L.fy = L.fz = L.dg = nullptr;
         L.cbf16 = 0;
-        if (p->var) {
+        L.rowptr = L.col = nullptr;
+        L.val = nullptr;
+        if (p->dim == 0) {  // the sparse operator: values and diagonal in T, shared row offsets and columns
+            std::vector<T> v(h.val.size()), dg(h.diag.size());
+            for (size_t i = 0; i < v.size(); ++i) v[i] = (T)h.val[i];
+            for (size_t i = 0; i < dg.size(); ++i) dg[i] = (T)h.diag[i];
+            T* dv = nullptr;
+            T* dd = nullptr;
+            CA(dalloc(p, &dv, v.size() * sizeof(T)));
+            CA(dalloc(p, &dd, dg.size() * sizeof(T)));
+            CK(cudaMemcpy(dv, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(dd, dg.data(), dg.size() * sizeof(T), cudaMemcpyHostToDevice));
+            L.rowptr = p->csr_rowptr;
+            L.col = p->csr_col;
+            L.val = dv;
+            L.dg = dd;
+            w.Lop = L;
+        } else if (p->var) {
             // the CG operator's faces in T; the V-cycle's in bf16 when asked (FP32 path), with the diagonal
             // summed from the stored values so each level operator is the M-matrix of its stored faces
             const bool bf = sizeof(T) == 4 && p->opt.smoother_bf16;
@@ -689,7 +720,8 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
         CA(dalloc(p, &w.dd[l], vb));
         const bool coarsest = (l == nlev - 1);
         int deg = p->opt.smoother_degree;
-        if (coarsest) deg = h.N == 1 ? 1 : (p->opt.coarse_degree > 0 ? p->opt.coarse_degree : coarse_degree_auto(h, p->d[0]));
+        if (coarsest) deg = h.N == 1 ? 1 : (p->opt.coarse_degree > 0 ? p->opt.coarse_degree
+                                            : p->dim == 0 ? kCsrDegree : coarse_degree_auto(h, p->d[0]));
         w.deg[l] = deg;
         // the Chebyshev tables (deg x Kp each) depend on the shifts: filled by upload_tables
         CA(dalloc(p, &w.c1[l], (size_t)deg * w.Kp * sizeof(T)));
@@ -703,7 +735,7 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
     // the first level with at most kExactPoints points is solved exactly (dense inverses); the levels
     // below it are never visited
     w.le = -1;
-    for (int l = 0; l < nlev; ++l)
+    for (int l = 0; l < nlev && p->dim != 0; ++l)
         if (p->hl[l].N <= kExactPoints) { w.le = l; break; }
     const int last = w.le >= 0 ? w.le : nlev - 1;
     w.lc = -1;
@@ -712,6 +744,7 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
     // measured on GB300 (2-D 1023^2, k = 7): the single CTA over shared memory beats the cluster, whose
     // sweeps each pay an L2 round trip and a cluster barrier (about 3 us of fixed cost per sweep)
     if (w.coarse_kind == BURA_COARSE_AUTO) w.coarse_kind = BURA_COARSE_CTA;
+    if (p->dim == 0) w.coarse_kind = BURA_COARSE_NONE;  // one level: the polynomial preconditioner alone
     if (w.coarse_kind == BURA_COARSE_CLUSTER) {
         // the small levels (at most kClusterPoints points each, L2 resident) run in one thread-block cluster
         for (int l = 0; l <= last; ++l)
@@ -773,7 +806,8 @@ template <class T>
 double vbytes(const bura_plan* p, int l, double vec, bool stencil) {
     const double N = (double)p->hl[l].N;
     double b = vec * N * p->K * sizeof(T);
-    if (stencil && p->var) b += N * p->dim * sizeof(T);
+    if (stencil && p->dim == 0) b += (double)p->hl[0].val.size() * (4 + sizeof(T)) + N * (4 + sizeof(T));
+    else if (stencil && p->var) b += N * p->dim * sizeof(T);
     return b;
 }
 
@@ -1172,9 +1206,11 @@ int init_scal(bura_plan* p, Scal* dev, const double* thr, const int* active, cud
 }
 
 // Per-system absolute thresholds on ||r_j||^2 so that sum_j c_j ||r_j|| / (lambda_lo - d_j) <= tol ||f||.
+// A sparse operator without a lower bound on lambda_min stops each system at ||r_j|| <= tol ||f|| (the
+// relative residual criterion of the paper's PCG runs, Sec. 5.4).
 void thresholds(const bura_plan* p, double tol, double fnorm2, double* thr) {
     for (int j = 0; j < p->K; ++j) {
-        const double t = tol * (p->lambda_lo - p->d[j]) / (p->K * p->c[j]);
+        const double t = p->lambda_lo > 0 ? tol * (p->lambda_lo - p->d[j]) / (p->K * p->c[j]) : tol;
         thr[j] = t * t * fnorm2;
     }
 }
@@ -1187,7 +1223,7 @@ void finish_stats(bura_plan* p, const double* rr, double fnorm2) {
         p->st.rel_res[j] = fn > 0 ? rn / fn : 0.0;
         eb += p->c[j] * rn / (p->lambda_lo - p->d[j]);
     }
-    p->st.err_bound = fn > 0 ? eb / fn : 0.0;
+    p->st.err_bound = p->lambda_lo > 0 ? (fn > 0 ? eb / fn : 0.0) : -1.0;
 }
 
 int solve_fp64(bura_plan* p, const double* f, double tol, cudaStream_t s) {
@@ -1572,6 +1608,75 @@ int check_options(const bura_options& o) {
     return BURA_OK;
 }
 
+// The device part of a plan's setup (after its levels and coefficients are on the host): workspaces,
+// tables, tensor maps, refinement buffers.  Frees the plan on failure.
+int setup_device(bura_plan* p, long long N, bura_plan** out) {
+    auto fail = [&](int rc) { destroy_plan(p); return rc; };
+    const bura_options& o = p->opt;
+    int rc = BURA_OK;
+    if (cudaGetDevice(&p->dev) != cudaSuccess) return fail(BURA_ECUDA);
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        p->cap = nullptr;
+        return fail(BURA_ECUDA);
+    }
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess || nsm <= 0)
+        return fail(BURA_ECUDA);
+    p->nsm = nsm;
+    int cl = 0;
+    p->cluster_ok = cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, p->dev) == cudaSuccess && cl != 0;
+    if (o.coarse_kernel == BURA_COARSE_CLUSTER && !p->cluster_ok) return fail(BURA_EINVAL);
+    if (p->dim == 0) {  // the sparse operator's row offsets and columns, shared by both precisions
+        const HostLevel& h = p->hl[0];
+        int* rp = nullptr;
+        int* ci = nullptr;
+        if ((rc = dalloc(p, &rp, h.rowptr.size() * sizeof(int))) != BURA_OK) return fail(rc);
+        if ((rc = dalloc(p, &ci, h.col.size() * sizeof(int))) != BURA_OK) return fail(rc);
+        if (cudaMemcpy(rp, h.rowptr.data(), h.rowptr.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(ci, h.col.data(), h.col.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(BURA_ECUDA);
+        p->csr_rowptr = rp;
+        p->csr_col = ci;
+    }
+
+    rc = build_work<double>(p, p->w64, o.precision == BURA_PREC_FP64);
+    if (rc != BURA_OK) return fail(rc);
+    if (o.precision == BURA_PREC_MIXED) {
+        rc = build_work<float>(p, p->w32);
+        if (rc != BURA_OK) return fail(rc);
+    }
+    const size_t v64b = (size_t)N * p->w64.Kp * sizeof(double);
+    if ((rc = dalloc(p, &p->v64, v64b)) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->r64, v64b)) != BURA_OK) return fail(rc);
+    const size_t max_blocks = (size_t)nsm * std::max(8, o.blocks_per_sm);
+    const size_t max_groups = (max_blocks + kRedGroup - 1) / kRedGroup;
+    if ((rc = dalloc(p, &p->partial, (max_blocks + max_groups) * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->tickets, (max_groups + 2) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
+    if (cudaMemset(p->tickets, 0, (max_groups + 2) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
+    p->red_nblk = p->tickets + max_groups + 1;
+    if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if (o.precision == BURA_PREC_MIXED && o.refine == BURA_REFINE_DF && (rc = build_df(p)) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = upload_outer(p)) != BURA_OK) return fail(rc);
+    if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
+        p->done = nullptr;
+        return fail(BURA_ECUDA);
+    }
+    if (cudaMallocHost(&p->hscal, sizeof(Scal)) != cudaSuccess) { p->hscal = nullptr; return fail(BURA_ENOMEM); }
+    if (cudaMallocHost(&p->hbuf, 4 * KMAXP * sizeof(double)) != cudaSuccess) { p->hbuf = nullptr; return fail(BURA_ENOMEM); }
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(BURA_ECUDA);
+    p->st.Lambda = p->Lambda;
+    p->st.E = p->E;
+    p->st.k = p->K - 1;
+    p->st.levels = (int)p->hl.size();
+    p->st.lambda_lo = p->lambda_lo;
+    *out = p;
+    return BURA_OK;
+}
+
 // A plan for the K weights c and shifts d (d[0] >= d[1] >= ... , all <= 0, c > 0) of a partial-fraction
 // sum u = sum_j c_j (A - d_j I)^{-1} f on the grid: scaling, multigrid hierarchy, tables, workspaces.
 int setup_plan(const bura_grid* grid, const double* const* faces, long long N, int K, const double* c,
@@ -1632,55 +1737,7 @@ int setup_plan(const bura_grid* grid, const double* const* faces, long long N, i
     p->lambda_lo = p->hl[0].lmin * (1.0 - 1e-12);
     p->out_scale = o.unscaled ? std::pow(p->Lambda, -alpha) : 1.0;
 
-    if (cudaGetDevice(&p->dev) != cudaSuccess) return fail(BURA_ECUDA);
-    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
-        p->cap = nullptr;
-        return fail(BURA_ECUDA);
-    }
-    int nsm = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess || nsm <= 0)
-        return fail(BURA_ECUDA);
-    p->nsm = nsm;
-    int cl = 0;
-    p->cluster_ok = cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, p->dev) == cudaSuccess && cl != 0;
-    if (o.coarse_kernel == BURA_COARSE_CLUSTER && !p->cluster_ok) return fail(BURA_EINVAL);
-
-    rc = build_work<double>(p, p->w64, o.precision == BURA_PREC_FP64);
-    if (rc != BURA_OK) return fail(rc);
-    if (o.precision == BURA_PREC_MIXED) {
-        rc = build_work<float>(p, p->w32);
-        if (rc != BURA_OK) return fail(rc);
-    }
-    const size_t v64b = (size_t)N * p->w64.Kp * sizeof(double);
-    if ((rc = dalloc(p, &p->v64, v64b)) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->r64, v64b)) != BURA_OK) return fail(rc);
-    const size_t max_blocks = (size_t)nsm * std::max(8, o.blocks_per_sm);
-    const size_t max_groups = (max_blocks + kRedGroup - 1) / kRedGroup;
-    if ((rc = dalloc(p, &p->partial, (max_blocks + max_groups) * KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->tickets, (max_groups + 2) * sizeof(unsigned int))) != BURA_OK) return fail(rc);
-    if (cudaMemset(p->tickets, 0, (max_groups + 2) * sizeof(unsigned int)) != cudaSuccess) return fail(BURA_ECUDA);
-    p->red_nblk = p->tickets + max_groups + 1;
-    if ((rc = dalloc(p, &p->red_out, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->scale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->invscale, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if (o.precision == BURA_PREC_MIXED && o.refine == BURA_REFINE_DF && (rc = build_df(p)) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
-    if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
-    if ((rc = upload_outer(p)) != BURA_OK) return fail(rc);
-    if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
-        p->done = nullptr;
-        return fail(BURA_ECUDA);
-    }
-    if (cudaMallocHost(&p->hscal, sizeof(Scal)) != cudaSuccess) { p->hscal = nullptr; return fail(BURA_ENOMEM); }
-    if (cudaMallocHost(&p->hbuf, 4 * KMAXP * sizeof(double)) != cudaSuccess) { p->hbuf = nullptr; return fail(BURA_ENOMEM); }
-    if (cudaDeviceSynchronize() != cudaSuccess) return fail(BURA_ECUDA);
-    p->st.Lambda = p->Lambda;
-    p->st.E = p->E;
-    p->st.k = K - 1;
-    p->st.levels = (int)p->hl.size();
-    p->st.lambda_lo = p->lambda_lo;
-    *out = p;
-    return BURA_OK;
+    return setup_device(p, N, out);
 }
 
 
@@ -1703,6 +1760,99 @@ int bura_setup(const bura_grid* grid, const double* const* faces, double alpha, 
     double E = 0.0;
     CA(bura_rational(alpha, k, c.data(), d.data(), &E));
     return setup_plan(grid, faces, N, k + 1, c.data(), d.data(), E, alpha, false, o, out);
+}
+
+int bura_setup_csr(const bura_csr* A, double alpha, int k, const bura_options* opt, bura_plan** out) {
+    if (!out) return BURA_EINVAL;
+    *out = nullptr;
+    if (!A || !A->row_ptr || !A->col || !A->val || A->n < 1 || A->nnz < A->n) return BURA_EINVAL;
+    if (!(alpha > 0 && alpha < 1) || k < 1 || k > BURA_MAX_K) return BURA_EINVAL;
+    if ((long long)A->n * 16 >= (1LL << 31) || A->nnz >= (1LL << 31)) return BURA_ERANGE;
+    if (!(A->lambda_min >= 0) || !std::isfinite(A->lambda_min)) return BURA_EINVAL;
+    bura_options o;
+    bura_default_options(&o);
+    if (opt) o = *opt;
+    CA(check_options(o));
+    if (o.refine == BURA_REFINE_DF) return BURA_EINVAL;  // double-float refinement: grids only
+    // structure: offsets from 0 to nnz, columns in range, finite values, a positive diagonal in every row,
+    // and symmetry (the entries sorted by (row, col) and by (col, row) must agree)
+    const int n = A->n;
+    const long long nnz = A->nnz;
+    if (A->row_ptr[0] != 0 || A->row_ptr[n] != nnz) return BURA_EINVAL;
+    HostLevel h0;
+    h0.n[0] = n;
+    h0.n[1] = h0.n[2] = 1;
+    h0.N = n;
+    h0.h[0] = h0.h[1] = h0.h[2] = 0.0;
+    h0.w[0] = h0.w[1] = h0.w[2] = 0.0;
+    h0.rowptr.assign(A->row_ptr, A->row_ptr + n + 1);
+    h0.col.assign(A->col, A->col + nnz);
+    h0.diag.assign(n, 0.0);
+    h0.rowsum.assign(n, 0.0);
+    std::vector<long long> ord((size_t)nnz);
+    for (int i = 0; i < n; ++i) {
+        if (A->row_ptr[i + 1] < A->row_ptr[i]) return BURA_EINVAL;
+        for (int q = A->row_ptr[i]; q < A->row_ptr[i + 1]; ++q) {
+            const int j = A->col[q];
+            const double v = A->val[q];
+            if (j < 0 || j >= n || !std::isfinite(v)) return BURA_EINVAL;
+            if (j == i) h0.diag[i] += v;
+            h0.rowsum[i] += std::fabs(v);
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (!(h0.diag[i] > 0)) return BURA_EINVAL;
+    {
+        struct E { int r, c; double v; };
+        std::vector<E> a, t;
+        a.reserve((size_t)nnz);
+        t.reserve((size_t)nnz);
+        for (int i = 0; i < n; ++i)
+            for (int q = A->row_ptr[i]; q < A->row_ptr[i + 1]; ++q) {
+                a.push_back({i, A->col[q], A->val[q]});
+                t.push_back({A->col[q], i, A->val[q]});
+            }
+        auto lt = [](const E& x, const E& y) { return x.r != y.r ? x.r < y.r : x.c < y.c; };
+        std::sort(a.begin(), a.end(), lt);
+        std::sort(t.begin(), t.end(), lt);
+        double amax = 0.0;
+        for (const E& e : a) amax = std::max(amax, std::fabs(e.v));
+        for (size_t q = 0; q < a.size(); ++q)
+            if (a[q].r != t[q].r || a[q].c != t[q].c || std::fabs(a[q].v - t[q].v) > 1e-14 * amax) return BURA_EINVAL;
+    }
+    double Lambda = 0.0;
+    for (int i = 0; i < n; ++i) Lambda = std::max(Lambda, h0.rowsum[i]);
+    h0.val.resize((size_t)nnz);
+    for (long long q = 0; q < nnz; ++q) h0.val[q] = A->val[q] / Lambda;
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        h0.diag[i] /= Lambda;
+        h0.rowsum[i] /= Lambda;
+        dmax = std::max(dmax, h0.diag[i]);
+    }
+    h0.amax = dmax;
+    h0.lmin = A->lambda_min / Lambda;
+    std::vector<double> c(k + 1, 0.0), d(k + 1, 0.0);
+    double E = 0.0;
+    CA(bura_rational(alpha, k, c.data(), d.data(), &E));
+    std::shared_lock<std::shared_mutex> guard(g_capture_guard);
+    bura_plan* p = new (std::nothrow) bura_plan();
+    if (!p) return BURA_ENOMEM;
+    p->dim = 0;
+    p->var = true;
+    p->k = k;
+    p->K = k + 1;
+    p->alpha = alpha;
+    p->opt = o;
+    p->wait_cycles = o.tma_wait_cycles;
+    p->c = c;
+    p->d = d;
+    p->E = E;
+    p->Lambda = Lambda;
+    p->lambda_lo = h0.lmin > 0 ? h0.lmin * (1.0 - 1e-12) : 0.0;
+    p->out_scale = o.unscaled ? std::pow(Lambda, -alpha) : 1.0;
+    p->hl.push_back(std::move(h0));
+    return setup_device(p, n, out);
 }
 
 int bura_scale(const bura_grid* grid, const double* const* faces, double* Lambda) {

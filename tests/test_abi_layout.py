@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 STRUCTS = {"bura_grid": bura.bura_grid, "bura_options": bura.bura_options, "bura_stats": bura.bura_stats,
            "bura_kernel_prof": bura.bura_kernel_prof, "bura_server_options": bura.bura_server_options,
            "bura_request": bura.bura_request, "bura_request_info": bura.bura_request_info,
-           "bura_server_stats": bura.bura_server_stats}
+           "bura_server_stats": bura.bura_server_stats, "bura_csr": bura.bura_csr}
 
 
 def test_struct_layouts_match_the_header(tmp_path):

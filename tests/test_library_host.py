@@ -246,3 +246,43 @@ def test_bp15_nodes_match_the_oracle(lib, alpha, kp):
     buf = np.zeros(2)
     rc = lib._lib().bura_quadrature_bp15(alpha, kp, lam, 2, lib._hptr(buf), lib._hptr(buf.copy()), C.byref(n))
     assert rc == lib.BURA_ERANGE and n.value == len(co)
+
+
+def _csr(A):
+    return A.indptr, A.indices, A.data
+
+
+@pytest.mark.parametrize("case", ["unsymmetric", "no_diagonal", "negative_diagonal", "bad_column", "nan",
+                                  "bad_offsets", "negative_lambda_min"])
+def test_setup_csr_rejects_bad_matrices_on_the_host(lib, case):
+    """bura_setup_csr checks the structure (offsets, columns, finite values, a positive diagonal in every
+    row) and the symmetry of the matrix before any CUDA call."""
+    import scipy.sparse as sp
+    from oracle import operators
+    A = operators.fd_matrix((5, 4)).tocsr().astype(np.float64)
+    A.sort_indices()
+    rp, ci, va = A.indptr.copy(), A.indices.copy(), A.data.copy()
+    lam = 0.0
+    if case == "unsymmetric":
+        va[1] *= 2.0
+    elif case == "no_diagonal":
+        B = A.tolil()
+        B[3, 3] = 0.0
+        B = B.tocsr()
+        B.eliminate_zeros()
+        rp, ci, va = B.indptr, B.indices, B.data
+    elif case == "negative_diagonal":
+        va[np.where(ci[: rp[1]] == 0)[0][0]] = -1.0
+    elif case == "bad_column":
+        ci = ci.copy()
+        ci[-1] = 99
+    elif case == "nan":
+        va[0] = float("nan")
+    elif case == "bad_offsets":
+        rp = rp.copy()
+        rp[-1] += 1
+    elif case == "negative_lambda_min":
+        lam = -1.0
+    with pytest.raises(lib.BuraError) as ei:
+        lib.bura_setup_csr(rp, ci, va, 0.5, 5, lambda_min=lam)
+    assert ei.value.code == lib.BURA_EINVAL
