@@ -260,13 +260,30 @@ int bura_quadrature_bp15(double alpha, double kprime, double Lambda, int cap, do
 /*
  * u = sum_j c_j (A - d_j I)^{-1} f, stream-ordered on `stream` (a cudaStream_t; NULL = the
  * legacy default stream).  f and u are DEVICE arrays of N doubles owned by the caller (they
- * may alias each other).  The call returns once the solve has converged; u is complete when
- * `stream` reaches this point.
+ * may alias each other).  The call returns once the solve has finished (bura_solve_async + bura_solve_wait);
+ * u is complete when `stream` reaches this point.
  *   tol: target bound on ||u - u_r|| / ||f||, u_r the exact value of eq. (Rgeneral).  Each system
  *        j stops when c_j ||f - (A - d_j I) v_j|| / (lambda_lo - d_j) <= tol ||f|| / (k+1).
  * Errors: BURA_EINVAL, BURA_ENOTSPD, BURA_ENOCONV (u still written), BURA_ECUDA.
  */
 int bura_solve(bura_plan* plan, const double* f, double* u, double tol, void* stream);
+
+/*
+ * bura_solve without waiting: the whole solve (the FP64 path, or the mixed path with FP64 refinement) runs
+ * as one captured CUDA graph whose controller kernels take every decision on the device (thresholds,
+ * refinement plan, convergence), so the call only enqueues work on `stream` and returns BURA_OK (or an
+ * argument / CUDA error).  u is complete when `stream` reaches this point; bura_solve_wait returns the
+ * solve's status.  The plan's buffers serve this solve until it completes: a later call on the same plan
+ * must be ordered after it (the same stream, or an event).  With double-float refinement or profiling on,
+ * the solve is host-driven and finishes within the call.  f and u as for bura_solve.
+ */
+int bura_solve_async(bura_plan* plan, const double* f, double* u, double tol, void* stream);
+
+/*
+ * Waits for the plan's last solve and returns its status (BURA_OK, BURA_ENOCONV, BURA_ENOTSPD,
+ * BURA_ETIMEOUT, or BURA_ECUDA if waiting failed); bura_get_stats then describes that solve.
+ */
+int bura_solve_wait(bura_plan* plan);
 
 /*
  * Same as bura_solve with HOST arrays f and u (N doubles each): copies f to the device,
@@ -394,7 +411,9 @@ int bura_destroy(bura_plan* plan);
 
 /* Batched solves: n independent problems, one per plan, solved concurrently on this GPU; every problem
  * is one BURA solve of eq. (Rgeneral) (its k+1 shifted systems are independent), so many systems x shifts
- * x right-hand sides are in flight together.
+ * x right-hand sides are in flight together.  When every plan is device-driven (see bura_batch_create) the
+ * call captures the batch as one graph, launches it once and waits (nworkers = parallel branches);
+ * otherwise worker threads solve the plans on their own streams as described below.
  *   plans[i]  plan of problem i (grid, coefficients, alpha, k, options of its own); a plan may appear
  *             only once in the list (its buffers serve one solve at a time);
  *   f[i]      device FP64 right-hand side of plan i's grid (N_i values, lexicographic, x fastest);
@@ -410,6 +429,28 @@ int bura_destroy(bura_plan* plan);
  * other error of any problem, or BURA_EINVAL (null pointers, n < 0, a plan listed twice). */
 int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
                      int nworkers, int* status);
+
+/*
+ * A batch captured once and launched many times: every problem's whole solve (its solve record, ||f||, the
+ * device-side controller, the refinement and PCG loops, the weighted sum and the outcome) is one branch of
+ * one CUDA graph, `branches` branches in parallel (problem i on branch i % branches; 0 = 64), so one launch
+ * solves all n problems of eq. (Rgeneral) with no host step between them.  Each problem runs the kernels
+ * and fixed-order reductions of its plan exactly as bura_solve does, so u[i] is bit-for-bit its single-
+ * problem result.  plans, f, u as for bura_solve_batch (device arrays; the addresses are part of the graph,
+ * so later runs read and write the same buffers); tol as for bura_solve.  Every plan must be device-driven
+ * (FP64, or mixed precision with FP64 refinement, profiling off) and on one device.  The plans must outlive
+ * the batch and must not be used by another solve while a run is in flight.
+ *   bura_batch_run enqueues one run on `stream`; bura_batch_wait waits for it and writes each problem's
+ *   status to status[i] (optional); bura_batch_destroy waits for the plans' last solves and frees the graph.
+ * Errors: BURA_EINVAL (null pointers, n < 1, a plan listed twice, a plan that is not device-driven, plans on
+ *         different devices, tol <= 0), BURA_ENOMEM, BURA_ECUDA; bura_batch_wait as bura_solve_batch.
+ */
+typedef struct bura_batch bura_batch;
+int bura_batch_create(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
+                      int branches, bura_batch** out);
+int bura_batch_run(bura_batch* batch, void* stream);
+int bura_batch_wait(bura_batch* batch, int* status);
+int bura_batch_destroy(bura_batch* batch);
 
 /*
  * Solve server: a continuous-batching front end for many independent requests (grids, coefficient

@@ -1,7 +1,8 @@
 """Compile the C-ABI shared library libbura.so in-tree with nvcc for sm_103a.
 
 Sources live in csrc/; the translation units are compiled in parallel and linked with
-``nvcc -shared``.  The library is rebuilt when a source or header is newer than it.
+``nvcc -shared``.  The library is rebuilt when a source or header is newer than it.  Extra nvcc flags
+(for instance a -D of a tuning macro) can be given in the environment variable BURA_NVCC_FLAGS.
 """
 from __future__ import annotations
 
@@ -15,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbura.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "solver.cu",
-           "noalloc.cu", "serve.cpp"]
+SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "outer.cu",
+           "solver.cu", "noalloc.cu", "serve.cpp"]
 HEADERS = ["kernels.cuh", "kernels_impl.cuh", "tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -39,7 +40,8 @@ def _stale():
 def _compile(src):
     out = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [_nvcc(), "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
-           "-I" + os.path.join(ROOT, "include"), *ARCH, "-c", os.path.join(CSRC, src), "-o", out]
+           "-I" + os.path.join(ROOT, "include"), *ARCH, *os.environ.get("BURA_NVCC_FLAGS", "").split(), "-c",
+           os.path.join(CSRC, src), "-o", out]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
         cmd.insert(2, "c++")

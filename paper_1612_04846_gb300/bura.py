@@ -119,6 +119,12 @@ def _lib():
                                  C.POINTER(P)]
         L.bura_solve.argtypes = [P, P, P, D, P]
         L.bura_solve_host.argtypes = [P, dp, dp, D, P]
+        L.bura_solve_async.argtypes = [P, P, P, D, P]
+        L.bura_solve_wait.argtypes = [P]
+        L.bura_batch_create.argtypes = [C.POINTER(P), C.POINTER(P), C.POINTER(P), I, D, I, C.POINTER(P)]
+        L.bura_batch_run.argtypes = [P, P]
+        L.bura_batch_wait.argtypes = [P, C.POINTER(I)]
+        L.bura_batch_destroy.argtypes = [P]
         L.bura_solve_systems.argtypes = [P, P, P, D, P]
         L.bura_apply_shifted.argtypes = [P, P, P, P]
         L.bura_get_rational.argtypes = [P, dp, dp, dp]
@@ -152,7 +158,9 @@ def _lib():
                      "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
                      "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
                      "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts", "bura_solve_sum",
-                     "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr", "bura_server_create", "bura_server_submit",
+                     "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr", "bura_solve_async",
+                     "bura_solve_wait", "bura_batch_create", "bura_batch_run", "bura_batch_wait", "bura_batch_destroy",
+                     "bura_server_create", "bura_server_submit",
                      "bura_server_wait", "bura_server_get_stats", "bura_server_destroy"):
             getattr(L, name).restype = I
         _LIB = L
@@ -310,6 +318,16 @@ def bura_solve(plan, f, u, tol, stream=None):
                   allow=(BURA_ENOCONV,))
 
 
+def bura_solve_async(plan, f, u, tol, stream=None):
+    """Enqueue u = sum_j c_j (A - d_j I)^{-1} f without waiting (device float64 tensors)."""
+    return _check(_lib().bura_solve_async(plan, _dptr(f), _dptr(u), float(tol), _stream(stream)), "bura_solve_async")
+
+
+def bura_solve_wait(plan):
+    """Status of the plan's last solve (waits for it); raises on an error other than BURA_ENOCONV."""
+    return _check(_lib().bura_solve_wait(plan), "bura_solve_wait", allow=(BURA_ENOCONV,))
+
+
 def bura_solve_batch(plans, fs, us, tol, nworkers=0):
     """Solve len(plans) independent problems concurrently (device float64 tensors fs[i], us[i]).
     Returns the list of per-problem statuses; raises on an error other than BURA_ENOCONV."""
@@ -324,6 +342,37 @@ def bura_solve_batch(plans, fs, us, tol, nworkers=0):
     _check(_lib().bura_solve_batch(pa, fa, ua, int(n), float(tol), int(nworkers), st), "bura_solve_batch",
            allow=(BURA_ENOCONV,))
     return list(st)[:n]
+
+
+class BuraBatch:
+    """bura_batch_create / _run / _wait / _destroy: a batch of (plan, f, u) captured once as one graph."""
+
+    def __init__(self, plans, fs, us, tol, branches=0):
+        n = len(plans)
+        if len(fs) != n or len(us) != n or n == 0:
+            raise ValueError("plans, fs and us must have the same nonzero length")
+        P = C.c_void_p
+        self._keep = (list(fs), list(us))
+        pa = (P * n)(*[C.cast(p, P) for p in plans])
+        fa = (P * n)(*[_dptr(t) for t in fs])
+        ua = (P * n)(*[_dptr(t) for t in us])
+        self.n = n
+        self.b = C.c_void_p()
+        _check(_lib().bura_batch_create(pa, fa, ua, int(n), float(tol), int(branches), C.byref(self.b)),
+               "bura_batch_create")
+
+    def run(self, stream=None):
+        return _check(_lib().bura_batch_run(self.b, _stream(stream)), "bura_batch_run")
+
+    def wait(self):
+        st = (C.c_int * self.n)()
+        _check(_lib().bura_batch_wait(self.b, st), "bura_batch_wait", allow=(BURA_ENOCONV,))
+        return list(st)
+
+    def close(self):
+        if self.b is not None:
+            _lib().bura_batch_destroy(self.b)
+            self.b = None
 
 
 def bura_solve_chain(plans, f, u, tol, stream=None):
@@ -504,6 +553,8 @@ EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve",
             "bura_solve_systems", "bura_apply_shifted", "bura_get_rational", "bura_get_stats", "bura_destroy",
             "bura_strerror", "bura_set_profiling", "bura_get_profile", "bura_residual_norms_noalloc",
             "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts",
-            "bura_solve_sum", "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr", "bura_server_default_options",
+            "bura_solve_sum", "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr",
+            "bura_solve_async", "bura_solve_wait", "bura_batch_create", "bura_batch_run", "bura_batch_wait",
+            "bura_batch_destroy", "bura_server_default_options",
             "bura_server_create", "bura_server_submit", "bura_server_wait", "bura_server_get_stats",
             "bura_server_destroy"]

@@ -70,6 +70,28 @@ struct Scal {
     long long wait_cycles;  // SM clocks a TMA kernel waits for one stage of its ring before giving up
 };
 
+// Device-driven solve (the whole solve one captured graph): the per-plan constants of the refinement
+// controller and the per-solve state it keeps (right-hand side and output addresses, tolerance, the
+// FP64 thresholds and plan, the outcome).  Written by k_solve_params / the controller kernels only.
+struct OuterCfg {
+    double c[KMAXP], d[KMAXP];  // weights and shifts
+    double lambda_lo;           // lower bound on lambda_min(A); 0: relative residual thresholds
+    double inner_rtol;          // largest residual reduction asked of one FP32 inner solve
+    long long wait_cycles;      // TMA ring wait budget of the inner solves (0: default)
+    int K, max_outer, max_iters;
+};
+struct OuterState {
+    const double* f;            // this solve's right-hand side (device)
+    double tol;
+    double fnorm2;
+    double thr64[KMAXP];        // FP64 thresholds on ||r_j||^2
+    double step[KMAXP];         // planned per-step residual reduction of each system
+    double rr[KMAXP];           // latest FP64 ||r_j||^2
+    int siters[KMAXP];          // iterations of each system over all inner solves
+    int outer, total_it, status;  // refinement steps, PCG iterations, bura_status of the solve
+    int done;                   // 1 once the controller has decided
+};
+
 // Chebyshev step coefficients of one level: d_m = c1 d_{m-1} + c2 Dinv res (c2 includes 1/(diag - d)
 // for constant coefficients, where Dinv is a per-system scalar).
 template <class C>
@@ -174,7 +196,8 @@ struct Launch {
 // ------------------------------------------------------------------ host launchers
 template <class T>
 struct Ops {
-    static void broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s);
+    static void broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s,
+                          const double* const* fp = nullptr);
     static void spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, T* pa, T* pb, T* q,
                        const Red& red, cudaStream_t s);
     static void cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, const T* pb, const T* q,
@@ -229,8 +252,10 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 // FP64 refinement and output kernels.
+// fp (optional): the address of a device pointer to the right-hand side, read by the kernel instead of f
+// (a captured solve whose right-hand side changes from launch to launch)
 void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
-                       double* r, const Red& red, cudaStream_t s);
+                       double* r, const Red& red, cudaStream_t s, const double* const* fp = nullptr);
 void launch_cast_scaled(const Launch& g64, const Launch& g32, long long N, int K, const double* r64,
                         const double* scale, float* r32, float* x32, float* p32, cudaStream_t s);
 void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, double* v, const float* e,
@@ -240,10 +265,23 @@ void launch_cast_f(const Launch& g32, long long N, int K, const double* f, const
 // u = sum_j c_j v_j (accumulate = 0) or u += sum_j c_j v_j (accumulate = 1), j = 0..K-1 in order.
 void launch_weighted_sum(long long N, int Kp, int K, const double* v, const double* c, double* u, int accumulate,
                          cudaStream_t s);
-void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s);
+void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s,
+                  const double* const* fp = nullptr);
 void launch_gather_systems(long long N, int Kp, int K, const double* v, double* V, cudaStream_t s);
 void launch_scatter_systems(long long N, int Kp, int K, const double* X, double* x, cudaStream_t s);
 void launch_gather_systems_f(long long N, int Kp, int K, const float* v, double* V, cudaStream_t s);
+
+// Device-side control of a captured solve (outer.cu).
+void launch_solve_params(OuterState* st, const double* f, double tol, cudaStream_t s);
+void launch_outer_begin(const OuterCfg* cfg, OuterState* st, const double* norm_partials, Scal* sc, double* scale,
+                        double* invscale, unsigned long long cond_outer, unsigned long long cond_inner, int fp64,
+                        cudaStream_t s);
+void launch_outer_next(const OuterCfg* cfg, OuterState* st, const double* rr_partials, Scal* sc, double* scale,
+                       double* invscale, unsigned long long cond_outer, cudaStream_t s);
+void launch_outer_end_fp64(const OuterCfg* cfg, OuterState* st, const Scal* sc, cudaStream_t s);
+void launch_cast_outer(const Launch& g64, const Launch& g32, long long N, int K, const OuterState* st,
+                       const double* r64, const double* invscale, float* r32, float* x32, float* p32,
+                       unsigned long long cond_inner, cudaStream_t s);
 
 // Double-float refinement of the mixed path (kernels_df.cu).  DfOpHost holds device pointers and the
 // hi/lo FP32 parts of the level-0 operator's coefficients.

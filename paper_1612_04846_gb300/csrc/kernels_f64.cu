@@ -9,9 +9,10 @@ template struct Ops<double>;
 
 // r = f - (A - d_j I) v (FP64 true residual of every system) and ||r_j||^2 -> red.out.
 template <int DIM, bool VAR>
-__global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const double* __restrict__ v,
-                             double* __restrict__ r, const double* __restrict__ dsh, Red red) {
+__global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f_arg, const double* const* fp,
+                             const double* __restrict__ v, double* __restrict__ r, const double* __restrict__ dsh, Red red) {
     constexpr int W = 2;
+    const double* __restrict__ f = fp ? *fp : f_arg;  // a captured solve reads its right-hand side's address
     const int off = threadIdx.x * W;
     double d[W];
     for (int q = 0; q < W; ++q) d[q] = dsh[off + q];
@@ -75,15 +76,15 @@ __global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f, const 
 }
 
 void launch_residual64(const Launch& g, const Lev& L, int dim, bool var, const double* f, const double* v,
-                       double* r, const Red& red, cudaStream_t s) {
+                       double* r, const Red& red, cudaStream_t s, const double* const* fp) {
     const size_t sh = (size_t)g.C * g.PPB * 2 * sizeof(double);
     // the shifts live in the device Scal record (address arithmetic only, no host dereference)
     const double* dsh = reinterpret_cast<const double*>(reinterpret_cast<const char*>(red.scal) + offsetof(Scal, dsh));
-    if (dim == 0) k_residual64<0, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
-    else if (dim == 2 && !var) k_residual64<2, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
-    else if (dim == 2) k_residual64<2, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
-    else if (!var) k_residual64<3, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
-    else k_residual64<3, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, v, r, dsh, red);
+    if (dim == 0) k_residual64<0, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, fp, v, r, dsh, red);
+    else if (dim == 2 && !var) k_residual64<2, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, fp, v, r, dsh, red);
+    else if (dim == 2) k_residual64<2, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, fp, v, r, dsh, red);
+    else if (!var) k_residual64<3, false><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, fp, v, r, dsh, red);
+    else k_residual64<3, true><<<g.blocks, dim3(g.C, g.PPB), sh, s>>>(L, g.Kp, f, fp, v, r, dsh, red);
 }
 
 // r32 = r64 * invscale_j (systems j < K with invscale > 0, else 0); x32 = 0; p32 = 0.  FP32 layout.
@@ -138,7 +139,8 @@ void launch_correct64(const Launch& g64, const Launch& g32, long long N, int K, 
 
 // ||f||^2 of a plain FP64 vector (red.out[0]); threads laid out as (1, 256) with two lanes of which
 // the second stays zero, so the shared reduction machinery applies unchanged.
-__global__ void k_norm2(int N, const double* __restrict__ f, Red red) {
+__global__ void k_norm2(int N, const double* __restrict__ f_arg, const double* const* fp, Red red) {
+    const double* __restrict__ f = fp ? *fp : f_arg;
     Accum<double> acc;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
@@ -152,11 +154,11 @@ __global__ void k_norm2(int N, const double* __restrict__ f, Red red) {
     reduce_finish<double>(acc, red, KMAXP);
 }
 
-void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s) {
+void launch_norm2(long long N, const double* f, const Red& red, int nsm, cudaStream_t s, const double* const* fp) {
     long long b = (N + 255) / 256;
     const int blocks = (int)(b < nsm * 2 ? (b > 0 ? b : 1) : nsm * 2);
     static_assert(KMAXP == 8 * 2, "k_norm2's launch shape gives KMAXP lanes");
-    k_norm2<<<blocks, dim3(8, 32), 256 * 2 * sizeof(double), s>>>((int)N, f, red);
+    k_norm2<<<blocks, dim3(8, 32), 256 * 2 * sizeof(double), s>>>((int)N, f, fp, red);
 }
 
 // Final step of a deferred grid reduction (Red::defer): the producer, the previous kernel on the

@@ -66,6 +66,26 @@ struct Accum {
 };
 
 struct Coord { int i, j, l; };
+
+// CTAs per SM the grid sweeps are compiled for (the register budget is 65536 / (256 x this)): the
+// 2-D constant-coefficient stencils fit 64 registers, the 3-D, variable-coefficient and sparse ones
+// (face weights, diagonal, coordinates of three axes) need BURA_SWEEP_REG_MINB or they spill.
+#ifndef BURA_SWEEP_REG_MINB
+#define BURA_SWEEP_REG_MINB 3
+#endif
+template <int DIM, bool VAR>
+constexpr int sweep_min_blocks() {
+    return (DIM == 2 && !VAR) ? kSweepMinBlocks : BURA_SWEEP_REG_MINB;
+}
+
+// Division by a shifted diagonal inside the preconditioner (Jacobi scaling of the Chebyshev steps): the
+// FP32 kernels use the fast reciprocal-based division (a deterministic function of its operands, so the
+// smoother stays the same fixed operator in every pre- and post-smoothing step); FP64 divides exactly.
+template <class T>
+__device__ __forceinline__ T jdiv(T a, T b) {
+    if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+    else return a / b;
+}
 template <int DIM>
 __device__ __forceinline__ Coord coord(const Lev& L, int P) {
     Coord c;
@@ -157,15 +177,15 @@ struct LoadPUpd {
 // First Chebyshev iterate from a zero guess, x1 = c2_0 Dinv b, evaluated on the fly.
 template <class T, int DIM, bool VAR>
 struct LoadCheb0 {
-    Lev L;
+    const T* dg;  // the level's diagonal (variable coefficients and sparse operators)
     const T* b;
     T c2[VecT<T>::W];
     T d[VecT<T>::W];
     __device__ __forceinline__ void operator()(int P, size_t idx, T (&o)[VecT<T>::W]) const {
         vld(b + idx, o);
         if (VAR) {
-            const T dg = diag_at<T, DIM, VAR>(L, P);
-            for (int v = 0; v < VecT<T>::W; ++v) o[v] = c2[v] * o[v] / (dg - d[v]);
+            const T dp = __ldg(dg + P);
+            for (int v = 0; v < VecT<T>::W; ++v) o[v] = jdiv(c2[v] * o[v], dp - d[v]);
         } else {
             for (int v = 0; v < VecT<T>::W; ++v) o[v] *= c2[v];
         }
@@ -502,7 +522,7 @@ __device__ __forceinline__ void sw_cheb_zero(const Lev& L, int Kp, const T* b, T
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
     LoadCheb0<T, DIM, VAR> ld;
-    ld.L = L;
+    ld.dg = reinterpret_cast<const T*>(L.dg);
     ld.b = b;
     for (int v = 0; v < W; ++v) { ld.c2[v] = (T)cs.c2[off + v]; ld.d[v] = (T)dsh[off + v]; }
     BURA_SWEEP(L.N) {
@@ -544,7 +564,7 @@ __device__ __forceinline__ void sw_cheb_step(const Lev& L, int Kp, const LD& ld,
             for (int v = 0; v < W; ++v) {
                 const T res = st.bv[v] - fma(-d[v], st.xc[v], st.Ax[v]);
                 T g = c2[v] * res;
-                if (VAR) g = g / (st.diag - d[v]);
+                if (VAR) g = jdiv(g, st.diag - d[v]);
                 st.dv[v] = fma(c1[v], st.dv[v], g);
                 xo[v] = st.xc[v] + st.dv[v];
             }
@@ -660,8 +680,9 @@ __device__ __forceinline__ void sw_prolong_add(const Lev& Lf, const Lev& Lc, int
 
 // ------------------------------------------------------------------ grid kernels
 template <class T>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_broadcast(const double* __restrict__ f, int N, int Kp, int K, T* r, T* x, T* p) {
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_broadcast(const double* __restrict__ f_arg, const double* const* fp, int N, int Kp, int K, T* r, T* x, T* p) {
     pdl_wait();
+    const double* __restrict__ f = fp ? *fp : f_arg;
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
     const int b0 = blockIdx.x, nb = gridDim.x;
@@ -679,7 +700,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_broadcast(co
 // The two direction buffers pa/pb alternate roles each iteration; the parity lives in the Scal
 // record (toggled by the last block of k_cg_update), so a captured loop body can stay fixed.
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_spmv_p(Lev L, int Kp, const T* __restrict__ z, T* pa, T* pb, T* __restrict__ q, Red red) {
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_spmv_p(Lev L, int Kp, const T* __restrict__ z, T* pa, T* pb, T* __restrict__ q, Red red) {
     pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
@@ -746,7 +767,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cg_update(in
 }
 
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_zero(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ x, ChebStepT<T> cs,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_cheb_zero(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ x, ChebStepT<T> cs,
                             const T* __restrict__ dsh) {
     pdl_wait();
     sw_cheb_zero<T, DIM, VAR>(L, Kp, b, x, cs, dsh, blockIdx.x, gridDim.x);
@@ -754,7 +775,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_zero(Le
 
 // Plain Chebyshev step (input iterate read from xin).
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_step(Lev L, int Kp, const T* __restrict__ xin, const T* __restrict__ din,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_cheb_step(Lev L, int Kp, const T* __restrict__ xin, const T* __restrict__ din,
                             const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStepT<T> cs,
                             const T* __restrict__ dsh, Red red) {
     pdl_wait();
@@ -770,13 +791,13 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_step(Le
 // First two Chebyshev steps from a zero guess in one sweep: x1 = c2_0 Dinv b is evaluated at the
 // stencil points on the fly (d_1 = x1), then the second step is applied.
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_pre2(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_cheb_pre2(Lev L, int Kp, const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout,
                             ChebStepT<T> cs0, ChebStepT<T> cs1, const T* __restrict__ dsh) {
     pdl_wait();
     constexpr int W = VecT<T>::W;
     const int off = threadIdx.x * W;
     LoadCheb0<T, DIM, VAR> ld;
-    ld.L = L;
+    ld.dg = reinterpret_cast<const T*>(L.dg);
     ld.b = b;
     for (int v = 0; v < W; ++v) { ld.c2[v] = (T)cs0.c2[off + v]; ld.d[v] = (T)dsh[off + v]; }
     sw_cheb_step<T, DIM, VAR>(L, Kp, ld, nullptr, true, b, xout, dout, cs1, dsh, nullptr, blockIdx.x, gridDim.x);
@@ -784,7 +805,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cheb_pre2(Le
 
 // First post-smoothing step with the coarse-grid correction added on the fly: xin = x + P ec.
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_post_prolong(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ ec,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_post_prolong(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ ec,
                                const T* __restrict__ b, T* __restrict__ xout, T* __restrict__ dout, ChebStepT<T> cs,
                                const T* __restrict__ dsh, Red red) {
     pdl_wait();
@@ -805,14 +826,14 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_prolong_add(
 }
 
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_restrict_res(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ b,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_restrict_res(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ b,
                                T* __restrict__ bc, const T* __restrict__ dsh) {
     pdl_wait();
     sw_restrict<T, DIM, VAR>(Lf, Lc, Kp, x, b, bc, dsh, blockIdx.x, gridDim.x);
 }
 
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_residual(Lev L, int Kp, const T* __restrict__ x,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_residual(Lev L, int Kp, const T* __restrict__ x,
                                                                          const T* __restrict__ b, T* __restrict__ r,
                                                                          const T* __restrict__ dsh) {
     pdl_wait();
@@ -827,7 +848,7 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_restrict_r(L
 }
 
 template <class T, int DIM, bool VAR>
-__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_apply_shifted(Lev L, int Kp, const T* __restrict__ x, T* __restrict__ y,
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_apply_shifted(Lev L, int Kp, const T* __restrict__ x, T* __restrict__ y,
                                 const T* __restrict__ dsh) {
     pdl_wait();
     constexpr int W = VecT<T>::W;
@@ -1117,8 +1138,9 @@ inline size_t shm(const Launch& g, int W) { return (size_t)g.C * g.PPB * W * siz
     } while (0)
 
 template <class T>
-void Ops<T>::broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s) {
-    launch_pdl(k_broadcast<T>, dim3(g.blocks), blk(g), 0, s, f, (int)N, g.Kp, K, r, x, p);
+void Ops<T>::broadcast(const Launch& g, const double* f, long long N, int K, T* r, T* x, T* p, cudaStream_t s,
+                       const double* const* fp) {
+    launch_pdl(k_broadcast<T>, dim3(g.blocks), blk(g), 0, s, f, fp, (int)N, g.Kp, K, r, x, p);
 }
 
 template <class T>

@@ -188,6 +188,16 @@ struct bura_plan {
     std::vector<void*> allocs;
     size_t dbytes = 0;           // sum of the allocations
     cudaEvent_t done = nullptr;  // recorded after the last kernel of every solve (bura_retarget waits on it)
+    // device-driven solve: the whole FP64 or mixed/FP64-refinement solve as one graph (controller kernels
+    // take the host's decisions); its outcome is copied to the pinned mirror hstate at the end of the solve
+    OuterCfg* ocfg = nullptr;
+    OuterState* ostate = nullptr;
+    OuterState* hstate = nullptr;
+    cudaGraph_t sgraph = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    long long s_fixed = 0, s_outer = 0, s_body = 0;  // launches: once, per refinement step, per PCG iteration
+    bool pending = false;        // a device-driven solve's outcome has not been read into st yet
+    int last_status = BURA_OK;   // status of the last solve whose outcome was read
     bura_stats st{};
     Tracer tr;
     cudaStream_t cap = nullptr;  // private stream used only to capture the PCG loop graphs
@@ -1523,7 +1533,251 @@ int upload_outer(bura_plan* p) {
     std::memset(&so, 0, sizeof(so));
     for (int j = 0; j < p->K; ++j) so.dsh[j] = p->d[j];
     CK(cudaMemcpy(p->scal_outer, &so, sizeof(Scal), cudaMemcpyHostToDevice));
+    if (p->ocfg) {
+        OuterCfg oc;
+        std::memset(&oc, 0, sizeof(oc));
+        for (int j = 0; j < p->K; ++j) {
+            oc.c[j] = p->c[j];
+            oc.d[j] = p->d[j];
+        }
+        oc.lambda_lo = p->lambda_lo;
+        oc.inner_rtol = p->opt.inner_rtol;
+        oc.wait_cycles = p->wait_cycles;
+        oc.K = p->K;
+        oc.max_outer = p->opt.max_outer;
+        oc.max_iters = p->opt.max_iters;
+        CK(cudaMemcpy(p->ocfg, &oc, sizeof(oc), cudaMemcpyHostToDevice));
+    }
     return BURA_OK;
+}
+
+// The device-driven solve applies to the FP64 path and to the mixed path with FP64 refinement, outside
+// per-kernel profiling (which times launches one by one).
+bool device_driven(const bura_plan* p) {
+    return !p->tr.on && (p->opt.precision == BURA_PREC_FP64 || p->opt.refine == BURA_REFINE_FP64);
+}
+
+// Add a WHILE node after the current capture dependencies of stream s, with a new condition handle of
+// the graph being captured (reset to `dflt` at every launch); capture continues after the node.
+int capture_while(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle* h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !g) return BURA_ECUDA;
+    CK(cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault));
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = *h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return BURA_OK;
+}
+
+// A condition handle of the graph that stream s is capturing into (to pass to a kernel before the node
+// that uses it is added).
+int capture_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive || !g) return BURA_ECUDA;
+    CK(cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault));
+    return BURA_OK;
+}
+
+// The WHILE node of an existing handle (created before its setter kernel was captured).
+int capture_while_h(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive || !g) return BURA_ECUDA;
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return BURA_OK;
+}
+
+// The device-driven solve is captured level by level: the top level into the graph that a stream is
+// capturing into, each WHILE body afterwards into its own body graph.
+struct BodyTask {
+    bura_plan* p;
+    cudaGraph_t body;
+    int kind;                          // 0: one PCG iteration; 1: one refinement step of the mixed path
+    cudaGraphConditionalHandle cond;   // the WHILE condition of this body
+};
+
+// Top level of one solve of plan p, captured on s (which is capturing): the FP64 path is ||f||, the
+// controller, WHILE(PCG), the outcome; the mixed path is zero v, ||f||, the controller, WHILE(refinement
+// step).  The right-hand side is read through the plan's solve record.  Bodies are queued in tasks.
+int capture_solve_top(bura_plan* p, cudaStream_t s, std::vector<BodyTask>& tasks) {
+    const long long N = p->hl[0].N;
+    const double* const* fpp =
+        reinterpret_cast<const double* const*>(reinterpret_cast<const char*>(p->ostate) + offsetof(OuterState, f));
+    Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
+    cudaGraphConditionalHandle h = 0;
+    cudaGraph_t body = nullptr;
+    if (p->opt.precision == BURA_PREC_FP64) {
+        Work<double>& w = p->w64;
+        Ops<double>::broadcast(w.g[0], nullptr, N, p->K, w.r, w.x, w.pa, s, fpp);
+        launch_norm2(N, nullptr, store, p->nsm, s, fpp);
+        CA(capture_handle(s, 0u, &h));
+        launch_outer_begin(p->ocfg, p->ostate, p->red_out, w.scal, p->scale, p->invscale, 0ull, (unsigned long long)h, 1, s);
+        CA(capture_while_h(s, h, &body));
+        launch_outer_end_fp64(p->ocfg, p->ostate, w.scal, s);
+        p->s_fixed += 4;
+        tasks.push_back({p, body, 0, h});
+    } else {
+        Work<float>& w = p->w32;
+        CK(cudaMemsetAsync(p->v64, 0, (size_t)N * p->w64.g[0].Kp * sizeof(double), s));
+        launch_norm2(N, nullptr, store, p->nsm, s, fpp);
+        CA(capture_handle(s, 0u, &h));
+        launch_outer_begin(p->ocfg, p->ostate, p->red_out, w.scal, p->scale, p->invscale, (unsigned long long)h, 0ull, 0, s);
+        CA(capture_while_h(s, h, &body));
+        p->s_fixed += 2;
+        tasks.push_back({p, body, 1, h});
+    }
+    CK(cudaGetLastError());
+    return BURA_OK;
+}
+
+// Capture one queued body (and queue the bodies it contains) on the plan's private capture stream.
+int capture_body(const BodyTask& t, std::vector<BodyTask>& tasks) {
+    bura_plan* p = t.p;
+    cudaStream_t s = p->cap;
+    const long long N = p->hl[0].N;
+    CK(cudaStreamBeginCaptureToGraph(s, t.body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = BURA_OK;
+    const long long b0 = p->tr.launches;
+    if (t.kind == 0) {
+        rc = p->opt.precision == BURA_PREC_FP64 ? pcg_body<double>(p, p->w64, (unsigned long long)t.cond, s)
+                                                : pcg_body<float>(p, p->w32, (unsigned long long)t.cond, s);
+        p->s_body = p->tr.launches - b0;
+    } else {
+        // one refinement step: the inner right-hand side (arming the inner loop), WHILE(PCG), the correction,
+        // the FP64 residual and the controller, which clears the outer condition when the solve is decided
+        Work<float>& w = p->w32;
+        const Launch& g64 = p->w64.g[0];
+        Red store{p->partial, p->tickets, p->scal_outer, p->red_out, RED_STORE, 0};
+        const double* const* fpp =
+            reinterpret_cast<const double* const*>(reinterpret_cast<const char*>(p->ostate) + offsetof(OuterState, f));
+        cudaGraphConditionalHandle hin = 0;
+        cudaGraph_t ibody = nullptr;
+        rc = capture_handle(s, 1u, &hin);
+        if (rc == BURA_OK) {
+            launch_cast_outer(g64, w.g[0], N, p->K, p->ostate, p->r64, p->invscale, w.r, w.x, w.pa,
+                              (unsigned long long)hin, s);
+            rc = capture_while_h(s, hin, &ibody);
+        }
+        if (rc == BURA_OK) {
+            launch_correct64(g64, w.g[0], N, p->K, p->v64, w.x, p->scale, s);
+            launch_residual64(g64, p->w64.L[0], p->dim, p->var, nullptr, p->v64, p->r64, store, s, fpp);
+            launch_outer_next(p->ocfg, p->ostate, p->red_out, w.scal, p->scale, p->invscale, (unsigned long long)t.cond,
+                              s);
+            p->s_outer += 4;
+            tasks.push_back({p, ibody, 0, hin});
+        }
+    }
+    cudaGraph_t done = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &done);
+    if (rc == BURA_OK && e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    return rc;
+}
+
+// Capture every queued body (depth first); profiling is off while capturing and launches are not counted.
+int capture_bodies(std::vector<BodyTask>& tasks) {
+    while (!tasks.empty()) {
+        const BodyTask t = tasks.back();
+        tasks.pop_back();
+        const bool was_on = t.p->tr.on;
+        const long long before = t.p->tr.launches;
+        t.p->tr.on = false;
+        const int rc = capture_body(t, tasks);
+        t.p->tr.on = was_on;
+        t.p->tr.launches = before;
+        if (rc != BURA_OK) return rc;
+    }
+    return BURA_OK;
+}
+
+// Build and instantiate the plan's device-driven solve graph once (capture under the exclusive guard).
+int build_solve_graph(bura_plan* p) {
+    if (p->sexec) return BURA_OK;
+    std::unique_lock<std::shared_mutex> lock(g_capture_guard);
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    p->s_fixed = p->s_outer = p->s_body = 0;
+    int rc = BURA_OK;
+    std::vector<BodyTask> tasks;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(p->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    if (rc == BURA_OK) {
+        const bool was_on = p->tr.on;
+        const long long before = p->tr.launches;
+        p->tr.on = false;
+        rc = capture_solve_top(p, p->cap, tasks);
+        p->tr.on = was_on;
+        p->tr.launches = before;
+        cudaGraph_t done = nullptr;
+        e = cudaStreamEndCapture(p->cap, &done);
+        if (rc == BURA_OK && e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    }
+    if (rc == BURA_OK) rc = capture_bodies(tasks);
+    cudaGraphExec_t ex = nullptr;
+    if (rc == BURA_OK) {
+        e = cudaGraphInstantiate(&ex, g, 0);
+        if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    }
+    if (rc != BURA_OK) {
+        cudaGetLastError();  // a failed capture's partial graph is left allocated (see build_graph)
+        return rc;
+    }
+    p->sgraph = g;
+    p->sexec = ex;
+    return BURA_OK;
+}
+
+// Enqueue the device-driven solve of f on s (no host synchronisation); the outcome is copied to the
+// pinned mirror after the output stage by the caller.
+int solve_device(bura_plan* p, const double* f, double tol, cudaStream_t s) {
+    int rc = build_solve_graph(p);
+    for (int attempt = 1; rc == BURA_ECUDA && attempt < 3; ++attempt) rc = build_solve_graph(p);
+    CA(rc);
+    launch_solve_params(p->ostate, f, tol, s);
+    CK(cudaGetLastError());
+    CK(cudaGraphLaunch(p->sexec, s));
+    return BURA_OK;
+}
+
+// The outcome of the last device-driven solve (waits for it): statistics and its status.
+int read_outcome(bura_plan* p) {
+    CK(cudaEventSynchronize(p->done));
+    if (!p->pending) return p->last_status;
+    p->pending = false;
+    const OuterState& o = *p->hstate;
+    p->st.iters = o.total_it;
+    p->st.outer = o.outer;
+    for (int j = 0; j <= p->k; ++j) p->st.shift_iters[j] = o.siters[j];
+    double rr[KMAXP] = {0};
+    for (int j = 0; j < p->K; ++j) rr[j] = o.rr[j];
+    finish_stats(p, rr, o.fnorm2);
+    p->st.launches = 2 + p->s_fixed + (long long)o.outer * p->s_outer + (long long)o.total_it * p->s_body;
+    p->last_status = o.status;
+    return o.status;
 }
 
 // Where the solutions are: FP64 path w64.x, mixed path with FP64 refinement v64 (both Kp64 layout),
@@ -1544,8 +1798,11 @@ int destroy_plan(bura_plan* p) {
     if (p->w64.graph) cudaGraphDestroy(p->w64.graph);
     if (p->w32.exec) cudaGraphExecDestroy(p->w32.exec);
     if (p->w32.graph) cudaGraphDestroy(p->w32.graph);
+    if (p->sexec) cudaGraphExecDestroy(p->sexec);
+    if (p->sgraph) cudaGraphDestroy(p->sgraph);
     if (p->cap) cudaStreamDestroy(p->cap);
     for (void* q : p->allocs) cudaFree(q);
+    if (p->hstate) cudaFreeHost(p->hstate);
     if (p->hscal) cudaFreeHost(p->hscal);
     if (p->hbuf) cudaFreeHost(p->hbuf);
     delete p;
@@ -1660,6 +1917,11 @@ int setup_device(bura_plan* p, long long N, bura_plan** out) {
     if (o.precision == BURA_PREC_MIXED && o.refine == BURA_REFINE_DF && (rc = build_df(p)) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->scal_outer, sizeof(Scal))) != BURA_OK) return fail(rc);
     if ((rc = dalloc(p, &p->cdev, KMAXP * sizeof(double))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->ocfg, sizeof(OuterCfg))) != BURA_OK) return fail(rc);
+    if ((rc = dalloc(p, &p->ostate, sizeof(OuterState))) != BURA_OK) return fail(rc);
+    if (cudaMemset(p->ostate, 0, sizeof(OuterState)) != cudaSuccess) return fail(BURA_ECUDA);
+    if (cudaMallocHost(&p->hstate, sizeof(OuterState)) != cudaSuccess) { p->hstate = nullptr; return fail(BURA_ENOMEM); }
+    std::memset(p->hstate, 0, sizeof(OuterState));
     if ((rc = upload_outer(p)) != BURA_OK) return fail(rc);
     if (cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
         p->done = nullptr;
@@ -1933,8 +2195,28 @@ int bura_setup_shifts(const bura_grid* grid, const double* const* faces, int nsy
 
 namespace {
 
+// The output stage of the device-driven solve and its outcome copy: u = sum_j c_j v_j (or the systems)
+// after the solve graph, then the solve record into the pinned mirror, then the plan's event.
+int enqueue_device_solve(bura_plan* p, const double* f, double* u, double* V, double tol, cudaStream_t s, int accumulate) {
+    if (!(tol > 0)) return BURA_EINVAL;
+    CK(cudaSetDevice(p->dev));
+    CA(solve_device(p, f, tol, s));
+    const long long N = p->hl[0].N;
+    if (V) launch_gather_systems(N, p->w64.Kp, p->K, solution_vectors(p), V, s);
+    else launch_weighted_sum(N, p->w64.Kp, p->K, solution_vectors(p), p->cdev, u, accumulate, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(p->hstate, p->ostate, sizeof(OuterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(p->done, s));
+    p->pending = true;
+    return BURA_OK;
+}
+
 // The solve and the output sum u = sum_j c_j v_j (accumulate = 1: u += ...), stream-ordered on s.
 int solve_into(bura_plan* p, const double* f, double* u, double tol, cudaStream_t s, int accumulate) {
+    if (device_driven(p)) {
+        CA(enqueue_device_solve(p, f, u, nullptr, tol, s, accumulate));
+        return read_outcome(p);
+    }
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     const double N = (double)p->hl[0].N;
@@ -1972,6 +2254,24 @@ int bura_solve(bura_plan* p, const double* f, double* u, double tol, void* strea
     return solve_into(p, f, u, tol, reinterpret_cast<cudaStream_t>(stream), 0);
 }
 
+int bura_solve_async(bura_plan* p, const double* f, double* u, double tol, void* stream) {
+    if (!p || !f || !u) return BURA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!device_driven(p)) {  // host-driven paths (double-float refinement, profiling) finish in the call
+        const int rc = solve_into(p, f, u, tol, s, 0);
+        p->st.launches = p->tr.launches;
+        return rc == BURA_ENOCONV ? BURA_OK : rc;
+    }
+    return enqueue_device_solve(p, f, u, nullptr, tol, s, 0);
+}
+
+int bura_solve_wait(bura_plan* p) {
+    if (!p) return BURA_EINVAL;
+    if (!p->pending) return p->last_status;
+    p->last_status = read_outcome(p);
+    return p->last_status;
+}
+
 int bura_solve_sum(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream) {
     if (!plans || n < 1 || !f || !u || !(tol > 0)) return BURA_EINVAL;
     for (int i = 0; i < n; ++i)
@@ -1988,8 +2288,11 @@ int bura_solve_sum(bura_plan* const* plans, int n, const double* f, double* u, d
 
 int bura_set_tma_wait_cycles(bura_plan* p, long long cycles) {
     if (!p || cycles < 0) return BURA_EINVAL;
-    p->wait_cycles = cycles;  // read by the next solve's CG state records
-    return BURA_OK;
+    p->wait_cycles = cycles;  // read by the next solve's CG state records (host-driven) or controller (captured)
+    std::shared_lock<std::shared_mutex> guard(g_capture_guard);
+    CK(cudaSetDevice(p->dev));
+    CK(cudaEventSynchronize(p->done));
+    return upload_outer(p);
 }
 
 int bura_solve_chain(bura_plan* const* plans, int n, const double* f, double* u, double tol, void* stream) {
@@ -2028,6 +2331,10 @@ int bura_solve_host(bura_plan* p, const double* f, double* u, double tol, void* 
 int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, void* stream) {
     if (!p || !f || !V) return BURA_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (device_driven(p)) {
+        CA(enqueue_device_solve(p, f, nullptr, V, tol, s, 0));
+        return read_outcome(p);
+    }
     int rc = solve_core(p, f, tol, s);
     if (rc != BURA_OK && rc != BURA_ENOCONV) return rc;
     traced(p, K_GATHER, false, true, 2.0 * p->hl[0].N * p->K * 8.0, s, [&] {
@@ -2044,6 +2351,145 @@ int bura_solve_systems(bura_plan* p, const double* f, double* V, double tol, voi
     return rc;
 }
 
+}  // extern "C"
+
+struct bura_batch {
+    int dev = 0;
+    std::vector<bura_plan*> plans;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> streams;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+};
+
+namespace {
+
+void free_batch(bura_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    delete b;
+}
+
+// Capture every problem of the batch into one graph: branch i % S of S parallel branches holds problem
+// i's whole device-driven solve (its solve record, ||f||, controller, WHILE loops, output sum and outcome
+// copy), so one launch of the graph solves them all, S at a time.
+int build_batch(bura_batch* b, const double* const* f, double* const* u, double tol, int S) {
+    std::unique_lock<std::shared_mutex> lock(g_capture_guard);
+    const int n = (int)b->plans.size();
+    b->streams.assign(S, nullptr);
+    for (int i = 0; i < S; ++i) CK(cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    b->joins.assign(S, nullptr);
+    for (int i = 0; i < S; ++i) CK(cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming));
+    CK(cudaGraphCreate(&b->graph, 0));
+    cudaStream_t s0 = b->streams[0];
+    std::vector<BodyTask> tasks;
+    for (bura_plan* p : b->plans) p->s_fixed = p->s_outer = p->s_body = 0;
+    CK(cudaStreamBeginCaptureToGraph(s0, b->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = BURA_OK;
+    cudaError_t e = cudaEventRecord(b->fork, s0);
+    for (int i = 1; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    for (int i = 0; i < n && rc == BURA_OK; ++i) {
+        bura_plan* p = b->plans[i];
+        cudaStream_t s = b->streams[i % S];
+        const bool was_on = p->tr.on;
+        const long long before = p->tr.launches;
+        p->tr.on = false;
+        launch_solve_params(p->ostate, f[i], tol, s);
+        rc = capture_solve_top(p, s, tasks);
+        p->tr.on = was_on;
+        p->tr.launches = before;
+        if (rc != BURA_OK) break;
+        launch_weighted_sum(p->hl[0].N, p->w64.Kp, p->K, solution_vectors(p), p->cdev, u[i], 0, s);
+        e = cudaMemcpyAsync(p->hstate, p->ostate, sizeof(OuterState), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    }
+    for (int i = 1; i < S && rc == BURA_OK; ++i) {
+        e = cudaEventRecord(b->joins[i], b->streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, b->joins[i], 0);
+        if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    }
+    cudaGraph_t done = nullptr;
+    e = cudaStreamEndCapture(s0, &done);
+    if (rc == BURA_OK && e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+    if (rc == BURA_OK) rc = capture_bodies(tasks);
+    if (rc == BURA_OK) {
+        e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; b->exec = nullptr; }
+    }
+    if (rc != BURA_OK) {
+        cudaGetLastError();
+        b->graph = nullptr;  // a failed capture's partial graph is left allocated (see build_graph)
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bura_batch_create(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
+                      int branches, bura_batch** out) {
+    if (!out) return BURA_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !plans || !f || !u || !(tol > 0) || branches < 0) return BURA_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || !f[i] || !u[i]) return BURA_EINVAL;
+        if (!device_driven(plans[i]) || plans[i]->dev != plans[0]->dev) return BURA_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return BURA_EINVAL;
+    }
+    bura_batch* b = new (std::nothrow) bura_batch();
+    if (!b) return BURA_ENOMEM;
+    b->dev = plans[0]->dev;
+    b->plans.assign(plans, plans + n);
+    cudaError_t e = cudaSetDevice(b->dev);
+    if (e != cudaSuccess) { g_last = e; delete b; return BURA_ECUDA; }
+    const int S = std::max(1, std::min(branches > 0 ? branches : 64, n));
+    const int rc = build_batch(b, f, u, tol, S);
+    if (rc != BURA_OK) { free_batch(b); return rc; }
+    *out = b;
+    return BURA_OK;
+}
+
+int bura_batch_run(bura_batch* b, void* stream) {
+    if (!b) return BURA_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(b->dev));
+    CK(cudaGraphLaunch(b->exec, s));
+    for (bura_plan* p : b->plans) {
+        CK(cudaEventRecord(p->done, s));
+        p->pending = true;
+    }
+    return BURA_OK;
+}
+
+int bura_batch_wait(bura_batch* b, int* status) {
+    if (!b) return BURA_EINVAL;
+    int rc = BURA_OK;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        const int st = read_outcome(b->plans[i]);
+        if (status) status[i] = st;
+        if (st != BURA_OK && (rc == BURA_OK || rc == BURA_ENOCONV)) rc = st;
+    }
+    return rc;
+}
+
+int bura_batch_destroy(bura_batch* b) {
+    if (!b) return BURA_OK;
+    std::shared_lock<std::shared_mutex> guard(g_capture_guard);
+    cudaSetDevice(b->dev);
+    for (bura_plan* p : b->plans) cudaEventSynchronize(p->done);
+    free_batch(b);
+    return BURA_OK;
+}
+
 int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
                      int nworkers, int* status) {
     if (n < 0 || nworkers < 0 || (n > 0 && (!plans || !f || !u))) return BURA_EINVAL;
@@ -2053,6 +2499,27 @@ int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* co
             if (plans[j] == plans[i]) return BURA_EINVAL;  // a plan's buffers serve one solve at a time
     }
     if (n == 0) return BURA_OK;
+    bool graphable = tol > 0;
+    for (int i = 0; i < n; ++i) graphable = graphable && device_driven(plans[i]) && plans[i]->dev == plans[0]->dev;
+    if (graphable) {  // one graph: every problem a branch of device-driven solves
+        bura_batch* b = nullptr;
+        int rc = bura_batch_create(plans, f, u, n, tol, nworkers, &b);
+        if (rc == BURA_OK) {
+            cudaStream_t s = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+            if (e == cudaSuccess)
+                for (bura_plan* p : b->plans) {
+                    cudaEventRecord(p->done, s);
+                    p->pending = true;
+                }
+            if (e != cudaSuccess) { g_last = e; rc = BURA_ECUDA; }
+            else rc = bura_batch_wait(b, status);
+            if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+            bura_batch_destroy(b);
+        }
+        return rc;
+    }
     const int nw = std::max(1, std::min(nworkers > 0 ? nworkers : 16, n));
     std::vector<int> st(n, BURA_OK);
     std::atomic<int> next(0);
@@ -2129,8 +2596,10 @@ int bura_get_rational(const bura_plan* p, double* c, double* d, double* E) {
     return BURA_OK;
 }
 
-int bura_get_stats(const bura_plan* p, bura_stats* st) {
-    if (!p || !st) return BURA_EINVAL;
+int bura_get_stats(const bura_plan* cp, bura_stats* st) {
+    if (!cp || !st) return BURA_EINVAL;
+    bura_plan* p = const_cast<bura_plan*>(cp);  // reading a finished solve's outcome updates the cached stats
+    if (p->pending) read_outcome(p);
     *st = p->st;
     st->device_bytes = p->dbytes;
     return BURA_OK;
