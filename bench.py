@@ -47,6 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--profile-steps", type=int, default=6, help="solves timed kernel by kernel for the roofline")
     ap.add_argument("--skip-3d", action="store_true", help="skip the 3D variable-coefficient workload")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched 256-problem workload")
+    ap.add_argument("--skip-csr", action="store_true", help="skip the sparse (P1 finite-element) workload")
     ap.add_argument("--skip-serve", action="store_true", help="skip the serving workload (Poisson arrivals)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s of the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured arrival window of the serving workload")
@@ -354,47 +355,141 @@ def bench_3d(bura, W, np, torch, dev, stream, flush, rank, ws, steps, cpu_leg):
     return out
 
 
+WORKLOAD_CSR = ("sparse: P1 finite-element stiffness matrix on the unit cube (63^3 interior vertices, six tetrahedra "
+                "per cube), a = 1e-3 on the half x < 1/2 and 1 elsewhere (the paper's heterogeneous 3-D test), assembled "
+                "as CSR; alpha=0.5, k=7, f~N(0,1) seed 13, FP32 multi-shift CG with a degree-8 Chebyshev-Jacobi "
+                "polynomial preconditioner inside FP64 refinement, each system to ||r_j|| <= 1e-6 ||f||")
+
+
+def bench_csr(bura, W, np, torch, dev, stream, flush, rank, steps):
+    """Solves/s of the sparse (CSR) workload and the roofline of its dominant kernel."""
+    n = 63
+    A = W.p1_matrix(n, W.half_cube_field(1e-3)).tocsr()
+    N = A.shape[0]
+    f = torch.from_numpy(W.rhs_normal((N,), 13 + 1000 * rank)).to(dev)
+    u = torch.zeros_like(f)
+    t0 = time.perf_counter()
+    plan = bura.bura_setup_csr(A.indptr, A.indices, A.data, 0.5, 7)
+    setup_s = time.perf_counter() - t0
+    try:
+        bura.bura_solve(plan, f, u, TOL, stream)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = bura.bura_solve(plan, f, u, TOL, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rc != bura.BURA_OK:
+                raise RuntimeError("sparse solve did not converge")
+            times.append(e0.elapsed_time(e1))
+        st = bura.bura_get_stats(plan)
+        bura.bura_set_profiling(plan, 1)
+        flush.zero_()
+        bura.bura_solve(plan, f, u, TOL, stream)
+        torch.cuda.synchronize()
+        prof = bura.bura_get_profile(plan)
+        bura.bura_set_profiling(plan, 0)
+    finally:
+        bura.bura_destroy(plan)
+    ms = sum(times) / len(times)
+    return {"workload": WORKLOAD_CSR, "rows": N, "nnz": int(A.nnz), "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+            "steps": steps, "Gunknown_shifts_per_s": N * 8 / (ms / 1e3) / 1e9, "inner_iters": st["iters"],
+            "outer": st["outer"], "setup_s": setup_s, "roofline": roofline_from_profile(prof, 1)}
+
+
 WORKLOAD_BATCH = ("batched: 256 right-hand sides over 2D 5-point grids drawn uniformly from {63^2,127^2,255^2,511^2}, "
                   "alpha ~ U(0.1,0.9), k ~ U{5..9}, f ~ U[-1,1] (seed 4), FP32 MG-PCG inner + FP64 refinement, "
-                  "tol 1e-6; bura_solve_batch, 32 worker streams")
+                  "tol 1e-6; all 256 solves captured as one CUDA graph (bura_batch, 64 parallel branches), options "
+                  "per (grid, k) class from the library's autotuner")
 
 
-def bench_batch(bura, W, np, torch, dev, rank, reps):
-    """Solves/s of the batched workload: bura_solve_batch over 256 resident plans (setup timed apart),
-    against the same 256 problems solved one after another on one stream."""
+def _batch_problems(W, np, rank):
     rng = np.random.default_rng(4 + 1000 * rank)
     sizes = [63, 127, 255, 511]
-    plans, fs, us, unk = [], [], [], 0
+    out = []
+    for i in range(256):
+        n = sizes[rng.integers(len(sizes))]
+        alpha = float(rng.uniform(0.1, 0.9))
+        k = int(rng.integers(5, 10))
+        out.append((n, alpha, k, W.rhs_uniform((n, n), 10000 + i)))
+    return out
+
+
+def _time_batch(bura, torch, plans, fs, us, reps, stream):
+    """Capture the batch once, then time `reps` launches (host wall clock around run + wait)."""
     t0 = time.perf_counter()
+    b = bura.BuraBatch(plans, fs, us, TOL, branches=64)
+    capture_s = time.perf_counter() - t0
     try:
-        for i in range(256):
-            n = sizes[rng.integers(len(sizes))]
-            alpha = float(rng.uniform(0.1, 0.9))
-            k = int(rng.integers(5, 10))
-            plans.append(bura.bura_setup((n, n), alpha, k))
-            fs.append(torch.from_numpy(W.rhs_uniform((n, n), 10000 + i)).to(dev))
-            us.append(torch.zeros_like(fs[-1]))
-            unk += n * n * (k + 1)
-        setup_s = time.perf_counter() - t0
-        bura.bura_solve_batch(plans, fs, us, TOL, 32)  # warm-up: captures every plan's PCG graph
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            st = bura.bura_solve_batch(plans, fs, us, TOL, 32)
-        torch.cuda.synchronize()
-        tb = (time.perf_counter() - t0) / reps
+        b.run(stream)
+        st = b.wait()
         if any(x != bura.BURA_OK for x in st):
             raise RuntimeError("batched solve did not converge")
         t0 = time.perf_counter()
-        bura.bura_solve_batch(plans, fs, us, TOL, 1)
+        for _ in range(reps):
+            b.run(stream)
+            b.wait()
+        tb = (time.perf_counter() - t0) / reps
+    finally:
+        b.close()
+    return tb, capture_s
+
+
+def bench_batch(bura, W, np, torch, dev, rank, reps):
+    """Solves/s of the batched workload: the 256 problems as one captured graph with tuned options, against
+    the same graph with the default options and the plain FP64 path solving the problems one at a time."""
+    from paper_1612_04846_gb300 import autotune
+    probs = _batch_problems(W, np, rank)
+    unk = sum(n * n * (k + 1) for n, _, k, _ in probs)
+    stream = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    table = autotune.tune(sorted({((n, n), k) for n, _, k, _ in probs}), alpha=0.5, tol=TOL, trials=3)
+    tune_s = time.perf_counter() - t0
+    fs = [torch.from_numpy(f).to(dev) for *_, f in probs]
+    us = [torch.zeros_like(f) for f in fs]
+    out = {"workload": WORKLOAD_BATCH, "reps": reps, "tune_s": tune_s,
+           "tuned": {k: {"smoother_degree": v["options"]["smoother_degree"], "smoother_ratio": v["options"]["smoother_ratio"],
+                         "sweeps": v["options"]["sweeps"], "ms": v["ms"]} for k, v in sorted(table.items())}}
+    for label, opts in (("tuned", lambda n, k: autotune.options_for(table, (n, n), k)),
+                        ("default", lambda n, k: bura.bura_default_options())):
+        plans = []
+        t0 = time.perf_counter()
+        try:
+            for n, alpha, k, _ in probs:
+                plans.append(bura.bura_setup((n, n), alpha, k, options=opts(n, k)))
+            setup_s = time.perf_counter() - t0
+            tb, cap_s = _time_batch(bura, torch, plans, fs, us, reps, stream)
+        finally:
+            for p in plans:
+                bura.bura_destroy(p)
+        out[label] = {"solves_per_s": 256 / tb, "ms_per_batch": 1e3 * tb, "Gunknown_shifts_per_s": unk / tb / 1e9,
+                      "setup_s": setup_s, "capture_s": cap_s}
+    # the plain FP64 path, one problem at a time on one stream (bura_solve waits for each)
+    plans = []
+    try:
+        for n, alpha, k, _ in probs:
+            o = bura.bura_default_options()
+            o.precision = bura.BURA_PREC_FP64
+            plans.append(bura.bura_setup((n, n), alpha, k, options=o))
+        for p, f, u in zip(plans[:8], fs, us):
+            bura.bura_solve(p, f, u, TOL, stream)
         torch.cuda.synchronize()
-        ts = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for p, f, u in zip(plans, fs, us):
+            bura.bura_solve(p, f, u, TOL, stream)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
     finally:
         for p in plans:
             bura.bura_destroy(p)
-    return {"workload": WORKLOAD_BATCH, "solves_per_s": 256 / tb, "ms_per_batch": 1e3 * tb, "reps": reps,
-            "Gunknown_shifts_per_s": unk / tb / 1e9, "one_stream_solves_per_s": 256 / ts, "setup_s": setup_s,
-            "timing": "host wall clock around the blocking bura_solve_batch call"}
+    out["fp64_one_at_a_time"] = {"solves_per_s": 256 / t64, "ms_per_batch": 1e3 * t64,
+                                 "timing": "host wall clock, bura_solve per problem on one stream, FP64 plans"}
+    out["solves_per_s"] = out["tuned"]["solves_per_s"]
+    out["timing"] = "host wall clock around bura_batch_run + bura_batch_wait (one graph launch per batch)"
+    return out
 
 
 SERVE_GRIDS = [(127, 127), (255, 255), (511, 511), (1023, 1023), (31, 31, 31), (63, 63, 63), (127, 127, 127)]
@@ -511,9 +606,42 @@ def bench_serve(bura, W, np, torch, rate, seconds, warm):
         st = srv.stats()
     finally:
         srv.close()
+    fp64 = serve_fp64_one_at_a_time(bura, np, data, upool, 300)
     return {"workload": serve_workload(rate, seconds, warm), "at_offered_rate": first,
-            "at_70pct_of_sustained": second, "server": st,
+            "at_70pct_of_sustained": second, "server": st, "fp64_one_at_a_time": fp64,
             "timing": "host wall clock; latency = scheduled arrival -> u in host memory"}
+
+
+def serve_fp64_one_at_a_time(bura, np, data, upool, count):
+    """The same request mix (the first `count` arrivals of the seed-5 schedule) served the plain way: one
+    request at a time, FP64 plans (one resident plan per class, moved to each request's alpha), host
+    buffers copied in and out (bura_solve_host).  Host wall clock; plan setup excluded."""
+    rng = np.random.default_rng(5)
+    reqs = []
+    while len(reqs) < count:
+        rng.exponential(1.0)
+        gi = int(rng.integers(len(SERVE_GRIDS)))
+        reqs.append((gi, bool(rng.integers(2)), float(rng.uniform(0.1, 0.9)), int(rng.integers(5, 10)),
+                     int(rng.integers(2))))
+    plans = {}
+    try:
+        for gi, var, _, k, _ in reqs:
+            if (gi, var, k) not in plans:
+                o = bura.bura_default_options()
+                o.precision = bura.BURA_PREC_FP64
+                plans[(gi, var, k)] = bura.bura_setup(SERVE_GRIDS[gi], 0.5, k, faces=data[gi][1] if var else None,
+                                                      options=o)
+        t0 = time.perf_counter()
+        for gi, var, alpha, k, fi in reqs:
+            p = plans[(gi, var, k)]
+            bura.bura_retarget(p, alpha)
+            bura.bura_solve_host(p, data[gi][0][fi], upool[gi][0], TOL)
+        secs = time.perf_counter() - t0
+    finally:
+        for p in plans.values():
+            bura.bura_destroy(p)
+    return {"requests": count, "solves_per_s": count / secs, "mean_ms": 1e3 * secs / count,
+            "timing": "host wall clock, one request after another (retarget + bura_solve_host), FP64 plans"}
 
 
 def main(argv=None):
@@ -692,6 +820,9 @@ def main(argv=None):
     if not args.skip_3d:
         w3 = bench_3d(bura, W, np, torch, dev, stream, flush, rank, ws, max(3, args.steps // 20),
                       rank == 0 and ws == 1 and not args.no_cpu_baseline)
+    wc = None
+    if not args.skip_csr:
+        wc = bench_csr(bura, W, np, torch, dev, stream, flush, rank, max(3, args.steps // 20))
     wb = None
     if not args.skip_batch:
         wb = bench_batch(bura, W, np, torch, dev, rank, 2)
@@ -712,7 +843,7 @@ def main(argv=None):
                 "fp64_path_solves_per_s": fp64_solves,
                 "df_refine_solves_per_s": df_solves,
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "batch_256_mixed_2d": wb,
+                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "csr_p1_63_halfcube_k7": wc, "batch_256_mixed_2d": wb,
                                                                "serve_poisson_mixed": wsv}}
         print(json.dumps(line), flush=True)
     if dist.is_initialized():

@@ -224,8 +224,8 @@ typedef struct {
  * The k+1 shifted systems run as one multi-shift CG on the GPU: the sparse product reads each entry's value
  * and column once for all systems (vectors interleaved by system, as on grids), and the preconditioner is a
  * Chebyshev polynomial in Dinv (A - d_j I) per system (degree opt->coarse_degree, 0 = 8, on the interval
- * [lambda_lo_j, Gershgorin bound of the scaled rows]; lambda_lo_j from lambda_min, else the upper bound /
- * opt->smoother_ratio, 0 = 30): geometric multigrid needs a grid.
+ * [hi_j / ratio, hi_j], hi_j the Gershgorin bound of the scaled rows, ratio = opt->smoother_ratio, 0 = 30):
+ * geometric multigrid needs a grid.  lambda_min enters the stopping rule only.
  * Stopping rule: with lambda_min > 0 that of bura_solve; with lambda_min = 0 every system stops at
  * ||f - (A - d_j I) v_j|| <= tol ||f|| (the relative residual criterion of the paper's PCG runs) and
  * bura_stats.err_bound is -1.  The arrays are copied (the caller keeps ownership); bura_solve* and
@@ -446,6 +446,20 @@ int bura_solve_batch(bura_plan* const* plans, const double* const* f, double* co
  *         different devices, tol <= 0), BURA_ENOMEM, BURA_ECUDA; bura_batch_wait as bura_solve_batch.
  */
 typedef struct bura_batch bura_batch;
+
+/*
+ * Autotuner of one problem class: sets up plans for the grid, coefficients, alpha and k with candidate
+ * option sets derived from *base (NULL: the defaults): smoother degree 2 or 3, the Chebyshev interval of
+ * the dimension or twice as wide, and on 2-D constant-coefficient grids in mixed precision the TMA-staged
+ * tiles or the grid-stride sweeps; times `trials` solves of each (CUDA events around the device-driven
+ * solve of a fixed pseudo-random right-hand side at tolerance tol, median) and writes the fastest option
+ * set to *best and its median to *best_ms (may be NULL).  A candidate that fails or misses tol is skipped.
+ * Allocates two N-vectors, a stream and the candidates' plans (freed before returning).  The paper has no
+ * counterpart: this chooses implementation parameters only, every candidate computes eq. (Rgeneral).
+ * Errors: BURA_EINVAL (bad arguments), BURA_ENOMEM, BURA_ENOCONV (no candidate converged).
+ */
+int bura_autotune(const bura_grid* grid, const double* const* faces, double alpha, int k, const bura_options* base,
+                  double tol, int trials, bura_options* best, double* best_ms);
 int bura_batch_create(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
                       int branches, bura_batch** out);
 int bura_batch_run(bura_batch* batch, void* stream);

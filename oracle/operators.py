@@ -22,7 +22,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["fd_matrix", "scaled_matrix", "constant_faces", "quadratic_form", "p1_matrix", "half_cube_field", "scaled_csr"]
+__all__ = ["fd_matrix", "scaled_matrix", "constant_faces", "quadratic_form", "scaled_csr"]
 
 
 def constant_faces(shape):
@@ -99,77 +99,6 @@ def quadratic_form(shape, faces, x):
         diff = np.diff(xp, axis=axis)  # n+1 faces along this axis
         total += float(np.sum(np.asarray(faces[fdir]) * diff * diff)) / h2
     return total
-
-
-# ---------------------------------------------------------------------- P1 finite elements (Sec. 5.4)
-def _kuhn_element_matrices():
-    """Stiffness matrices G G^T |T| of the six tetrahedra of the unit cube that share its main diagonal
-    (vertices 0, e_a, e_a + e_b, (1,1,1) for every ordering (a, b, c) of the axes), for a = 1 and h = 1.
-    G holds the gradients of the four barycentric functions: the rows of J^-1 and minus their sum."""
-    import itertools
-    mats, verts = [], []
-    for perm in itertools.permutations(range(3)):
-        v = np.zeros((4, 3))
-        for m in range(1, 4):
-            v[m] = v[m - 1]
-            v[m, perm[m - 1]] = 1.0
-        J = (v[1:] - v[0]).T  # columns: edge vectors from vertex 0, so x = v0 + J (l1, l2, l3)
-        Ginv = np.linalg.inv(J)  # row m-1: gradient of the barycentric function of vertex m
-        G = np.vstack([-Ginv.sum(axis=0), Ginv])
-        vol = abs(np.linalg.det(J)) / 6.0
-        mats.append(vol * G @ G.T)
-        verts.append(v.astype(np.int64))
-    return mats, verts
-
-
-def p1_matrix(n, field=None):
-    """Stiffness matrix (CSR) of continuous piecewise-linear finite elements for -div(a grad u) on the
-    unit cube with homogeneous Dirichlet data (the operator of the paper's 3-D tests, Sec. 5.4, with the
-    coefficient a = a(x) I piecewise constant).  Mesh: (n+1)^3 cubes of side h = 1/(n+1), each cut into
-    the six tetrahedra around its main diagonal; unknowns are the n^3 interior vertices, numbered
-    x fastest.  field: None (a = 1) or an array of shape (b, b, b) indexed [z, y, x] giving a on the b^3
-    equal blocks of the cube; a tetrahedron takes the value of the block holding its centroid.
-    With a = 1 this is h^3 times the 7-point finite-difference matrix (tested)."""
-    n = int(n)
-    h = 1.0 / (n + 1)
-    mats, verts = _kuhn_element_matrices()
-    c = np.arange(n + 1)
-    cz, cy, cx = np.meshgrid(c, c, c, indexing="ij")
-    cz, cy, cx = cz.ravel(), cy.ravel(), cx.ravel()
-    rows, cols, vals = [], [], []
-    for Ke, v in zip(mats, verts):
-        # grid coordinates (0..n+1) of the four vertices of this tetrahedron in every cube
-        px = cx[:, None] + v[None, :, 0]
-        py = cy[:, None] + v[None, :, 1]
-        pz = cz[:, None] + v[None, :, 2]
-        if field is None:
-            a = np.ones(cx.size)
-        else:
-            fld = np.asarray(field, dtype=np.float64)
-            b = fld.shape[0]
-            cen = (np.stack([px, py, pz], axis=-1).mean(axis=1)) * h  # centroids, (x, y, z)
-            blk = np.minimum((cen * b).astype(np.int64), b - 1)
-            a = fld[blk[:, 2], blk[:, 1], blk[:, 0]]
-        inside = (px >= 1) & (px <= n) & (py >= 1) & (py <= n) & (pz >= 1) & (pz <= n)
-        idx = ((pz - 1) * n + (py - 1)) * n + (px - 1)
-        for r in range(4):
-            for s in range(4):
-                m = inside[:, r] & inside[:, s]
-                rows.append(idx[m, r])
-                cols.append(idx[m, s])
-                vals.append(a[m] * Ke[r, s] * h)  # |T| = h^3 |T_1|, gradients scale by 1/h
-    N = n ** 3
-    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
-    A.sum_duplicates()
-    A.eliminate_zeros()
-    return A
-
-
-def half_cube_field(mu, b=2):
-    """Block field of the paper's heterogeneous 3-D test: a = mu on the half x < 1/2, a = 1 elsewhere."""
-    fld = np.ones((b, b, b))
-    fld[:, :, : b // 2] = float(mu)
-    return fld
 
 
 def scaled_csr(A):

@@ -125,6 +125,8 @@ def _lib():
         L.bura_batch_run.argtypes = [P, P]
         L.bura_batch_wait.argtypes = [P, C.POINTER(I)]
         L.bura_batch_destroy.argtypes = [P]
+        L.bura_autotune.argtypes = [C.POINTER(bura_grid), C.POINTER(dp), D, I, C.POINTER(bura_options), D, I,
+                                    C.POINTER(bura_options), dp]
         L.bura_solve_systems.argtypes = [P, P, P, D, P]
         L.bura_apply_shifted.argtypes = [P, P, P, P]
         L.bura_get_rational.argtypes = [P, dp, dp, dp]
@@ -160,7 +162,7 @@ def _lib():
                      "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts", "bura_solve_sum",
                      "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr", "bura_solve_async",
                      "bura_solve_wait", "bura_batch_create", "bura_batch_run", "bura_batch_wait", "bura_batch_destroy",
-                     "bura_server_create", "bura_server_submit",
+                     "bura_autotune", "bura_server_create", "bura_server_submit",
                      "bura_server_wait", "bura_server_get_stats", "bura_server_destroy"):
             getattr(L, name).restype = I
         _LIB = L
@@ -342,6 +344,19 @@ def bura_solve_batch(plans, fs, us, tol, nworkers=0):
     _check(_lib().bura_solve_batch(pa, fa, ua, int(n), float(tol), int(nworkers), st), "bura_solve_batch",
            allow=(BURA_ENOCONV,))
     return list(st)[:n]
+
+
+def bura_autotune(shape, alpha, k, tol=1e-6, trials=3, faces=None, base=None):
+    """(best bura_options, median ms) over the library's candidate option sets for this problem class."""
+    g = _grid_of(shape, faces)
+    keep = []
+    fptr = _faces_arg(faces, keep)
+    b = base if base is not None else bura_default_options()
+    best = bura_options()
+    ms = C.c_double()
+    _check(_lib().bura_autotune(C.byref(g), fptr, float(alpha), int(k), C.byref(b), float(tol), int(trials),
+                                C.byref(best), C.byref(ms)), "bura_autotune")
+    return best, ms.value
 
 
 class BuraBatch:
@@ -555,6 +570,6 @@ EXPORTED = ["bura_default_options", "bura_rational", "bura_setup", "bura_solve",
             "bura_last_cuda_error", "bura_solve_batch", "bura_retarget", "bura_solve_chain", "bura_setup_shifts",
             "bura_solve_sum", "bura_set_tma_wait_cycles", "bura_scale", "bura_quadrature_bp15", "bura_setup_csr",
             "bura_solve_async", "bura_solve_wait", "bura_batch_create", "bura_batch_run", "bura_batch_wait",
-            "bura_batch_destroy", "bura_server_default_options",
+            "bura_batch_destroy", "bura_autotune", "bura_server_default_options",
             "bura_server_create", "bura_server_submit", "bura_server_wait", "bura_server_get_stats",
             "bura_server_destroy"]

@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "../../include/bura.h"
+#include "guard.h"
 
 namespace {
 
@@ -93,6 +94,8 @@ int scratch_address(int dev, double** out) {
     if (dev < 0 || dev >= 256) return BURA_ECUDA;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
+        // the lookup may load the module on this device: not beside another thread's graph capture
+        std::shared_lock<std::shared_mutex> guard(bura::capture_guard());
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return BURA_ECUDA;
         g_addr[dev] = ptr;

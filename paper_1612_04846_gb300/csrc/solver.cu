@@ -15,8 +15,16 @@
 #include <vector>
 
 #include "../../include/bura.h"
+#include "guard.h"
 #include "kernels.cuh"
 #include "tma.cuh"
+
+namespace bura {
+std::shared_mutex& capture_guard() {
+    static std::shared_mutex m;
+    return m;
+}
+}  // namespace bura
 
 using namespace bura;
 
@@ -208,8 +216,9 @@ namespace {
 thread_local cudaError_t g_last = cudaSuccess;
 // Stream capture of a PCG graph is invalidated by a device-synchronising call of another thread (a
 // device-wide synchronisation, a free, a synchronous copy or memset).  The library's own such calls
-// (plan setup, retargeting, destruction) hold this guard shared; a capture holds it exclusively.
-std::shared_mutex g_capture_guard;  // per calling thread (batch workers run in parallel)
+// (plan setup, retargeting, destruction, the allocation-free entry point's first symbol lookup) hold
+// this guard shared; a capture holds it exclusively.
+std::shared_mutex& g_capture_guard = bura::capture_guard();
 #define CK(call)                                  \
     do {                                          \
         cudaError_t e_ = (call);                  \
@@ -412,8 +421,12 @@ void cheb_tables(const HostLevel& h, bool var, const std::vector<double>& d, int
             hi = 0.0;
             for (size_t i = 0; i < h.rowsum.size(); ++i) hi = std::max(hi, (h.rowsum[i] + mds) / (h.diag[i] + mds));
         }
+        // a sparse operator's polynomial preconditioner takes [hi / ratio, hi] even with a lambda_min bound:
+        // lambda_min / max(diag) underestimates the bottom of Dinv A by the spread of the diagonal (a
+        // coefficient jump), and the wide interval converges far more slowly (353 against 12 CG iterations
+        // on the P1 half-cube matrix with mu = 1e-3, 15^3)
         double lo;
-        if (coarse_solve && !(h.rowsum.size() && h.lmin <= 0)) lo = (h.lmin + mds) / (h.amax + mds);
+        if (coarse_solve && h.rowsum.empty()) lo = (h.lmin + mds) / (h.amax + mds);
         else lo = std::max(hi / ratio, mds / (h.amax + mds));
         lo = std::min(lo, hi * (1.0 - 1e-12));
         const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
@@ -2433,6 +2446,88 @@ int build_batch(bura_batch* b, const double* const* f, double* const* u, double 
 }  // namespace
 
 extern "C" {
+
+int bura_autotune(const bura_grid* grid, const double* const* faces, double alpha, int k, const bura_options* base,
+                  double tol, int trials, bura_options* best, double* best_ms) {
+    if (!grid || !best || !(alpha > 0 && alpha < 1) || k < 1 || k > BURA_MAX_K || !(tol > 0) || trials < 1)
+        return BURA_EINVAL;
+    long long N = 0;
+    CA(check_grid(grid, faces, &N));
+    bura_options b0;
+    bura_default_options(&b0);
+    if (base) b0 = *base;
+    CA(check_options(b0));
+    // candidates: smoother degree 2 or 3, the Chebyshev interval by dimension or twice as wide, and on 2-D
+    // constant-coefficient grids the TMA-staged tiles or the grid-stride sweeps
+    std::vector<bura_options> cand;
+    const double r0 = b0.smoother_ratio > 0 ? b0.smoother_ratio : (grid->dim == 3 ? 8.0 : 4.0);
+    const bool tiles = grid->dim == 2 && grid->coef_kind == BURA_COEF_CONSTANT && b0.precision == BURA_PREC_MIXED;
+    for (int deg = 2; deg <= 3; ++deg)
+        for (int wide = 0; wide <= 1; ++wide)
+            for (int sw = 0; sw <= (tiles ? 1 : 0); ++sw) {
+                bura_options o = b0;
+                o.smoother_degree = deg;
+                o.smoother_ratio = wide ? 2.0 * r0 : r0;
+                o.sweeps = sw ? BURA_SWEEP_GRID : BURA_SWEEP_AUTO;
+                cand.push_back(o);
+            }
+    // a fixed pseudo-random right-hand side in [-1, 1] (the timing does not depend on its values)
+    std::vector<double> fh((size_t)N);
+    unsigned long long x = 0x9e3779b97f4a7c15ull;
+    for (auto& v : fh) {
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        v = (double)(x >> 11) / 9007199254740992.0 * 2.0 - 1.0;
+    }
+    double* fd = nullptr;
+    double* ud = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (fd) cudaFree(fd);
+        if (ud) cudaFree(ud);
+        if (s) cudaStreamDestroy(s);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    {
+        std::shared_lock<std::shared_mutex> guard(g_capture_guard);
+        if (cudaMalloc(&fd, N * sizeof(double)) != cudaSuccess || cudaMalloc(&ud, N * sizeof(double)) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess ||
+            cudaMemcpy(fd, fh.data(), N * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cleanup();
+            return BURA_ENOMEM;
+        }
+    }
+    double bms = 1e300;
+    int found = 0;
+    for (const bura_options& o : cand) {
+        bura_plan* p = nullptr;
+        if (bura_setup(grid, faces, alpha, k, &o, &p) != BURA_OK) continue;
+        bool ok = bura_solve(p, fd, ud, tol, s) == BURA_OK;  // warm-up: captures the graphs
+        std::vector<float> t;
+        for (int i = 0; ok && i < trials; ++i) {
+            float ms = 0.f;
+            ok = cudaEventRecord(e0, s) == cudaSuccess && bura_solve_async(p, fd, ud, tol, s) == BURA_OK &&
+                 cudaEventRecord(e1, s) == cudaSuccess && bura_solve_wait(p) == BURA_OK &&
+                 cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            t.push_back(ms);
+        }
+        bura_destroy(p);
+        if (!ok) continue;
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (med < bms) {
+            bms = med;
+            *best = o;
+            found = 1;
+        }
+    }
+    cleanup();
+    if (!found) return BURA_ENOCONV;
+    if (best_ms) *best_ms = bms;
+    return BURA_OK;
+}
 
 int bura_batch_create(bura_plan* const* plans, const double* const* f, double* const* u, int n, double tol,
                       int branches, bura_batch** out) {

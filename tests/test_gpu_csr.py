@@ -51,7 +51,7 @@ def _matrix(kind):
     if kind == "fd2d":
         return operators.fd_matrix((31, 31)).tocsr()
     if kind == "p1_halfcube":
-        return operators.p1_matrix(15, operators.half_cube_field(1e-3)).tocsr()
+        return W.p1_matrix(15, W.half_cube_field(1e-3)).tocsr()
     return _random_spd(2000, 7)
 
 
@@ -138,7 +138,7 @@ def test_csr_p1_finite_elements_full_bound_at_63(lib):
     matrix for a = 1 and the quadratic form is monotone in a), and the oracle's sparse matrix checks the
     rigorous bound sum_j c_j ||r_j|| / (lambda_lo - d_j) <= tol ||f||."""
     n, mu, alpha, k, tol = 63, 1e-3, 0.5, 7, 1e-6
-    At = operators.p1_matrix(n, operators.half_cube_field(mu)).tocsr()
+    At = W.p1_matrix(n, W.half_cube_field(mu)).tocsr()
     As, lam = operators.scaled_csr(At)
     h = 1.0 / (n + 1)
     lmin = mu * h ** 3 * float(exact.eigenvalues((n, n, n)).min()) * exact.gershgorin((n, n, n))

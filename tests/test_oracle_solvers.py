@@ -139,7 +139,7 @@ def test_p1_constant_coefficient_is_the_7_point_matrix(n):
     """P1 finite elements on the tetrahedra around each cube's main diagonal (Sec. 5.4's element type):
     with a = 1 the stiffness matrix is h^3 times the 7-point finite-difference matrix."""
     h = 1.0 / (n + 1)
-    A = operators.p1_matrix(n)
+    A = W.p1_matrix(n)
     assert abs(A - h ** 3 * operators.fd_matrix((n, n, n))).max() < 1e-15
 
 
@@ -147,8 +147,8 @@ def test_p1_variable_coefficient_is_spd_and_monotone():
     """With a piecewise-constant a (the paper's half cube scaled by mu): symmetric, an M-matrix (off-diagonal
     entries <= 0, row sums >= 0), and its quadratic form lies between mu and 1 times the a = 1 form."""
     n, mu = 7, 1e-3
-    A = operators.p1_matrix(n, operators.half_cube_field(mu))
-    A1 = operators.p1_matrix(n)
+    A = W.p1_matrix(n, W.half_cube_field(mu))
+    A1 = W.p1_matrix(n)
     assert abs(A - A.T).max() == 0
     B = A.tocoo()
     assert np.all(B.data[B.row != B.col] <= 0)
