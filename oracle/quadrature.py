@@ -29,9 +29,10 @@ def bp15_counts(alpha, kprime):
     return m, M
 
 
-def bp15_shifts(alpha, kprime, Lam):
-    """Weights c_l and shifts d_l (l = -m .. M) of u_Q for the scaled operator A = Atilde / Lam."""
-    m, M = bp15_counts(alpha, kprime)
+def bp15_shifts(alpha, kprime, Lam, counts=None):
+    """Weights c_l and shifts d_l (l = -m .. M) of u_Q for the scaled operator A = Atilde / Lam; counts
+    (m, M) overrides the truncation of the printed formula (used to check the untruncated sum)."""
+    m, M = bp15_counts(alpha, kprime) if counts is None else counts
     pre = 2.0 * kprime * math.sin(math.pi * alpha) / math.pi
     c, d = [], []
     for l in range(-m, M + 1):

@@ -202,6 +202,11 @@ struct Ops {
                        const Red& red, cudaStream_t s);
     static void cg_update(const Launch& g, long long N, T* x, T* r, const T* pa, const T* pb, const T* q,
                           const Red& red, cudaStream_t s);
+    // the CG direction update and the operator apply of spmv_p as two sweeps (p = z + beta p; then
+    // q = (A - dI) p with p.q): for operators whose stencil evaluation per neighbour is costly
+    static void pupdate(const Launch& g, long long N, const T* z, T* pa, T* pb, const Red& red, cudaStream_t s);
+    static void spmv_q(const Launch& g, const Lev& L, int dim, bool var, const T* pa, const T* pb, T* q, const Red& red,
+                       cudaStream_t s);
     static void cheb_zero(const Launch& g, const Lev& L, int dim, bool var, const T* b, T* x, ChebStepT<T> cs,
                           const T* dsh, cudaStream_t s);
     static void cheb_step(const Launch& g, const Lev& L, int dim, bool var, const T* xin, const T* din, const T* b,

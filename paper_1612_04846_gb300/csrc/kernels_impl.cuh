@@ -731,6 +731,61 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k
     reduce_finish<T>(acc, red, Kp);
 }
 
+// p = z + beta p into the direction buffer the parity selects (the p update of k_spmv_p as its own
+// pointwise sweep, for operators whose stencil is costly to evaluate twice per neighbour).
+template <class T>
+__global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_pupdate(int N, int Kp, const T* __restrict__ z,
+                                                                        T* pa, T* pb, Red red) {
+    pdl_wait();
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    const int par = red.scal->parity;
+    const T* __restrict__ pold = par ? pb : pa;
+    T* __restrict__ pnew = par ? pa : pb;
+    T beta[W];
+    for (int v = 0; v < W; ++v) beta[v] = scal_val<T>(red.scal->beta, red.scal->betaf, off + v);
+    struct St { T zv[VecT<T>::W], pv[VecT<T>::W]; };
+    sweep_u<St>(
+        N, blockIdx.x, gridDim.x,
+        [&](int P, St& st) {
+            const size_t base = (size_t)P * Kp + off;
+            vld(z + base, st.zv);
+            vld(pold + base, st.pv);
+        },
+        [&](int P, St& st) {
+            T o[W];
+            for (int v = 0; v < W; ++v) o[v] = fma(beta[v], st.pv[v], st.zv[v]);
+            vst(pnew + (size_t)P * Kp + off, o);
+        });
+    pdl_trigger();
+}
+
+// q = (A - dI) p and p.q for the direction k_pupdate wrote (pa or pb by the parity).
+template <class T, int DIM, bool VAR>
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_spmv_q(Lev L, int Kp, const T* pa,
+                                                                                     const T* pb, T* __restrict__ q,
+                                                                                     Red red) {
+    pdl_wait();
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    const T* __restrict__ p = red.scal->parity ? pa : pb;
+    LoadPlain<T> ld{p};
+    T dsh[W];
+    for (int v = 0; v < W; ++v) dsh[v] = scal_val<T>(red.scal->dsh, red.scal->dshf, off + v);
+    Accum<T> acc;
+    sweep_u<StencilState<T>>(
+        L.N, blockIdx.x, gridDim.x,
+        [&](int P, StencilState<T>& st) { stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag); },
+        [&](int P, StencilState<T>& st) {
+            T qv[W];
+            for (int v = 0; v < W; ++v) qv[v] = fma(-dsh[v], st.xc[v], st.Ax[v]);
+            vst(q + (size_t)P * Kp + off, qv);
+            acc.add(st.xc, qv);
+        });
+    pdl_trigger();
+    reduce_finish<T>(acc, red, Kp);
+}
+
 template <class T>
 __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_cg_update(int N, int Kp, T* __restrict__ x, T* __restrict__ r, const T* pa, const T* pb,
                             const T* __restrict__ q, Red red) {
@@ -1147,6 +1202,17 @@ template <class T>
 void Ops<T>::spmv_p(const Launch& g, const Lev& L, int dim, bool var, const T* z, T* pa, T* pb, T* q,
                     const Red& red, cudaStream_t s) {
     BURA_DISPATCH_PDL0(dim, var, k_spmv_p, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, L, g.Kp, z, pa, pb, q, red);
+}
+
+template <class T>
+void Ops<T>::pupdate(const Launch& g, long long N, const T* z, T* pa, T* pb, const Red& red, cudaStream_t s) {
+    launch_pdl(k_pupdate<T>, dim3(g.blocks), blk(g), 0, s, (int)N, g.Kp, z, pa, pb, red);
+}
+
+template <class T>
+void Ops<T>::spmv_q(const Launch& g, const Lev& L, int dim, bool var, const T* pa, const T* pb, T* q, const Red& red,
+                    cudaStream_t s) {
+    BURA_DISPATCH_PDL0(dim, var, k_spmv_q, dim3(g.blocks), blk(g), shm(g, VecT<T>::W), s, L, g.Kp, pa, pb, q, red);
 }
 
 template <class T>

@@ -47,7 +47,7 @@ struct HostLevel {
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
            K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_REDFIN,
-           K_POST2, K_RESID, K_NK };
+           K_POST2, K_RESID, K_PUPD, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -73,7 +73,8 @@ const char* const kNames[K_NK][2][2] = {
     {{"cast_f_df", "cast_f_df"}, {"cast_f_df", "cast_f_df"}},
     {{"red_finish_f64", "red_finish_f64"}, {"red_finish_f32", "red_finish_f32"}},
     {{"post2_f64", "post2_f64@coarse"}, {"post2_f32", "post2_f32@coarse"}},
-    {{"residual_f64", "residual_f64@coarse"}, {"residual_f32", "residual_f32@coarse"}}};
+    {{"residual_f64", "residual_f64@coarse"}, {"residual_f32", "residual_f32@coarse"}},
+    {{"p_update_f64", "p_update_f64"}, {"p_update_f32", "p_update_f32"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -848,6 +849,11 @@ ChebStepT<T> step_of(const Work<T>& w, int l, int m, bool with_c1 = true) {
     return ChebStepT<T>{with_c1 ? w.c1[l] + (size_t)m * w.Kp : nullptr, w.c2[l] + (size_t)m * w.Kp};
 }
 
+// 3-D grids, variable coefficients and sparse operators run the first pre-smoothing step and the CG
+// direction update as their own pointwise sweeps: re-evaluating them at every stencil neighbour (as the
+// fused kernels do) costs more there than the extra vector pass.
+bool split_sweeps(const bura_plan* p) { return p->dim != 2 || p->var; }
+
 // Launch the shared-memory V-cycle over levels w.lc..nlev-1 for the right-hand side b (global), one
 // CTA per 16-byte chunk of systems; the result of level lc is written to w.xa[lc].  Inside a CTA every
 // level has b, xa, xb, dd of its chunk in shared memory; a level's pre-smoothing (zero step + deg-1
@@ -1031,10 +1037,24 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
         if (rz_fused) red_finish(p, beta, w.Kp, f32, s);
         return A;
     }
-    // pre-smoothing from a zero initial guess; the first two Chebyshev steps share one sweep
+    // pre-smoothing from a zero initial guess; the first two Chebyshev steps share one sweep (or, with
+    // split sweeps, the first step is a pointwise sweep and the second reads it as its previous direction)
     if (deg == 1) {
         traced(p, K_CHEB0, f32, fine, vbytes<T>(p, l, 2.0, var), s,
                [&] { Ops<T>::cheb_zero(g, L, dim, var, b, A, step_of(w, l, 0), w.dsh, s); });
+    } else if (!tl.on && split_sweeps(p)) {
+        traced(p, K_CHEB0, f32, fine, vbytes<T>(p, l, 2.0, var), s,
+               [&] { Ops<T>::cheb_zero(g, L, dim, var, b, A, step_of(w, l, 0), w.dsh, s); });
+        // d_1 = x_1 (the step from zero): the second step reads A as both iterate and direction
+        traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, deg > 2 ? 4.0 : 3.0, true), s,
+               [&] { cheb(A, A, B, deg > 2 ? D : nullptr, step_of(w, l, 1), none); });
+        std::swap(cur, oth);
+        for (int m = 2; m < deg; ++m) {
+            T* dout = m < deg - 1 ? D : nullptr;
+            traced(p, K_CHEB, f32, fine, vbytes<T>(p, l, 4.0 + (dout ? 1.0 : 0.0), true), s,
+                   [&] { cheb(cur, D, oth, dout, step_of(w, l, m), none); });
+            std::swap(cur, oth);
+        }
     } else {
         traced(p, K_PRE2, f32, fine, vbytes<T>(p, l, deg > 2 ? 3.0 : 2.0, true), s, [&] {
             const CUtensorMap* mb = tl.on ? tl.find(TB_HALO, b) : nullptr;
@@ -1101,13 +1121,18 @@ int pcg_body(bura_plan* p, Work<T>& w, unsigned long long cond, cudaStream_t s) 
     const Red rconv = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_CONV, cond});
     T* z = vcycle<T>(p, w, 0, w.r, true, s);
     const auto& tl = w.tma[0];
-    traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, 4.0, true), s, [&] {
+    if (!tl.on && split_sweeps(p))  // p = z + beta p as its own pointwise sweep
+        traced(p, K_PUPD, f32, true, vbytes<T>(p, 0, 3.0, false), s,
+               [&] { Ops<T>::pupdate(g, L.N, z, w.pa, w.pb, ralpha, s); });
+    traced(p, K_SPMV, f32, true, vbytes<T>(p, 0, !tl.on && split_sweeps(p) ? 2.0 : 4.0, true), s, [&] {
         const CUtensorMap* mz = tl.on ? tl.find(TB_HALO, z) : nullptr;
         const CUtensorMap* ma = tl.on ? tl.find(TB_HALO, w.pa) : nullptr;
         const CUtensorMap* mbb = tl.on ? tl.find(TB_HALO, w.pb) : nullptr;
         if (mz && ma && mbb)
             (void)tma_spmv_p(tl.geo, p->nsm, *mz, *ma, *mbb, reinterpret_cast<float*>(w.pa),
                              reinterpret_cast<float*>(w.pb), reinterpret_cast<float*>(w.q), ralpha, s);
+        else if (split_sweeps(p))
+            Ops<T>::spmv_q(g, L, p->dim, p->var, w.pa, w.pb, w.q, ralpha, s);
         else
             Ops<T>::spmv_p(g, L, p->dim, p->var, z, w.pa, w.pb, w.q, ralpha, s);
     });
