@@ -304,6 +304,90 @@ __device__ __forceinline__ void stencil(const Lev& L, int Kp, int P, int off, co
     }
 }
 
+// ------------------------------------------------------------------ 3-D column sweeps
+// The 3-D grid sweeps march along z: a work item is a segment of blockDim.y consecutive points of one
+// x-row over kZRun planes, a thread one point column of it (one 16-byte chunk).  The values of x on the
+// plane below and on the current plane stay in registers, so a point costs five neighbour loads (the new
+// plane above and the four in-plane neighbours) instead of seven, and the coordinates come from the item,
+// not from divisions per point.  Items are taken in a fixed order per CTA (b0, b0 + nb, ...), so the
+// per-thread partial sums are deterministic.
+constexpr int kZRun = 16;
+
+template <class T, bool VAR, class Body>
+__device__ __forceinline__ void zmarch(const Lev& L, int Kp, const T* __restrict__ x, int b0, int nb, Body&& body) {
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    const int PX = (int)blockDim.y;
+    const int nxs = (L.nx + PX - 1) / PX;
+    const int nzc = (L.nz + kZRun - 1) / kZRun;
+    const int per_z = nxs * L.ny;
+    const int items = per_z * nzc;
+    const size_t sx = (size_t)Kp, sy = (size_t)L.nx * Kp, sz = (size_t)L.plane * Kp;
+    const T wxc = sizeof(T) == 4 ? (T)L.wxf : (T)L.wx, wyc = sizeof(T) == 4 ? (T)L.wyf : (T)L.wy;
+    const T wzc = sizeof(T) == 4 ? (T)L.wzf : (T)L.wz;
+    for (int item = b0; item < items; item += nb) {
+        const int zc = item / per_z;
+        const int rem = item - zc * per_z;
+        const int j = rem / nxs;
+        const int i = (rem - j * nxs) * PX + (int)threadIdx.y;
+        if (i >= L.nx) continue;
+        const int l0 = zc * kZRun;
+        const int l1 = min(L.nz, l0 + kZRun);
+        int P = (l0 * L.ny + j) * L.nx + i;
+        size_t base = (size_t)P * Kp + off;
+        T xm1[W], x0[W], xp1[W];
+        for (int v = 0; v < W; ++v) xm1[v] = T(0);
+        if (l0 > 0) vld(x + base - sz, xm1);
+        vld(x + base, x0);
+        T zlo = T(0);  // the face weight between planes l - 1 and l
+        if (VAR) zlo = coef<T>(L, L.fz, (size_t)P);
+        for (int l = l0; l < l1; ++l, P += (int)L.plane, base += sz) {
+            for (int v = 0; v < W; ++v) xp1[v] = T(0);
+            if (l + 1 < L.nz) vld(x + base + sz, xp1);
+            T xl[W], xr[W], xd[W], xu[W];
+            for (int v = 0; v < W; ++v) xl[v] = xr[v] = xd[v] = xu[v] = T(0);
+            if (i > 0) vld(x + base - sx, xl);
+            if (i < L.nx - 1) vld(x + base + sx, xr);
+            if (j > 0) vld(x + base - sy, xd);
+            if (j < L.ny - 1) vld(x + base + sy, xu);
+            T wxm, wxp, wym, wyp, wzm, wzp, diag;
+            if (VAR) {
+                const size_t row = (size_t)l * L.ny + j;
+                wxm = coef<T>(L, L.fx, row * (L.nx + 1) + i);
+                wxp = coef<T>(L, L.fx, row * (L.nx + 1) + i + 1);
+                const size_t yb = ((size_t)l * (L.ny + 1) + j) * L.nx + i;
+                wym = coef<T>(L, L.fy, yb);
+                wyp = coef<T>(L, L.fy, yb + L.nx);
+                wzm = zlo;
+                wzp = coef<T>(L, L.fz, (size_t)P + L.plane);
+                zlo = wzp;
+                diag = __ldg(reinterpret_cast<const T*>(L.dg) + P);
+            } else {
+                wxm = wxp = wxc;
+                wym = wyp = wyc;
+                wzm = wzp = wzc;
+                diag = wxm + wxp + wym + wyp + wzm + wzp;
+            }
+            T Ax[W];
+            for (int v = 0; v < W; ++v) {
+                T a = diag * x0[v];
+                a = fma(-wxm, xl[v], a);
+                a = fma(-wxp, xr[v], a);
+                a = fma(-wym, xd[v], a);
+                a = fma(-wyp, xu[v], a);
+                a = fma(-wzm, xm1[v], a);
+                a = fma(-wzp, xp1[v], a);
+                Ax[v] = a;
+            }
+            body(P, base, x0, Ax, diag);
+            for (int v = 0; v < W; ++v) {
+                xm1[v] = x0[v];
+                x0[v] = xp1[v];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ void finish_one(const Red& red, Scal* S, int s, double tot) {
     switch (red.op) {
@@ -773,15 +857,24 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k
     T dsh[W];
     for (int v = 0; v < W; ++v) dsh[v] = scal_val<T>(red.scal->dsh, red.scal->dshf, off + v);
     Accum<T> acc;
-    sweep_u<StencilState<T>>(
-        L.N, blockIdx.x, gridDim.x,
-        [&](int P, StencilState<T>& st) { stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag); },
-        [&](int P, StencilState<T>& st) {
+    if constexpr (DIM == 3) {
+        zmarch<T, VAR>(L, Kp, p, blockIdx.x, gridDim.x, [&](int, size_t base, const T(&xc)[W], const T(&Ax)[W], T) {
             T qv[W];
-            for (int v = 0; v < W; ++v) qv[v] = fma(-dsh[v], st.xc[v], st.Ax[v]);
-            vst(q + (size_t)P * Kp + off, qv);
-            acc.add(st.xc, qv);
+            for (int v = 0; v < W; ++v) qv[v] = fma(-dsh[v], xc[v], Ax[v]);
+            vst(q + base, qv);
+            acc.add(xc, qv);
         });
+    } else {
+        sweep_u<StencilState<T>>(
+            L.N, blockIdx.x, gridDim.x,
+            [&](int P, StencilState<T>& st) { stencil<T, DIM, VAR>(L, Kp, P, off, ld, st.xc, st.Ax, st.diag); },
+            [&](int P, StencilState<T>& st) {
+                T qv[W];
+                for (int v = 0; v < W; ++v) qv[v] = fma(-dsh[v], st.xc[v], st.Ax[v]);
+                vst(q + (size_t)P * Kp + off, qv);
+                acc.add(st.xc, qv);
+            });
+    }
     pdl_trigger();
     reduce_finish<T>(acc, red, Kp);
 }
@@ -837,8 +930,35 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k
     LoadPlain<T> ld{xin};
     Accum<T> acc;
     const bool dot = red.op != RED_NONE;
-    sw_cheb_step<T, DIM, VAR>(L, Kp, ld, din, false, b, xout, dout, cs, dsh, dot ? &acc : nullptr, blockIdx.x,
-                              gridDim.x);
+    if constexpr (DIM == 3) {
+        constexpr int W = VecT<T>::W;
+        const int off = threadIdx.x * W;
+        T c1[W], c2[W], d[W];
+        for (int v = 0; v < W; ++v) {
+            c1[v] = cs.c1 ? (T)cs.c1[off + v] : T(0);
+            c2[v] = (T)cs.c2[off + v];
+            d[v] = (T)dsh[off + v];
+        }
+        zmarch<T, VAR>(L, Kp, xin, blockIdx.x, gridDim.x, [&](int, size_t base, const T(&xc)[W], const T(&Ax)[W], T diag) {
+            T bv[W], dv[W], xo[W];
+            vld(b + base, bv);
+            if (din) vld(din + base, dv);
+            else for (int v = 0; v < W; ++v) dv[v] = T(0);
+            for (int v = 0; v < W; ++v) {
+                const T res = bv[v] - fma(-d[v], xc[v], Ax[v]);
+                T g = c2[v] * res;
+                if (VAR) g = jdiv(g, diag - d[v]);
+                dv[v] = fma(c1[v], dv[v], g);
+                xo[v] = xc[v] + dv[v];
+            }
+            vst(xout + base, xo);
+            if (dout) vst(dout + base, dv);
+            if (dot) acc.add(bv, xo);
+        });
+    } else {
+        sw_cheb_step<T, DIM, VAR>(L, Kp, ld, din, false, b, xout, dout, cs, dsh, dot ? &acc : nullptr, blockIdx.x,
+                                  gridDim.x);
+    }
     pdl_trigger();
     if (dot) reduce_finish<T>(acc, red, Kp);
 }
@@ -892,7 +1012,20 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k
                                                                          const T* __restrict__ b, T* __restrict__ r,
                                                                          const T* __restrict__ dsh) {
     pdl_wait();
-    sw_residual<T, DIM, VAR>(L, Kp, x, b, r, dsh, blockIdx.x, gridDim.x);
+    if constexpr (DIM == 3) {
+        constexpr int W = VecT<T>::W;
+        const int off = threadIdx.x * W;
+        T d[W];
+        for (int v = 0; v < W; ++v) d[v] = (T)dsh[off + v];
+        zmarch<T, VAR>(L, Kp, x, blockIdx.x, gridDim.x, [&](int, size_t base, const T(&xc)[W], const T(&Ax)[W], T) {
+            T bv[W], rv[W];
+            vld(b + base, bv);
+            for (int v = 0; v < W; ++v) rv[v] = bv[v] - fma(-d[v], xc[v], Ax[v]);
+            vst(r + base, rv);
+        });
+    } else {
+        sw_residual<T, DIM, VAR>(L, Kp, x, b, r, dsh, blockIdx.x, gridDim.x);
+    }
 }
 
 template <class T, int DIM>

@@ -69,8 +69,15 @@ constexpr size_t kSmemPerSM = 228 * 1024;    // shared memory of an SM
 constexpr size_t kSmemPerCTA = 226 * 1024;   // largest dynamic allocation of one CTA (the 227 KB opt-in limit
                                              // covers static shared memory too: keep 1 KB for it)
 constexpr size_t kSmemReserved = 1024;       // per CTA, by the system
-constexpr int kPost2CtasPerSM = 2;           // the fused post-smoothing ring + scratch: 2 CTAs per SM (FP32,
-                                             // 8 values per point), so its registers may be more
+#ifndef BURA_POST2_CTAS
+#define BURA_POST2_CTAS 2
+#endif
+#ifndef BURA_POST2_STAGES
+#define BURA_POST2_STAGES 0
+#endif
+constexpr int kPost2CtasPerSM = BURA_POST2_CTAS;  // the fused post-smoothing ring + scratch: 2 CTAs per SM (FP32,
+                                                  // 8 values per point), so its registers may be more
+constexpr int kPost2Stages = BURA_POST2_STAGES;   // ring depth of the fused post-smoothing (0: the plan's)
 
 // The tile pipeline.  issue(stage, tile, bar) is called by thread 0 only; compute(stage, tile) by
 // every thread.  Returns false (after draining the copies in flight and flagging the fault) when a
@@ -925,6 +932,7 @@ cudaError_t tma_prepare(int Kp) {
 // Ring depth of a launch: the requested depth, reduced until the ring fits one CTA (at least 1).
 int ring_stages(const TmaGeo& g, int kind) {
     int S = g.stages < 1 ? kTmaStages : (g.stages > kTmaMaxStages ? kTmaMaxStages : g.stages);
+    if (kind == TK_POST2 && kPost2Stages > 0) S = kPost2Stages;
     while (S > 1 && dyn_smem(kind, g.Kp, S) + kRingSlack > kSmemPerCTA) --S;
     return S;
 }
