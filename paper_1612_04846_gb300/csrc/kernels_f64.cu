@@ -56,6 +56,15 @@ __global__ void k_residual64(Lev L, int Kp, const double* __restrict__ f_arg, co
                 vst(r + (size_t)P * Kp + off, rv);
                 acc.add(rv, rv);
             });
+    } else if constexpr (DIM == 3) {
+        zmarch<double, VAR>(L, Kp, v, blockIdx.x, gridDim.x,
+                            [&](int P, size_t base, const double(&xc)[W], const double(&Ax)[W], double) {
+                                const double fv = __ldg(f + P);
+                                double rv[W];
+                                for (int q = 0; q < W; ++q) rv[q] = fv - fma(-d[q], xc[q], Ax[q]);
+                                vst(r + base, rv);
+                                acc.add(rv, rv);
+                            });
     } else {
         LoadPlain<double> ld{v};
         sweep_u<StencilState<double>>(

@@ -366,7 +366,8 @@ __device__ __forceinline__ void zmarch(const Lev& L, int Kp, const T* __restrict
                 wxm = wxp = wxc;
                 wym = wyp = wyc;
                 wzm = wzp = wzc;
-                diag = wxm + wxp + wym + wyp + wzm + wzp;
+                diag = wxm + wxp + wym + wyp;
+                diag += wzm + wzp;  // the association of the point stencil's diagonal
             }
             T Ax[W];
             for (int v = 0; v < W; ++v) {
