@@ -48,6 +48,9 @@ def parse_args(argv=None):
     ap.add_argument("--skip-3d", action="store_true", help="skip the 3D variable-coefficient workload")
     ap.add_argument("--skip-batch", action="store_true", help="skip the batched 256-problem workload")
     ap.add_argument("--skip-csr", action="store_true", help="skip the sparse (P1 finite-element) workload")
+    ap.add_argument("--skip-bp15", action="store_true", help="skip the BURA / [BP15] quadrature comparison")
+    ap.add_argument("--shape3", type=int, default=255, help="interior points per axis of the 3D workload "
+                    "(255 for the measured line; a smaller size keeps a profiler capture small)")
     ap.add_argument("--skip-serve", action="store_true", help="skip the serving workload (Poisson arrivals)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests/s of the serving workload")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured arrival window of the serving workload")
@@ -167,8 +170,9 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it matches these sources."""
+def ncu_traffic(kernel, workload="2d_1023_k7"):
+    """DRAM bytes per launch of `kernel` on a workload from the committed ncu summary, if it matches these
+    sources (a capture of a smaller case is scaled to the full size by the points processed)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
             d = json.load(fh)
@@ -176,7 +180,7 @@ def ncu_traffic(kernel):
         return None
     if d.get("sources_sha") != sources_sha():
         return None
-    ent = d.get("kernels", {}).get(kernel)
+    ent = d.get("workloads", {}).get(workload, {}).get(kernel)
     return None if ent is None else float(ent["dram_bytes_per_launch_full_size"])
 
 
@@ -259,13 +263,13 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
-SHAPE3 = (255, 255, 255)
+N3 = 255  # interior points per axis of the 3D workload (bench.py --shape3)
 WORKLOAD3 = ("3D 7-point -div(a grad u), 255^3 interior (N=16581375), Dirichlet, a log-uniform in [1e-2,1] "
              "on 8^3 blocks (seed 2), alpha=0.5, k=9, f~N(0,1) seed 3, FP32 MG-PCG inner + FP64 refinement, "
              "tol 1e-6")
 
 
-def roofline_from_profile(prof, nsolves):
+def roofline_from_profile(prof, nsolves, workload="2d_1023_k7"):
     """HBM roofline of the kernel with the largest share of the timed fine-level kernel time: algorithmic
     bytes of its launches / their summed CUDA-event durations, against the measured copy peak."""
     if not prof:
@@ -275,7 +279,7 @@ def roofline_from_profile(prof, nsolves):
     peak, peak_kind = measured_hbm_peak()
     achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
     return {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(dom["name"]),
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": ncu_traffic(dom["name"], workload),
             "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
             "ms_per_launch": dom["ms"] / dom["launches"], "share_of_fine_kernel_time": dom["ms"] / prof_total,
             "kernels": {p["name"]: {"launches_per_solve": p["launches"] / nsolves, "ms_per_launch": p["ms"] / p["launches"],
@@ -286,15 +290,16 @@ def bench_3d(bura, W, np, torch, dev, stream, flush, rank, ws, steps, cpu_leg):
     """The 3D variable-coefficient workload: solves/s (CUDA events per solve, L2 flushed between), the
     roofline of its dominant kernel, end to end through host buffers, and the oracle's same-method solve
     of its hardest system on the host cores."""
-    nps = tuple(reversed(SHAPE3))
-    N = int(np.prod(SHAPE3))
+    shape3 = (N3, N3, N3)
+    nps = tuple(reversed(shape3))
+    N = int(np.prod(shape3))
     faces = W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 2)
     f_host = W.rhs_normal(nps, 3 + 1000 * rank)
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)
     t0 = time.perf_counter()
     o = bura.bura_default_options()
-    plan = bura.bura_setup(SHAPE3, 0.5, 9, faces=faces, options=o)
+    plan = bura.bura_setup(shape3, 0.5, 9, faces=faces, options=o)
     setup_s = time.perf_counter() - t0
     try:
         bura.bura_solve(plan, f, u, TOL, stream)
@@ -331,10 +336,10 @@ def bench_3d(bura, W, np, torch, dev, stream, flush, rank, ws, steps, cpu_leg):
     finally:
         bura.bura_destroy(plan)
     ms = sum(times) / len(times)
-    out = {"workload": WORKLOAD3, "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "steps": steps,
+    out = {"workload": WORKLOAD3 if N3 == 255 else WORKLOAD3.replace("255^3", "%d^3" % N3), "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "steps": steps,
            "Gunknown_shifts_per_s": N * 10 / (ms / 1e3) / 1e9, "inner_iters": st["iters"], "outer": st["outer"],
            "shift_iters": st["shift_iters"], "err_bound": st["err_bound"], "levels": st["levels"], "setup_s": setup_s,
-           "roofline": roofline_from_profile(prof, 1),
+           "roofline": roofline_from_profile(prof, 1, "3d_%d_var_k9" % N3),
            "e2e": {"value": aggregate(ne2e, ws, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": N * 8,
                    "d2h_bytes_per_step": N * 8, "entry_point": "bura_solve_host"}}
     if cpu_leg:
@@ -397,7 +402,67 @@ def bench_csr(bura, W, np, torch, dev, stream, flush, rank, steps):
     ms = sum(times) / len(times)
     return {"workload": WORKLOAD_CSR, "rows": N, "nnz": int(A.nnz), "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
             "steps": steps, "Gunknown_shifts_per_s": N * 8 / (ms / 1e3) / 1e9, "inner_iters": st["iters"],
-            "outer": st["outer"], "setup_s": setup_s, "roofline": roofline_from_profile(prof, 1)}
+            "outer": st["outer"], "setup_s": setup_s, "roofline": roofline_from_profile(prof, 1, "csr_p1_63_k7")}
+
+
+WORKLOAD_BP15 = ("comparison with the [BP15] sinc quadrature (Sec. 5.3): 2D 1023^2, checkerboard f, the paper's "
+                 "equal-accuracy system counts (BURA k = 9 / 8 / 7 against 40 / 21 / 15 quadrature nodes for alpha = "
+                 "0.25 / 0.5 / 0.75), both on the same multi-shift solver (quadrature nodes over plans of <= 13 systems, "
+                 "bura_solve_sum), mixed precision, tol 1e-8")
+BP15_CASES = ((0.25, 9, 40), (0.5, 8, 21), (0.75, 7, 15))
+
+
+def _kprime_for(bura, alpha, nsys, lam):
+    """The largest k' (smallest step) whose quadrature has exactly nsys nodes, by bisection on the count."""
+    lo, hi = 0.05, 5.0
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        n = len(bura.bura_quadrature_bp15(alpha, mid, lam)[0])
+        if n > nsys:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def bench_bp15(bura, W, np, torch, dev, stream, flush, cpu_leg):
+    """GPU time of the BURA solve against the [BP15] quadrature at the paper's equal-accuracy system counts;
+    with the CPU leg, both results' relative l2 errors against the exact A^-alpha f (oracle)."""
+    shape = (1023, 1023)
+    f_host = W.checkerboard_rhs(shape)
+    f = torch.from_numpy(f_host).to(dev)
+    u = torch.zeros_like(f)
+    lam = bura.bura_scale(shape)
+    out = {"workload": WORKLOAD_BP15, "cases": []}
+    for alpha, k, nq in BP15_CASES:
+        kp = _kprime_for(bura, alpha, nq, lam)
+        c, d = bura.bura_quadrature_bp15(alpha, kp, lam)
+        bplan = [bura.bura_setup(shape, alpha, k)]
+        qplans = [bura.bura_setup_shifts(shape, c[i:i + 13], d[i:i + 13]) for i in range(0, len(c), 13)]
+        case = {"alpha": alpha, "bura_k": k, "bura_systems": k + 1, "bp15_kprime": kp, "bp15_systems": len(c)}
+        try:
+            for label, plans in (("bura", bplan), ("bp15", qplans)):
+                bura.bura_solve_sum(plans, f, u, 1e-8, stream)
+                torch.cuda.synchronize()
+                t = []
+                for _ in range(5):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    bura.bura_solve_sum(plans, f, u, 1e-8, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    t.append(e0.elapsed_time(e1))
+                case[label + "_ms"] = sorted(t)[2]
+                if cpu_leg:
+                    from oracle import exact
+                    ref = exact.fractional(tuple(reversed(shape)), f_host, alpha)
+                    case[label + "_rel_err_vs_exact"] = float(np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref))
+        finally:
+            for p in bplan + qplans:
+                bura.bura_destroy(p)
+        out["cases"].append(case)
+    return out
 
 
 WORKLOAD_BATCH = ("batched: 256 right-hand sides over 2D 5-point grids drawn uniformly from {63^2,127^2,255^2,511^2}, "
@@ -645,7 +710,9 @@ def serve_fp64_one_at_a_time(bura, np, data, upool, count):
 
 
 def main(argv=None):
+    global N3
     args = parse_args(argv)
+    N3 = args.shape3
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
@@ -823,6 +890,9 @@ def main(argv=None):
     wc = None
     if not args.skip_csr:
         wc = bench_csr(bura, W, np, torch, dev, stream, flush, rank, max(3, args.steps // 20))
+    wq = None
+    if not args.skip_bp15:
+        wq = bench_bp15(bura, W, np, torch, dev, stream, flush, rank == 0 and ws == 1 and not args.no_cpu_baseline)
     wb = None
     if not args.skip_batch:
         wb = bench_batch(bura, W, np, torch, dev, rank, 2)
@@ -843,7 +913,8 @@ def main(argv=None):
                 "fp64_path_solves_per_s": fp64_solves,
                 "df_refine_solves_per_s": df_solves,
                 "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "csr_p1_63_halfcube_k7": wc, "batch_256_mixed_2d": wb,
+                "clocks": clk, "cpu_baseline": cpu, "workloads": {"3d_255_var_k9": w3, "csr_p1_63_halfcube_k7": wc, "bp15_comparison_1023": wq,
+                                                               "batch_256_mixed_2d": wb,
                                                                "serve_poisson_mixed": wsv}}
         print(json.dumps(line), flush=True)
     if dist.is_initialized():
