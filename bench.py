@@ -336,7 +336,8 @@ def bench_3d(bura, W, np, torch, dev, stream, flush, rank, ws, steps, cpu_leg):
     finally:
         bura.bura_destroy(plan)
     ms = sum(times) / len(times)
-    out = {"workload": WORKLOAD3 if N3 == 255 else WORKLOAD3.replace("255^3", "%d^3" % N3), "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "steps": steps,
+    wl = WORKLOAD3 if N3 == 255 else WORKLOAD3.replace("255^3 interior (N=16581375)", "%d^3 interior (N=%d)" % (N3, N))
+    out = {"workload": wl, "solves_per_s": 1e3 / ms, "ms_per_solve": ms, "steps": steps,
            "Gunknown_shifts_per_s": N * 10 / (ms / 1e3) / 1e9, "inner_iters": st["iters"], "outer": st["outer"],
            "shift_iters": st["shift_iters"], "err_bound": st["err_bound"], "levels": st["levels"], "setup_s": setup_s,
            "roofline": roofline_from_profile(prof, 1, "3d_%d_var_k9" % N3),

@@ -627,32 +627,41 @@ __global__ void __launch_bounds__(kTmaThreads, kPost2CtasPerSM)
             const float* B = reinterpret_cast<const float*>(st + b_ofs);
             // (1) xin = x + P ec on the two-point halo region, by 2 x 2 blocks of fine points: the block
             // at even (fi, fj) interpolates from coarse points (fi/2 - 1 .. fi/2) x (fj/2 - 1 .. fj/2),
-            // at box offsets (bx, by); the weighted sums are k_prolong_cheb_tma's, term for term
-            for (int q = threadIdx.y; q < (kH2X / 2) * (kH2Y / 2); q += blockDim.y) {
-                const int by = q / (kH2X / 2), bx = q - by * (kH2X / 2);
-                float e00[4], e01[4], e10[4], e11[4];
-                ld4(E + (by * kCp2X + bx) * Kp + off, e00);
+            // at box offsets (bx, by); the weighted sums are k_prolong_cheb_tma's, term for term.  Item q
+            // is the column hx = 2 bx + (q & 1) of block q >> 1 (its two points): consecutive threads
+            // touch consecutive points of the x stage, so its loads and stores are free of bank conflicts.
+            for (int q = threadIdx.y; q < kH2X * (kH2Y / 2); q += blockDim.y) {
+                const int blk = q >> 1, px = q & 1;
+                const int by = blk / (kH2X / 2), bx = blk - by * (kH2X / 2);
+                float e01[4], e11[4], sa[4], sb[4];  // sa: point (px, 0), sb: point (px, 1) of the block
                 ld4(E + (by * kCp2X + bx + 1) * Kp + off, e01);
-                ld4(E + ((by + 1) * kCp2X + bx) * Kp + off, e10);
                 ld4(E + ((by + 1) * kCp2X + bx + 1) * Kp + off, e11);
-                float s4[4][4];  // [fine point of the block: (0,0), (1,0), (0,1), (1,1)][value]
-                for (int v = 0; v < 4; ++v) {
-                    float t = fmaf(0.25f, e00[v], 0.f);
-                    t = fmaf(0.25f, e01[v], t);
-                    t = fmaf(0.25f, e10[v], t);
-                    s4[0][v] = fmaf(0.25f, e11[v], t);
-                    s4[1][v] = fmaf(0.5f, e11[v], fmaf(0.5f, e01[v], 0.f));
-                    s4[2][v] = fmaf(0.5f, e11[v], fmaf(0.5f, e10[v], 0.f));
-                    s4[3][v] = fmaf(1.f, e11[v], 0.f);
+                if (px == 0) {
+                    float e00[4], e10[4];
+                    ld4(E + (by * kCp2X + bx) * Kp + off, e00);
+                    ld4(E + ((by + 1) * kCp2X + bx) * Kp + off, e10);
+                    for (int v = 0; v < 4; ++v) {
+                        float t = fmaf(0.25f, e00[v], 0.f);
+                        t = fmaf(0.25f, e01[v], t);
+                        t = fmaf(0.25f, e10[v], t);
+                        sa[v] = fmaf(0.25f, e11[v], t);
+                        sb[v] = fmaf(0.5f, e11[v], fmaf(0.5f, e10[v], 0.f));
+                    }
+                } else {
+                    for (int v = 0; v < 4; ++v) {
+                        sa[v] = fmaf(0.5f, e11[v], fmaf(0.5f, e01[v], 0.f));
+                        sb[v] = fmaf(1.f, e11[v], 0.f);
+                    }
                 }
-                for (int j = 0; j < 4; ++j) {
-                    const int hx = 2 * bx + (j & 1), hy = 2 * by + (j >> 1);
-                    const int fi = x0 - 2 + hx, fj = y0 - 2 + hy;
+                const int hx = 2 * bx + px;
+                const int fi = x0 - 2 + hx;
+                for (int r = 0; r < 2; ++r) {
+                    const int hy = 2 * by + r, fj = y0 - 2 + hy;
                     const int h = (hy * kH2X + hx) * Kp + off;
                     float xn[4] = {0.f, 0.f, 0.f, 0.f};
                     if (fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny) {
                         ld4(X + h, xn);
-                        for (int v = 0; v < 4; ++v) xn[v] += s4[j][v];
+                        for (int v = 0; v < 4; ++v) xn[v] += r ? sb[v] : sa[v];
                     }
                     st4(X + h, xn);
                 }
