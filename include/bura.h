@@ -66,11 +66,17 @@ typedef struct {
 
 /* How the small levels of the multigrid V-cycle are run. */
 typedef enum {
-    BURA_COARSE_AUTO = 0,    /* currently CTA (the faster of the two on GB300) */
+    BURA_COARSE_AUTO = 0,    /* FDIAG for 2-D constant coefficients, else CTA (faster than CLUSTER on GB300) */
     BURA_COARSE_CLUSTER = 1, /* levels with <= 16384 points in one thread-block cluster (vectors in L2);
                                 bura_setup returns BURA_EINVAL on a device without cluster launch */
     BURA_COARSE_CTA = 2,     /* the levels that fit 200 KB of shared memory in a single CTA */
-    BURA_COARSE_NONE = 3     /* every level as grid-wide kernels; the coarsest level is smoothed only */
+    BURA_COARSE_NONE = 3,    /* every level as grid-wide kernels; the coarsest level is smoothed only */
+    BURA_COARSE_FDIAG = 4    /* 2-D constant coefficients only (else BURA_EINVAL; also without cluster launch):
+                                the first level with at most 63 (FP32) or 31 (FP64) points per axis is
+                                solved exactly by fast diagonalization, (A - d_j I)^{-1} = S_y (S_y . S_x ./
+                                (lambda_x + lambda_y - d_j)) S_x in the sine eigenbasis of the 5-point
+                                operator (per axis the eigenpairs of the three-point matrix of Sec. 4.1; the
+                                eigen-expansion of eq. (exacalg), Sec. 1.2), and the V-cycle stops there */
 } bura_coarse_kernel;
 
 /* How the level sweeps of the large levels are run. */

@@ -21,7 +21,7 @@ BURA_OK, BURA_EINVAL, BURA_ENOMEM, BURA_EREMEZ = 0, -1, -2, -3
 BURA_ENOTSPD, BURA_ENOCONV, BURA_ETIMEOUT, BURA_ECUDA, BURA_ERANGE = -4, -5, -6, -7, -8
 BURA_COEF_CONSTANT, BURA_COEF_FACES = 0, 1
 BURA_PREC_FP64, BURA_PREC_MIXED = 0, 1
-BURA_COARSE_AUTO, BURA_COARSE_CLUSTER, BURA_COARSE_CTA, BURA_COARSE_NONE = 0, 1, 2, 3
+BURA_COARSE_AUTO, BURA_COARSE_CLUSTER, BURA_COARSE_CTA, BURA_COARSE_NONE, BURA_COARSE_FDIAG = 0, 1, 2, 3, 4
 BURA_SWEEP_AUTO, BURA_SWEEP_GRID = 0, 1
 BURA_REFINE_FP64, BURA_REFINE_DF = 0, 1
 

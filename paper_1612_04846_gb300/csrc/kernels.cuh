@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include <utility>
+#include <vector>
 
 namespace bura {
 
@@ -165,6 +166,14 @@ constexpr long long kClusterPoints = 16384; // levels with at most this many poi
 
 constexpr unsigned int kNoCopy = 0xffffffffu;
 constexpr long long kExactPoints = 64;  // a coarse-CTA level this small is solved with dense inverses
+// Most points per axis of the level solved exactly by fast diagonalization (2-D, constant coefficients):
+// 63 in FP32 (measured on GB300: the 127^2 solve costs more than the two levels it replaces), 31 in FP64 (whose
+// multiply-add rate on GB300 is a small fraction of FP32's).
+#ifndef BURA_FDIAG_MAXN32
+#define BURA_FDIAG_MAXN32 63
+#endif
+template <class T>
+constexpr int kFdiagMaxN = sizeof(T) == 4 ? BURA_FDIAG_MAXN32 : 31;
 constexpr int kMaxCoarseLevels = 16;
 // Grid sweeps run CTAs of at most 256 threads; the register cap of 64 keeps 8 CTAs of 128 threads
 // (or 4 of 256) resident per SM, so one wave covers the whole grid.
@@ -192,6 +201,31 @@ struct CoarseArgs {
 struct Launch {
     int Kp, C, PPB, blocks;
 };
+
+// Exact coarsest-level solve of a 2-D constant-coefficient operator by fast diagonalization (fdiag.cu):
+// one thread-block cluster of G CTAs per shifted system; every array holds element type T.
+struct FdiagArgs {
+    int nx, ny, Kp;
+    const void* b;     // right-hand sides, [ny][nx][Kp]
+    void* x;           // solutions, [ny][nx][Kp]
+    const void* simg;  // the orthonormal sine bases along x and y ([nx][nx], [ny][ny], symmetric) laid out
+                       // as the kernel keeps them in shared memory (fdiag_image)
+    const void* lx;    // eigenvalues of the x part of the level operator, [nx]
+    const void* ly;    // and of the y part, [ny]
+    const void* dsh;   // the shifts d_j, [Kp]
+    Scal* scal;        // wait budget (wait_cycles) and fault flag
+};
+template <class T>
+size_t fdiag_smem_bytes(int nx, int ny, int G);
+// The shared-memory image of the two sine bases (given row-major in FP64), in T.
+template <class T>
+void fdiag_image(int nx, int ny, const double* sx, const double* sy, std::vector<T>& img);
+// Largest cluster size G (16 .. 1, at most min(nx, ny)) with all nsys clusters resident at once (else the
+// most CTAs resident), and its dynamic shared memory; sets the kernel's launch attributes.
+template <class T>
+cudaError_t fdiag_prepare(int nx, int ny, int nsys, int* G, size_t* smem);
+template <class T>
+cudaError_t fdiag_launch(const FdiagArgs& a, int G, size_t smem, int nsys, cudaStream_t s);
 
 // ------------------------------------------------------------------ host launchers
 template <class T>

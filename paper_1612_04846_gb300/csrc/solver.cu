@@ -47,7 +47,7 @@ struct HostLevel {
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
            K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_REDFIN,
-           K_POST2, K_RESID, K_PUPD, K_NK };
+           K_POST2, K_RESID, K_PUPD, K_FDIAG, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -74,7 +74,8 @@ const char* const kNames[K_NK][2][2] = {
     {{"red_finish_f64", "red_finish_f64"}, {"red_finish_f32", "red_finish_f32"}},
     {{"post2_f64", "post2_f64@coarse"}, {"post2_f32", "post2_f32@coarse"}},
     {{"residual_f64", "residual_f64@coarse"}, {"residual_f32", "residual_f32@coarse"}},
-    {{"p_update_f64", "p_update_f64"}, {"p_update_f32", "p_update_f32"}}};
+    {{"p_update_f64", "p_update_f64"}, {"p_update_f32", "p_update_f32"}},
+    {{"coarse_fdiag_f64", "coarse_fdiag_f64@coarse"}, {"coarse_fdiag_f32", "coarse_fdiag_f32@coarse"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -100,13 +101,18 @@ struct Work {
     std::vector<T*> c1, c2;       // [level] -> deg rows of Kp coefficients, in the kernels' precision
     std::vector<int> deg;
     int lc = -1;                  // first level run by the coarse kernel (-1: none, grid kernels to the end)
-    int coarse_kind = 0;          // BURA_COARSE_CLUSTER or BURA_COARSE_CTA
+    int coarse_kind = 0;          // BURA_COARSE_CLUSTER, BURA_COARSE_CTA or BURA_COARSE_FDIAG
     int csize = 0;                // CTAs of the cluster (cluster kind)
     int le = -1;                  // level solved exactly with dense inverses inside that kernel (-1: none)
     T* minv = nullptr;            // the inverses, [row][col][Kp]
     size_t coarse_smem = 0;       // shared-memory bytes of the single-CTA kind's vectors
     size_t minv_smem = 0;         // bytes of one chunk's inverses staged in its shared memory (0: not staged)
     Launch gc{};                  // launch shape of the coarse kernel (one CTA)
+    // fast-diagonalization coarse solve (BURA_COARSE_FDIAG): level lc solved exactly, one cluster of fd_G
+    // CTAs per system; sine bases and 1-D eigenvalues of level lc in the kernels' precision
+    T *fd_img = nullptr, *fd_lx = nullptr, *fd_ly = nullptr;
+    int fd_G = 0;
+    size_t fd_smem = 0;
     T* dsh = nullptr;  // the shifts d_j (KMAXP entries) in the kernels' precision
     Scal* scal = nullptr;
     // TMA-staged sweeps (FP32, 2-D, constant coefficients) of the levels with at least one tile per SM:
@@ -588,6 +594,40 @@ double smoother_ratio(const bura_plan* p) {
     return p->dim == 3 ? 8.0 : 4.0;
 }
 
+// The fast-diagonalization tables of level lc (independent of the shifts): for each axis the orthonormal
+// sine basis S_ik = sqrt(2/(n+1)) sin(pi (i+1)(k+1)/(n+1)) and the eigenvalues w (2 - 2 cos(pi (k+1)/(n+1)))
+// = 4 w sin^2(pi (k+1) / (2 (n+1))) of w tridiag(-1, 2, -1), in FP64, rounded to T.
+template <class T>
+int upload_fdiag(bura_plan* p, Work<T>& w) {
+    const HostLevel& h = p->hl[w.lc];
+    std::vector<double> S[2];
+    T** dst_l[2] = {&w.fd_lx, &w.fd_ly};
+    for (int a = 0; a < 2; ++a) {
+        const int n = h.n[a];
+        const double pi = 3.14159265358979323846;
+        const double sc = std::sqrt(2.0 / (n + 1));
+        S[a].resize((size_t)n * n);
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) {
+                // (i+1)(k+1) reduced modulo 2 (n+1): the same angle, with no large argument
+                const long long m = (long long)(i + 1) * (k + 1) % (2LL * (n + 1));
+                S[a][(size_t)i * n + k] = sc * std::sin(pi * (double)m / (n + 1));
+            }
+        std::vector<T> lam(n);
+        for (int k = 0; k < n; ++k) {
+            const double sk = std::sin(pi * (k + 1) / (2.0 * (n + 1)));
+            lam[k] = (T)(4.0 * h.w[a] * sk * sk);
+        }
+        CA(dalloc(p, dst_l[a], (size_t)n * sizeof(T)));
+        CK(cudaMemcpy(*dst_l[a], lam.data(), lam.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    std::vector<T> img;
+    fdiag_image<T>(h.n[0], h.n[1], S[0].data(), S[1].data(), img);
+    CA(dalloc(p, &w.fd_img, img.size() * sizeof(T)));
+    CK(cudaMemcpy(w.fd_img, img.data(), img.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return BURA_OK;
+}
+
 // The shift-dependent tables of a work set, written into its existing buffers: per level the Chebyshev
 // coefficients c1, c2 (deg x Kp), the shifts, and the dense inverses of the exact level.  Their sizes
 // do not depend on the shifts (the coarsest degree depends on d_0 = 0 only), so a plan can be moved
@@ -765,11 +805,22 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
     w.lc = -1;
     w.coarse_smem = 0;
     w.coarse_kind = p->opt.coarse_kernel;
-    // measured on GB300 (2-D 1023^2, k = 7): the single CTA over shared memory beats the cluster, whose
-    // sweeps each pay an L2 round trip and a cluster barrier (about 3 us of fixed cost per sweep)
-    if (w.coarse_kind == BURA_COARSE_AUTO) w.coarse_kind = BURA_COARSE_CTA;
+    // 2-D constant coefficients: the exact fast-diagonalization solve of a level of up to kFdiagMaxN
+    // points per axis replaces that level and every coarser one.  Otherwise, as measured on GB300 (2-D
+    // 1023^2, k = 7), the single CTA over shared memory beats the cluster, whose sweeps each pay an L2
+    // round trip and a cluster barrier (about 3 us of fixed cost per sweep).
+    if (w.coarse_kind == BURA_COARSE_AUTO)
+        w.coarse_kind = (p->dim == 2 && !p->var && p->cluster_ok) ? BURA_COARSE_FDIAG : BURA_COARSE_CTA;
     if (p->dim == 0) w.coarse_kind = BURA_COARSE_NONE;  // one level: the polynomial preconditioner alone
-    if (w.coarse_kind == BURA_COARSE_CLUSTER) {
+    if (w.coarse_kind == BURA_COARSE_FDIAG) {
+        for (int l = 0; l < nlev; ++l)
+            if (std::max(p->hl[l].n[0], p->hl[l].n[1]) <= kFdiagMaxN<T>) { w.lc = l; break; }
+        if (w.lc >= 0) {
+            const int nx = p->hl[w.lc].n[0], ny = p->hl[w.lc].n[1];
+            CK(fdiag_prepare<T>(nx, ny, w.Kp, &w.fd_G, &w.fd_smem));
+            CA(upload_fdiag<T>(p, w));
+        }
+    } else if (w.coarse_kind == BURA_COARSE_CLUSTER) {
         // the small levels (at most kClusterPoints points each, L2 resident) run in one thread-block cluster
         for (int l = 0; l <= last; ++l)
             if (p->hl[l].N <= kClusterPoints && last - l + 1 <= kMaxCoarseLevels) { w.lc = l; break; }
@@ -791,7 +842,7 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
             }
         }
     }
-    if (w.lc < 0) w.le = -1;  // the dense solve lives in the coarse kernel only
+    if (w.lc < 0 || w.coarse_kind == BURA_COARSE_FDIAG) w.le = -1;  // the dense solve lives in the CTA / cluster kernels only
     if (w.le >= 0) {  // [row][col][Kp] dense inverses of the exact level, filled by upload_tables
         const size_t n = (size_t)p->hl[w.le].N;
         CA(dalloc(p, &w.minv, n * n * w.Kp * sizeof(T)));
@@ -949,6 +1000,27 @@ T* cluster_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
     return reinterpret_cast<T*>(const_cast<void*>(a.lev[0].result));
 }
 
+// The exact solve of level lc by fast diagonalization for the right-hand side b; the result is written
+// to w.xa[lc].
+template <class T>
+T* fdiag_part(bura_plan* p, Work<T>& w, const T* b, cudaStream_t s) {
+    const HostLevel& h = p->hl[w.lc];
+    FdiagArgs a;
+    a.nx = h.n[0];
+    a.ny = h.n[1];
+    a.Kp = w.Kp;
+    a.b = b;
+    a.x = w.xa[w.lc];
+    a.simg = w.fd_img;
+    a.lx = w.fd_lx;
+    a.ly = w.fd_ly;
+    a.dsh = w.dsh;
+    a.scal = w.scal;
+    traced(p, K_FDIAG, sizeof(T) == 4, w.lc == 0, vbytes<T>(p, w.lc, 2.0, false), s,
+           [&] { (void)fdiag_launch<T>(a, w.fd_G, w.fd_smem, w.Kp, s); });  // errors: cudaGetLastError
+    return w.xa[w.lc];
+}
+
 // Symmetric V-cycle on level l for rhs b; returns the buffer holding the result.  With rz_fused
 // (level 0 only) the last smoothing step also forms r^T z and the CG beta of every system.
 template <class T>
@@ -963,7 +1035,9 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     Red none{p->partial, p->tickets, w.scal, nullptr, RED_NONE, 0};
     const Red beta = deferred(p, Red{p->partial, p->tickets, w.scal, nullptr, RED_BETA, 0});
     if (l == w.lc) {  // the rest of the hierarchy in one kernel
-        T* res = w.coarse_kind == BURA_COARSE_CLUSTER ? cluster_part(p, w, b, s) : coarse_part(p, w, b, s);
+        T* res = w.coarse_kind == BURA_COARSE_CLUSTER ? cluster_part(p, w, b, s)
+                 : w.coarse_kind == BURA_COARSE_FDIAG ? fdiag_part(p, w, b, s)
+                                                      : coarse_part(p, w, b, s);
         if (rz_fused) {
             traced(p, K_DOT, f32, fine, vbytes<T>(p, l, 2.0, false), s, [&] { Ops<T>::dot(g, L.N, b, res, beta, s); });
             red_finish(p, beta, w.Kp, f32, s);
@@ -1892,7 +1966,7 @@ int check_options(const bura_options& o) {
     if (o.smoother_degree < 1 || o.smoother_degree > 16 || !(o.smoother_ratio == 0 || o.smoother_ratio > 1) || o.max_iters < 1 ||
         o.max_outer < 1 || !(o.inner_rtol > 0 && o.inner_rtol < 1) || o.coarse_degree < 0 || o.coarse_degree > 1000 ||
         o.block_points < 0 || o.block_points > 1024 || o.blocks_per_sm < 0 || o.blocks_per_sm > 64 ||
-        o.coarse_kernel < BURA_COARSE_AUTO || o.coarse_kernel > BURA_COARSE_NONE ||
+        o.coarse_kernel < BURA_COARSE_AUTO || o.coarse_kernel > BURA_COARSE_FDIAG ||
         !(o.cluster_size == 0 || o.cluster_size == 2 || o.cluster_size == 4 || o.cluster_size == 8 ||
           o.cluster_size == 16) ||
         o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
@@ -1920,7 +1994,8 @@ int setup_device(bura_plan* p, long long N, bura_plan** out) {
     p->nsm = nsm;
     int cl = 0;
     p->cluster_ok = cudaDeviceGetAttribute(&cl, cudaDevAttrClusterLaunch, p->dev) == cudaSuccess && cl != 0;
-    if (o.coarse_kernel == BURA_COARSE_CLUSTER && !p->cluster_ok) return fail(BURA_EINVAL);
+    if ((o.coarse_kernel == BURA_COARSE_CLUSTER || o.coarse_kernel == BURA_COARSE_FDIAG) && !p->cluster_ok)
+        return fail(BURA_EINVAL);
     if (p->dim == 0) {  // the sparse operator's row offsets and columns, shared by both precisions
         const HostLevel& h = p->hl[0];
         int* rp = nullptr;
@@ -1983,6 +2058,7 @@ int setup_plan(const bura_grid* grid, const double* const* faces, long long N, i
                const double* d, double E, double alpha, bool shifts_only, const bura_options& o, bura_plan** out) {
     const int dim = grid->dim;
     const bool var = grid->coef_kind == BURA_COEF_FACES;
+    if (o.coarse_kernel == BURA_COARSE_FDIAG && (dim != 2 || var)) return BURA_EINVAL;
     std::shared_lock<std::shared_mutex> guard(g_capture_guard);
     bura_plan* p = new (std::nothrow) bura_plan();
     if (!p) return BURA_ENOMEM;
@@ -2074,6 +2150,7 @@ int bura_setup_csr(const bura_csr* A, double alpha, int k, const bura_options* o
     if (opt) o = *opt;
     CA(check_options(o));
     if (o.refine == BURA_REFINE_DF) return BURA_EINVAL;  // double-float refinement: grids only
+    if (o.coarse_kernel == BURA_COARSE_FDIAG) return BURA_EINVAL;  // a grid operator's coarse solve
     // structure: offsets from 0 to nnz, columns in range, finite values, a positive diagonal in every row,
     // and symmetry (the entries sorted by (row, col) and by (col, row) must agree)
     const int n = A->n;

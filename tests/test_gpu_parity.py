@@ -172,6 +172,53 @@ def test_fp64_solve_each_coarse_kernel(lib, kind, csize, shape, var):
     assert (has_cluster, has_cta) == (kind == "CLUSTER", kind == "CTA"), names
 
 
+@pytest.mark.parametrize("shape", [(255, 255), (127, 63), (31, 31), (20, 13), (1, 1)])
+def test_fp64_solve_fdiag_coarse_kernel(lib, shape):
+    """The exact coarse solve by fast diagonalization (the sine eigenbasis of the 5-point operator, per
+    axis the eigenpairs of the three-point matrix of Sec. 4.1) converges to the BURA value at 1e-10.
+    Where the whole grid is the exact level (31^2, the unrefinable 20 x 13, one point) the preconditioner
+    is (A - d_j I)^{-1} itself, so every system converges in a single PCG iteration."""
+    nps = _np_shape(shape)
+    alpha, k = 0.5, 7
+    f = W.rhs_normal(nps, 6)
+    o = _opts(lib, lib.BURA_PREC_FP64, coarse_kernel=lib.BURA_COARSE_FDIAG)
+    plan = lib.bura_setup(shape, alpha, k, options=o)
+    try:
+        lib.bura_set_profiling(plan, True)
+        fd = torch.from_numpy(f).cuda()
+        ud = torch.zeros_like(fd)
+        assert lib.bura_solve(plan, fd, ud, 1e-11) == lib.BURA_OK
+        torch.cuda.synchronize()
+        names = {e["name"] for e in lib.bura_get_profile(plan)}
+        st = lib.bura_get_stats(plan)
+        u = ud.cpu().numpy()
+    finally:
+        lib.bura_destroy(plan)
+    ref = tables.entry(alpha, k)
+    assert _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"])) <= 1e-10
+    assert any(n.startswith("coarse_fdiag") for n in names), names
+    if max(shape) <= 31:
+        assert list(st["shift_iters"]) == [1] * (k + 1), st["shift_iters"]
+
+
+@pytest.mark.parametrize("shape", [(63, 63), (50, 37), (127, 127), (1023, 1023)])
+def test_mixed_solve_fdiag_coarse_kernel(lib, shape):
+    """The FP32 fast-diagonalization coarse solve inside the mixed path (the default for 2-D constant
+    coefficients) meets the solve tolerance against the exact BURA value; when the whole grid is the
+    exact level (at most 63 points per axis in FP32) each inner solve needs at most two PCG iterations
+    (FP32 rounding of the inverse)."""
+    nps = _np_shape(shape)
+    alpha, k, tol = 0.25, 7, 1e-6
+    f = W.rhs_uniform(nps, 4)
+    u, st, rc, (c, d, E) = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED,
+                                  coarse_kernel=lib.BURA_COARSE_FDIAG)
+    assert rc == lib.BURA_OK
+    ref = tables.entry(alpha, k)
+    assert _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"])) <= tol
+    if max(shape) <= 63:
+        assert st["iters"] <= 2 * st["outer"], (st["iters"], st["outer"])
+
+
 # ------------------------------------------------------------------ mixed path
 @pytest.mark.parametrize("sweeps", ["AUTO", "GRID"])
 @pytest.mark.parametrize("shape,alpha,k,tol", [((64, 64), 0.5, 5, 1e-6), ((127, 127), 0.25, 7, 1e-6),

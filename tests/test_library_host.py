@@ -54,7 +54,7 @@ def test_setup_rejects_bad_arguments_on_the_host(lib, shape, alpha, k):
     assert ei.value.code == lib.BURA_EINVAL
 
 
-@pytest.mark.parametrize("field,value", [("coarse_kernel", -1), ("coarse_kernel", 4), ("cluster_size", 3),
+@pytest.mark.parametrize("field,value", [("coarse_kernel", -1), ("coarse_kernel", 5), ("cluster_size", 3),
                                          ("cluster_size", 32), ("smoother_degree", 0), ("inner_rtol", 1.0),
                                          ("unscaled", 2), ("unscaled", -1), ("tma_wait_cycles", -1)])
 def test_setup_rejects_bad_options_on_the_host(lib, field, value):
@@ -285,4 +285,25 @@ def test_setup_csr_rejects_bad_matrices_on_the_host(lib, case):
         lam = -1.0
     with pytest.raises(lib.BuraError) as ei:
         lib.bura_setup_csr(rp, ci, va, 0.5, 5, lambda_min=lam)
+    assert ei.value.code == lib.BURA_EINVAL
+
+
+@pytest.mark.parametrize("case", ["3d", "faces", "csr"])
+def test_fdiag_coarse_kernel_rejected_off_2d_constant_grids_on_the_host(lib, case):
+    """BURA_COARSE_FDIAG (the exact sine-eigenbasis solve of a coarse level) exists for 2-D constant-
+    coefficient grids only: 3-D grids, face coefficients and sparse matrices are rejected before any
+    CUDA call."""
+    o = lib.bura_default_options()
+    o.coarse_kernel = lib.BURA_COARSE_FDIAG
+    with pytest.raises(lib.BuraError) as ei:
+        if case == "3d":
+            lib.bura_setup((7, 7, 7), 0.5, 5, options=o)
+        elif case == "faces":
+            from paper_1612_04846_gb300 import workloads as W
+            lib.bura_setup((7, 7), 0.5, 5, faces=W.block_lognormal_faces((7, 7), 2, 0.1, 1.0, 1), options=o)
+        else:
+            from oracle import operators
+            A = operators.fd_matrix((5, 4)).tocsr().astype(np.float64)
+            A.sort_indices()
+            lib.bura_setup_csr(A.indptr, A.indices, A.data, 0.5, 5, options=o)
     assert ei.value.code == lib.BURA_EINVAL
