@@ -16,8 +16,14 @@ namespace bura {
 
 // Tile of grid points staged per TMA load (x extent, y extent); the stencil input is loaded with a
 // one-point halo on every side, (kTX + 2) x (kTY + 2) points.
-constexpr int kTX = 32;
-constexpr int kTY = 8;
+#ifndef BURA_TMA_TX
+#define BURA_TMA_TX 32
+#endif
+#ifndef BURA_TMA_TY
+#define BURA_TMA_TY 8
+#endif
+constexpr int kTX = BURA_TMA_TX;
+constexpr int kTY = BURA_TMA_TY;
 // Coarse tile of the fused smoothing + restriction kernel: kTXc x kTYc coarse points, i.e. the fine
 // region of one fine tile; its right-hand side is loaded with a two-point halo (2 kTXc + 5 points).
 constexpr int kTXc = kTX / 2;
