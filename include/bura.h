@@ -113,12 +113,14 @@ typedef struct {
     int refine;           /* bura_refine (mixed precision only); default BURA_REFINE_FP64 */
     int tma_stages;       /* depth of the shared-memory ring of the TMA-staged sweeps, 1..4 (a kernel whose
                              ring does not fit shared memory uses fewer); 0 = auto (2) */
-    int post_smooth_split; /* 0 (default): on TMA-staged levels with degree-2 smoothing, the prolongation and
-                             both post-smoothing steps run as one sweep (the first step recomputed on a
-                             one-point halo); 1: as two sweeps (prolongation + first step, then the second
-                             step).  Every point gets the same operations either way; r.z is summed by
-                             a sweep with another CTA count, so the iterates may differ in the last
-                             bits of the FP32 beta. */
+    int post_smooth_split; /* on the TMA-staged levels (2-D, constant coefficients, FP32) with degree-2
+                             smoothing, how the prolongation and both post-smoothing steps run:
+                             0 (default): one sweep over TMA tiles (the first step recomputed on a
+                             one-point halo of each tile); 1: two sweeps (prolongation + first step, then
+                             the second step); 2: one sweep as y-marching strips (no recomputed rows,
+                             slower on GB300).  Every point gets the same operations each way; r.z is
+                             summed in another grouping, so the iterates may differ in the last bits of
+                             the FP32 beta. */
     int unscaled;         /* 0 (default): u solves the scaled problem A^alpha u = f.  1: f is the right-hand
                              side ftilde of the unscaled problem Atilde^alpha utilde = ftilde and u = utilde =
                              Lambda^-alpha (A^-alpha ftilde), since Atilde = Lambda A (eq. (algebraic), Sec. 1.4;

@@ -21,6 +21,8 @@
 // on the host exactly as the CTA keeps them (issued before the wait for the previous kernel).
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "kernels_impl.cuh"
 #include "tma.cuh"
 
@@ -268,9 +270,28 @@ void fdiag_image(int nx, int ny, const double* sx, const double* sy, std::vector
         for (int k = 0; k < ny; ++k) img[(size_t)lay.osy + (size_t)i * lay.ldsy + k] = (T)sy[(size_t)i * ny + k];
 }
 
+// The dynamic shared-memory limit of a kernel variant on the current device is only ever raised: a
+// captured graph of an earlier plan launches with its own (larger) size, and lowering the limit under
+// it would make those launches fail.
+template <class K>
+cudaError_t raise_smem_limit(K fn, int variant, int bytes) {
+    static std::mutex m;
+    static int limit[4][kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(m);
+    if (bytes <= limit[variant][dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) limit[variant][dev] = bytes;
+    return e;
+}
+
 template <class T>
 cudaError_t fdiag_prepare(int nx, int ny, int nsys, int* G, size_t* smem) {
     auto fn = fdiag_kernel<T>(nx, ny);
+    const int variant = (sizeof(T) == 8 ? 2 : 0) + (fdiag_small(nx, ny) ? 0 : 1);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     *G = 0;
@@ -280,7 +301,7 @@ cudaError_t fdiag_prepare(int nx, int ny, int nsys, int* G, size_t* smem) {
         if (c > nx || c > ny) continue;
         const size_t bytes = fdiag_smem_bytes<T>(nx, ny, c);
         if (bytes > 227 * 1024) continue;
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        e = raise_smem_limit(fn, variant, (int)bytes);
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
@@ -302,7 +323,7 @@ cudaError_t fdiag_prepare(int nx, int ny, int nsys, int* G, size_t* smem) {
     if (bestG == 0) return cudaErrorInvalidConfiguration;
     *G = bestG;
     *smem = fdiag_smem_bytes<T>(nx, ny, bestG);
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+    return raise_smem_limit(fn, variant, (int)*smem);
 }
 
 template <class T>

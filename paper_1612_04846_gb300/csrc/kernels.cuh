@@ -202,6 +202,26 @@ struct Launch {
     int Kp, C, PPB, blocks;
 };
 
+// Prolongation and both post-smoothing steps of a 2-D constant-coefficient FP32 level as y-marching
+// strips (strips.cu): items of 128 columns x SH rows, one CTA of Kp/4 x 132 threads per item.
+struct StripGeo {
+    int nx, ny, nxc, nyc, Kp;
+    int SH;       // rows per item (even)
+    int nstrips;  // strips across the level
+    int items;    // strips x row segments
+    float wx, wy;
+};
+StripGeo strip_geo(int nx, int ny, int nxc, int nyc, int Kp, float wx, float wy, int nsm);
+size_t strip_smem_bytes(int Kp);
+// Sets the strip kernel's dynamic shared-memory limit on the current device (a fixed size per Kp); called
+// at plan setup, outside any stream capture.
+cudaError_t strip_prepare(int Kp);
+// x, b: the level's iterate and right-hand side; ec: the coarse correction ([nyc][nxc][Kp]); xout: the result
+// (distinct from x and b); cs0 = (0, c2) of the first step, cs1 = (c1, c2) of the second; with red, b . xout.
+cudaError_t launch_post2_strip(const StripGeo& g, int nsm, const float* x, const float* ec, const float* b, float* xout,
+                               ChebStepT<float> cs0, ChebStepT<float> cs1, const float* dsh, const Red& red,
+                               cudaStream_t s);
+
 // Exact coarsest-level solve of a 2-D constant-coefficient operator by fast diagonalization (fdiag.cu):
 // one thread-block cluster of G CTAs per shifted system; every array holds element type T.
 struct FdiagArgs {

@@ -47,7 +47,7 @@ struct HostLevel {
 // Kernel types for launch counting and per-kernel timing (fine level only).
 enum KId { K_SPMV, K_CGUPD, K_CHEB0, K_CHEB, K_RESTRICT, K_PRE2, K_PROLONG, K_COARSE, K_DOT, K_BCAST, K_NORM,
            K_RES64, K_CAST, K_CORR64, K_WSUM, K_GATHER, K_CLUSTER, K_PRE2R, K_PROCHEB, K_RESDF, K_CASTDF, K_REDFIN,
-           K_POST2, K_RESID, K_PUPD, K_FDIAG, K_NK };
+           K_POST2, K_RESID, K_PUPD, K_FDIAG, K_POST2S, K_NK };
 // [kernel][f32][coarser level]
 const char* const kNames[K_NK][2][2] = {
     {{"spmv_p_f64", "spmv_p_f64@coarse"}, {"spmv_p_f32", "spmv_p_f32@coarse"}},
@@ -75,7 +75,8 @@ const char* const kNames[K_NK][2][2] = {
     {{"post2_f64", "post2_f64@coarse"}, {"post2_f32", "post2_f32@coarse"}},
     {{"residual_f64", "residual_f64@coarse"}, {"residual_f32", "residual_f32@coarse"}},
     {{"p_update_f64", "p_update_f64"}, {"p_update_f32", "p_update_f32"}},
-    {{"coarse_fdiag_f64", "coarse_fdiag_f64@coarse"}, {"coarse_fdiag_f32", "coarse_fdiag_f32@coarse"}}};
+    {{"coarse_fdiag_f64", "coarse_fdiag_f64@coarse"}, {"coarse_fdiag_f32", "coarse_fdiag_f32@coarse"}},
+    {{"post2_strip_f64", "post2_strip_f64@coarse"}, {"post2_strip_f32", "post2_strip_f32@coarse"}}};
 constexpr int kSlots = K_NK * 4;
 
 struct Tracer {
@@ -871,6 +872,7 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
     CA(dalloc(p, &w.scal, sizeof(Scal)));
     CK(cudaMemset(w.scal, 0, sizeof(Scal)));
     CA(build_tma(p, w));
+    if (sizeof(T) == 4 && p->dim == 2 && !p->var && w.Kp <= 16) CK(strip_prepare(w.Kp));
     w.ready = true;
     return BURA_OK;
 }
@@ -1083,7 +1085,21 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
                                 : ec == w.xb[lc1] ? tl.find(TB_CPRO2, w.xb[lc1]) : nullptr;
         const CUtensorMap* m_xa2 = tl.find(TB_HALO2, A);
         const CUtensorMap* m_bh = tl.find(TB_HALO, b);
-        if (!p->opt.post_smooth_split && mec2 && m_xa2 && m_bh) {
+        // the same as y-marching strips (no recomputed halo rows, the vertical neighbours in registers),
+        // option post_smooth_split = 2
+        const int pss = p->opt.post_smooth_split;
+        if (pss == 2 && l + 1 < (int)p->hl.size()) {
+            const Red& red = rz_fused ? beta : none;
+            const StripGeo sg = strip_geo(L.nx, L.ny, w.L[l + 1].nx, w.L[l + 1].ny, w.Kp, L.wxf, L.wyf, p->nsm);
+            traced(p, K_POST2S, f32, fine, vbytes<T>(p, l, 3.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
+                (void)launch_post2_strip(sg, p->nsm, f32_ptr(A), f32_ptr(ec), f32_ptr(b), reinterpret_cast<float*>(B),
+                                         f32_step(step_of(w, l, 0, false)), f32_step(step_of(w, l, 1)),
+                                         f32_ptr(w.dsh), red, s);
+            });
+            if (rz_fused) red_finish(p, beta, w.Kp, f32, s);
+            return B;
+        }
+        if (pss == 0 && mec2 && m_xa2 && m_bh) {
             const Red& red = rz_fused ? beta : none;
             traced(p, K_POST2, f32, fine, vbytes<T>(p, l, 3.0, false) + vbytes<T>(p, l + 1, 1.0, false), s, [&] {
                 (void)tma_post2(tl.geo, p->nsm, *m_xa2, *mec2, *m_bh, reinterpret_cast<float*>(B),
@@ -1971,7 +1987,7 @@ int check_options(const bura_options& o) {
           o.cluster_size == 16) ||
         o.sweeps < BURA_SWEEP_AUTO || o.sweeps > BURA_SWEEP_GRID || o.refine < BURA_REFINE_FP64 ||
         o.refine > BURA_REFINE_DF || o.tma_stages < 0 || o.tma_stages > 4 || o.post_smooth_split < 0 ||
-        o.post_smooth_split > 1 || o.unscaled < 0 || o.unscaled > 1 || o.tma_wait_cycles < 0 ||
+        o.post_smooth_split > 2 || o.unscaled < 0 || o.unscaled > 1 || o.tma_wait_cycles < 0 ||
         o.smoother_bf16 < 0 || o.smoother_bf16 > 1)
         return BURA_EINVAL;
     return BURA_OK;

@@ -239,21 +239,22 @@ def test_mixed_solve_within_tolerance(lib, shape, alpha, k, tol, sweeps):
     assert err <= tol, (err, st)
 
 
+@pytest.mark.parametrize("mode", [0, 2])
 @pytest.mark.parametrize("shape,alpha,k", [((1023, 1023), 0.5, 7), ((255, 255), 0.25, 3), ((511, 255), 0.75, 10),
-                                           ((127, 63), 0.5, 12), ((383, 129), 0.9, 7)])
-def test_fused_post_smoothing_matches_two_sweeps(lib, shape, alpha, k):
-    """The prolongation and both post-smoothing steps as one TMA sweep (the first step recomputed on a
-    one-point halo of every tile) against the same as two sweeps.  Every point gets the same operations,
-    but r.z is summed by a sweep with another CTA count, so its FP32 partial sums group differently;
-    beta reaches the kernels as an FP32 copy, which mostly absorbs that, not always.  A preconditioner
-    fault would change the iteration counts or the iterates at the solve tolerance: both must agree,
-    the solutions to 1e-8 (observed: bit-identical or within 1e-9), and both meet the oracle.  k = 3, 7,
-    10, 12 give 4, 8, 12 and 16 FP32 values per point (16 on 3-D tensor maps); every grid has ragged
-    last tiles."""
+                                           ((127, 63), 0.5, 12), ((383, 129), 0.9, 7), ((1023, 255), 0.25, 1)])
+def test_fused_post_smoothing_matches_two_sweeps(lib, shape, alpha, k, mode):
+    """The prolongation and both post-smoothing steps as one sweep (mode 0: TMA tiles, the first step
+    recomputed on a one-point halo of every tile; mode 2: y-marching strips of 124 columns, the vertical
+    neighbours in registers) against the same as two sweeps.  Every point gets the same operations, but r.z is summed in another grouping, so its
+    FP32 partial sums differ; beta reaches the kernels as an FP32 copy, which mostly absorbs that, not
+    always.  A preconditioner fault would change the iteration counts or the iterates at the solve
+    tolerance: both must agree, the solutions to 1e-8 (observed: bit-identical or within 1e-9), and both
+    meet the oracle.  k = 1, 3, 7, 10, 12 give 4, 4, 8, 12 and 16 FP32 values per point (16 on 3-D tensor
+    maps); every grid has ragged last tiles and strips."""
     nps = _np_shape(shape)
     f = W.rhs_uniform(nps, 5)
     tol = 1e-6
-    u1, st1, rc1, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED, post_smooth_split=0)
+    u1, st1, rc1, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED, post_smooth_split=mode)
     u2, st2, rc2, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED, post_smooth_split=1)
     assert rc1 == lib.BURA_OK and rc2 == lib.BURA_OK
     assert st1["iters"] == st2["iters"] and st1["outer"] == st2["outer"]
@@ -424,18 +425,20 @@ def test_full_size_3d_variable_coefficients(lib):
     assert _rel(u, usum) <= 1e-12
 
 
+@pytest.mark.parametrize("kind", ["CTA", "FDIAG"])
 @pytest.mark.parametrize("precision,tol", [("MIXED", 1e-6), ("FP64", 1e-10)])
-def test_plan_set_up_after_a_larger_coarse_cta_solves_both(lib, precision, tol):
-    """The single-CTA coarse kernel's shared-memory limit belongs to the kernel, not to a plan: a plan
-    set up later with a smaller coarse CTA (31^2: three levels, ~134 KB) must not lower the limit under
-    an earlier plan whose CTA holds its whole hierarchy (63x31: four levels, ~187 KB).  Both plans are
-    solved after both are set up, first the larger one."""
+def test_plan_set_up_after_a_larger_coarse_cta_solves_both(lib, precision, tol, kind):
+    """A coarse kernel's shared-memory limit belongs to the kernel, not to a plan: a plan set up later
+    with a smaller coarse CTA (31^2: three levels, ~134 KB; or a smaller fast-diagonalization level) must
+    not lower the limit under an earlier plan whose CTA holds its whole hierarchy (63x31: four levels,
+    ~187 KB; or the 63x31 exact level).  Both plans are solved after both are set up, the larger first."""
     probs = [((63, 31), 0.25, 9), ((31, 31), 0.5, 5)]
     prec = getattr(lib, "BURA_PREC_" + precision)
     plans = []
     try:
         for shape, alpha, k in probs:
-            plans.append(lib.bura_setup(shape, alpha, k, options=_opts(lib, prec)))
+            o = _opts(lib, prec, coarse_kernel=getattr(lib, "BURA_COARSE_" + kind))
+            plans.append(lib.bura_setup(shape, alpha, k, options=o))
         for i, (shape, alpha, k) in enumerate(probs):
             nps = _np_shape(shape)
             f = W.rhs_uniform(nps, 30 + i)
