@@ -783,7 +783,10 @@ def main(argv=None):
         if not sel:
             continue
         st = bura.bura_get_stats(plans[a])
-        per_alpha["%.2f" % a] = {"ms_mean": sum(sel) / len(sel), "inner_iters": st["iters"], "outer": st["outer"],
+        ss = sorted(sel)
+        per_alpha["%.2f" % a] = {"ms_mean": sum(sel) / len(sel), "p50_ms": ss[len(ss) // 2],
+                                 "p99_ms": ss[min(len(ss) - 1, int(round(0.99 * (len(ss) - 1))))],
+                                 "solves": len(sel), "inner_iters": st["iters"], "outer": st["outer"],
                                  "err_bound": st["err_bound"]}
 
     # ---- kernel-level timing of the same solves (events around every fine-level launch)
