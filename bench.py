@@ -587,7 +587,7 @@ def serve_pass(bura, np, torch, srv, data, upool, rate, seconds, warm, seed):
     free = {gi: list(upool[gi]) for gi in range(len(SERVE_GRIDS))}  # pinned before the pass: no CUDA
                                                                       # allocation beside the server's work
     state = {"in_flight": 0}
-    lat, done_t, per = [], [], {}
+    lat, done_t, per, per_kind, queue_ms = [], [], {}, {}, []
     state["shed"] = 0
     q = queue.Queue()
 
@@ -630,6 +630,9 @@ def serve_pass(bura, np, torch, srv, data, upool, rate, seconds, warm, seed):
                     lat.append(info["total_ms"] + 1e3 * (t_sub - t_sched))
                     done_t.append(t_done)
                     per.setdefault(gi, []).append(info["service_ms"])
+                    kind = "built" if info.get("built") else "retargeted" if info.get("retargeted") else "reused"
+                    per_kind.setdefault(kind, []).append(info["service_ms"])
+                    queue_ms.append(info.get("queue_ms", 0.0))
 
     th = threading.Thread(target=collect, daemon=True)
     th.start()
@@ -647,7 +650,12 @@ def serve_pass(bura, np, torch, srv, data, upool, rate, seconds, warm, seed):
     pct = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))] if lat else float("nan")
     return {"offered_per_s": rate, "arrivals_measured": n_meas, "completed": len(lat), "shed": state["shed"],
             "solves_per_s": len(lat) / span if lat else 0.0, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
-            "mean_service_ms_per_grid": {"x".join(map(str, SERVE_GRIDS[g])): float(np.mean(v)) for g, v in sorted(per.items())}}
+            "mean_service_ms_per_grid": {"x".join(map(str, SERVE_GRIDS[g])): float(np.mean(v)) for g, v in sorted(per.items())},
+            "median_service_ms_per_grid": {"x".join(map(str, SERVE_GRIDS[g])): float(np.median(v))
+                                           for g, v in sorted(per.items())},
+            "service_by_plan_state": {kd: {"requests": len(v), "mean_ms": float(np.mean(v)), "p50_ms": float(np.median(v))}
+                                      for kd, v in sorted(per_kind.items())},
+            "mean_queue_ms": float(np.mean(queue_ms)) if queue_ms else 0.0}
 
 
 def bench_serve(bura, W, np, torch, rate, seconds, warm):
