@@ -1001,6 +1001,96 @@ __global__ void __launch_bounds__(kSweepThreads, kSweepMinBlocks) k_prolong_add(
     sw_prolong_add<T, DIM>(Lf, Lc, Kp, ec, x, blockIdx.x, gridDim.x);
 }
 
+// 3-D x += P ec (trilinear) as z-marching columns, items as in zmarch: the bilinear (x, y) interpolation
+// of the coarse correction on a coarse plane is formed once and serves the three fine planes that
+// read it (2m, 2m + 1, 2m + 2); a fine plane takes it with weight 1 (odd) or the two neighbouring
+// coarse planes with 1/2 each (even), zero outside the coarse grid.  The same operator as prolong_at,
+// summed in another order (the (x, y) weights first).
+template <class T>
+__device__ __forceinline__ void prolong_axis(int f, int nc, int& lo, int& hi, T& wl, T& wh) {
+    if (f & 1) { lo = hi = (f - 1) >> 1; wl = T(1); wh = T(0); }
+    else {
+        lo = (f >> 1) - 1; hi = f >> 1;
+        wl = lo >= 0 ? T(0.5) : T(0);
+        wh = hi < nc ? T(0.5) : T(0);
+        if (lo < 0) lo = 0;
+        if (hi >= nc) hi = nc - 1;
+    }
+}
+template <class T>
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<3, true>()) k_prolong_add_z(Lev Lf, Lev Lc, int Kp, const T* __restrict__ ec, T* __restrict__ x) {
+    pdl_wait();
+    constexpr int W = VecT<T>::W;
+    const int off = threadIdx.x * W;
+    const int PX = (int)blockDim.y;
+    const int nxs = (Lf.nx + PX - 1) / PX;
+    const int nzc = (Lf.nz + kZRun - 1) / kZRun;
+    const int per_z = nxs * Lf.ny;
+    const int items = per_z * nzc;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int zc = item / per_z;
+        const int rem = item - zc * per_z;
+        const int j = rem / nxs;
+        const int i = (rem - j * nxs) * PX + (int)threadIdx.y;
+        if (i >= Lf.nx) continue;
+        int xl, xh, yl, yh;
+        T wxl, wxh, wyl, wyh;
+        prolong_axis<T>(i, Lc.nx, xl, xh, wxl, wxh);
+        prolong_axis<T>(j, Lc.ny, yl, yh, wyl, wyh);
+        const T w00 = wxl * wyl, w01 = wxh * wyl, w10 = wxl * wyh, w11 = wxh * wyh;
+        // the footprint of coarse plane m (zero outside the coarse grid), and its (x, y) interpolation
+        auto fetch = [&](int m, T (&e)[4][W]) {
+            for (int q = 0; q < 4; ++q)
+                for (int v = 0; v < W; ++v) e[q][v] = T(0);
+            if (m < 0 || m >= Lc.nz) return;
+            const size_t pb = (size_t)m * Lc.ny;
+            if (w00 != T(0)) vld(ec + ((pb + yl) * Lc.nx + xl) * Kp + off, e[0]);
+            if (w01 != T(0)) vld(ec + ((pb + yl) * Lc.nx + xh) * Kp + off, e[1]);
+            if (w10 != T(0)) vld(ec + ((pb + yh) * Lc.nx + xl) * Kp + off, e[2]);
+            if (w11 != T(0)) vld(ec + ((pb + yh) * Lc.nx + xh) * Kp + off, e[3]);
+        };
+        auto combine = [&](const T (&e)[4][W], T (&sv)[W]) {
+            for (int v = 0; v < W; ++v) {
+                T t = T(0);
+                if (w00 != T(0)) t = fma(w00, e[0][v], t);
+                if (w01 != T(0)) t = fma(w01, e[1][v], t);
+                if (w10 != T(0)) t = fma(w10, e[2][v], t);
+                if (w11 != T(0)) t = fma(w11, e[3][v], t);
+                sv[v] = t;
+            }
+        };
+        const int l0 = zc * kZRun;  // even
+        const int l1 = min(Lf.nz, l0 + kZRun);
+        T sp[W], sc[W];             // the interpolations on coarse planes l / 2 - 1 and l / 2 (l even)
+        T en[4][W];                 // the footprint of the next coarse plane, fetched one fine plane early
+        fetch((l0 >> 1) - 1, en);
+        combine(en, sp);
+        fetch(l0 >> 1, en);
+        combine(en, sc);
+        size_t base = ((size_t)l0 * Lf.plane + (size_t)j * Lf.nx + i) * Kp + off;
+        const size_t sz = (size_t)Lf.plane * Kp;
+        T xn[W];  // x on the next fine plane, loaded one plane early
+        vld(x + base, xn);
+        for (int l = l0; l < l1; ++l, base += sz) {
+            T xv[W], val[W];
+            for (int v = 0; v < W; ++v) xv[v] = xn[v];
+            if (l + 1 < l1) vld(x + base + sz, xn);
+            if (l & 1) {
+                for (int v = 0; v < W; ++v) val[v] = sc[v];
+                if (l + 1 < l1) fetch((l + 1) >> 1, en);  // the plane the next (even) fine plane adds
+            } else {
+                if (l > l0) {
+                    for (int v = 0; v < W; ++v) sp[v] = sc[v];
+                    combine(en, sc);
+                }
+                for (int v = 0; v < W; ++v) val[v] = fma(T(0.5), sc[v], T(0.5) * sp[v]);
+            }
+            for (int v = 0; v < W; ++v) xv[v] += val[v];
+            vst(x + base, xv);
+        }
+    }
+}
+
 template <class T, int DIM, bool VAR>
 __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<DIM, VAR>()) k_restrict_res(Lev Lf, Lev Lc, int Kp, const T* __restrict__ x, const T* __restrict__ b,
                                T* __restrict__ bc, const T* __restrict__ dsh) {
@@ -1405,7 +1495,7 @@ void Ops<T>::restrict_r(const Launch& gc, const Lev& Lf, const Lev& Lc, int dim,
 template <class T>
 void Ops<T>::prolong_add(const Launch& gf, const Lev& Lf, const Lev& Lc, int dim, const T* ec, T* x, cudaStream_t s) {
     if (dim == 2) launch_pdl(k_prolong_add<T, 2>, dim3(gf.blocks), blk(gf), 0, s, Lf, Lc, gf.Kp, ec, x);
-    else launch_pdl(k_prolong_add<T, 3>, dim3(gf.blocks), blk(gf), 0, s, Lf, Lc, gf.Kp, ec, x);
+    else launch_pdl(k_prolong_add_z<T>, dim3(gf.blocks), blk(gf), 0, s, Lf, Lc, gf.Kp, ec, x);
 }
 
 // The dynamic shared memory limit is a property of the kernel function (per device), not of a launch, so
