@@ -172,14 +172,16 @@ def test_fp64_solve_each_coarse_kernel(lib, kind, csize, shape, var):
     assert (has_cluster, has_cta) == (kind == "CLUSTER", kind == "CTA"), names
 
 
-@pytest.mark.parametrize("shape", [(255, 255), (127, 63), (31, 31), (20, 13), (1, 1)])
-def test_fp64_solve_fdiag_coarse_kernel(lib, shape):
+@pytest.mark.parametrize("shape,k", [((255, 255), 7), ((127, 63), 7), ((31, 31), 7), ((20, 13), 7), ((1, 1), 7),
+                                     ((127, 127), 2), ((63, 31), 9)])
+def test_fp64_solve_fdiag_coarse_kernel(lib, shape, k):
     """The exact coarse solve by fast diagonalization (the sine eigenbasis of the 5-point operator, per
     axis the eigenpairs of the three-point matrix of Sec. 4.1) converges to the BURA value at 1e-10.
     Where the whole grid is the exact level (31^2, the unrefinable 20 x 13, one point) the preconditioner
-    is (A - d_j I)^{-1} itself, so every system converges in a single PCG iteration."""
+    is (A - d_j I)^{-1} itself, so every system converges in a single PCG iteration.  k = 2 and 9 (3 and 10
+    systems) leave padding lanes in the 16-byte chunks of the FP64 layout."""
     nps = _np_shape(shape)
-    alpha, k = 0.5, 7
+    alpha = 0.5
     f = W.rhs_normal(nps, 6)
     o = _opts(lib, lib.BURA_PREC_FP64, coarse_kernel=lib.BURA_COARSE_FDIAG)
     plan = lib.bura_setup(shape, alpha, k, options=o)
