@@ -148,7 +148,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = ("kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "outer.cu", "fdiag.cu", "strips.cu", "noalloc.cu",
+KERNEL_SOURCES = ("kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "outer.cu", "fdiag.cu", "strips.cu", "sweep3d.cu", "noalloc.cu",
                   "kernels.cuh", "kernels_impl.cuh", "tma.cuh")
 
 

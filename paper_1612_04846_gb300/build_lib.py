@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbura.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "outer.cu", "fdiag.cu", "strips.cu",
+SOURCES = ["rational.cpp", "kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "outer.cu", "fdiag.cu", "strips.cu", "sweep3d.cu",
            "solver.cu", "noalloc.cu", "serve.cpp"]
 HEADERS = ["kernels.cuh", "kernels_impl.cuh", "tma.cuh", "guard.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

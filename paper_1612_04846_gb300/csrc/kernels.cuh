@@ -222,6 +222,22 @@ cudaError_t launch_post2_strip(const StripGeo& g, int nsm, const float* x, const
                                ChebStepT<float> cs0, ChebStepT<float> cs1, const float* dsh, const Red& red,
                                cudaStream_t s);
 
+// The 3-D FP32 Chebyshev step with its inputs staged plane by plane in a shared-memory ring (sweep3d.cu);
+// face weights in FP32 (not bf16).  cheb3s_prepare sets the kernel's shared-memory limit (plan setup).
+#ifndef BURA_CHEB3S
+#define BURA_CHEB3S 1
+#endif
+#ifndef BURA_CHEB3S_MIN_N
+#define BURA_CHEB3S_MIN_N 127
+#endif
+constexpr bool kCheb3s = BURA_CHEB3S != 0;     // 3-D Chebyshev steps of levels >= kCheb3sMinN wide staged
+constexpr int kCheb3sMinN = BURA_CHEB3S_MIN_N;  // in shared memory (else the z-marching grid sweep)
+size_t cheb3s_smem_bytes(int Kp, bool var);
+cudaError_t cheb3s_prepare(int Kp, bool var);
+cudaError_t launch_cheb_step3s(const Lev& L, int Kp, bool var, int nsm, const float* xin, const float* din,
+                               const float* b, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
+                               const Red& red, cudaStream_t s);
+
 // Exact coarsest-level solve of a 2-D constant-coefficient operator by fast diagonalization (fdiag.cu):
 // one thread-block cluster of G CTAs per shifted system; every array holds element type T.
 struct FdiagArgs {

@@ -873,6 +873,7 @@ int build_work(bura_plan* p, Work<T>& w, bool full = true) {
     CK(cudaMemset(w.scal, 0, sizeof(Scal)));
     CA(build_tma(p, w));
     if (sizeof(T) == 4 && p->dim == 2 && !p->var && w.Kp <= 16) CK(strip_prepare(w.Kp));
+    if (sizeof(T) == 4 && p->dim == 3 && w.Kp <= 16) CK(cheb3s_prepare(w.Kp, p->var));
     w.ready = true;
     return BURA_OK;
 }
@@ -1060,6 +1061,10 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
         if (mx && mb && (md || !din))
             (void)tma_cheb_step(tl.geo, p->nsm, *mx, md, *mb, reinterpret_cast<float*>(xout),
                                 reinterpret_cast<float*>(dout), f32_step(cs), f32_ptr(w.dsh), red, s);
+        else if (f32 && dim == 3 && kCheb3s && !L.cbf16 && L.nx >= kCheb3sMinN)
+            (void)launch_cheb_step3s(L, w.Kp, var, p->nsm, f32_ptr(xin), f32_ptr(din), f32_ptr(b),
+                                     reinterpret_cast<float*>(xout), reinterpret_cast<float*>(dout), f32_step(cs),
+                                     f32_ptr(w.dsh), red, s);
         else
             Ops<T>::cheb_step(g, L, dim, var, xin, din, b, xout, dout, cs, w.dsh, red, s);
     };
