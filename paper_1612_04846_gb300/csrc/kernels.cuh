@@ -237,6 +237,9 @@ cudaError_t cheb3s_prepare(int Kp, bool var);
 cudaError_t launch_cheb_step3s(const Lev& L, int Kp, bool var, int nsm, const float* xin, const float* din,
                                const float* b, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
                                const Red& red, cudaStream_t s);
+// r = b - (A - d_j I) x with the same staging
+cudaError_t launch_residual3s(const Lev& L, int Kp, bool var, int nsm, const float* x, const float* b, float* r,
+                              const float* dsh, cudaStream_t s);
 
 // Exact coarsest-level solve of a 2-D constant-coefficient operator by fast diagonalization (fdiag.cu):
 // one thread-block cluster of G CTAs per shifted system; every array holds element type T.

@@ -1180,7 +1180,13 @@ T* vcycle(bura_plan* p, Work<T>& w, int l, const T* b, bool rz_fused, cudaStream
     // second sweep: 27 (3-D) stencil evaluations per coarse point cost more than the extra vector pass.
     if (dim == 3 || var) {
         traced(p, K_RESID, f32, fine, vbytes<T>(p, l, 3.0, true), s,
-               [&] { Ops<T>::residual(g, L, dim, var, cur, b, D, w.dsh, s); });
+               [&] {
+                   if (f32 && dim == 3 && kCheb3s && !L.cbf16 && L.nx >= kCheb3sMinN)
+                       (void)launch_residual3s(L, w.Kp, var, p->nsm, f32_ptr(cur), f32_ptr(b),
+                                               reinterpret_cast<float*>(D), f32_ptr(w.dsh), s);
+                   else
+                       Ops<T>::residual(g, L, dim, var, cur, b, D, w.dsh, s);
+               });
         traced(p, K_RESTRICT, f32, fine, vbytes<T>(p, l, 1.0, false) + vbytes<T>(p, l + 1, 1.0, false), s,
                [&] { Ops<T>::restrict_r(w.g[l + 1], L, w.L[l + 1], dim, D, w.b[l + 1], s); });
     } else {

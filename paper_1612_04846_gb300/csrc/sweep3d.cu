@@ -1,4 +1,5 @@
-// The 3-D Chebyshev step (FP32) with its inputs staged in shared memory.
+// The 3-D Chebyshev step and the 3-D residual r = b - (A - d_j I) x (FP32) with their inputs staged in
+// shared memory.
 //
 // A work item is a tile of kPX x kPY points of the (x, y) plane over kPZ consecutive planes.  A CTA of
 // Kp/4 x kPX x kPY threads (one 16-byte chunk of one point each) marches the item along z: a ring of
@@ -50,7 +51,8 @@ __host__ __device__ constexpr int slot_floats(int Kp) {
     return (kPHalo + 2 * kPPts) * Kp + (VAR ? kPFaces : 0);
 }
 
-template <int C, bool VAR>
+// RES: store the residual b - (A - d_j I) x instead of the Chebyshev step (no d, no coefficients, no sum)
+template <int C, bool VAR, bool RES>
 __global__ void __launch_bounds__(C * kPPts, C <= 3 ? 2 : 1)
     k_cheb_step3s(Lev L, const float* __restrict__ xin, const float* __restrict__ din, const float* __restrict__ b,
                   float* __restrict__ xout, float* __restrict__ dout, ChebStepT<float> cs,
@@ -66,15 +68,15 @@ __global__ void __launch_bounds__(C * kPPts, C <= 3 ? 2 : 1)
     const int tid = p * C + c, nthr = C * kPPts;
     float c1[4], c2[4], d[4];
     for (int v = 0; v < 4; ++v) {
-        c1[v] = cs.c1 ? cs.c1[off + v] : 0.f;
-        c2[v] = cs.c2[off + v];
+        c1[v] = !RES && cs.c1 ? cs.c1[off + v] : 0.f;
+        c2[v] = RES ? 0.f : cs.c2[off + v];
         d[v] = dsh[off + v];
     }
     const float* fx = reinterpret_cast<const float*>(L.fx);
     const float* fy = reinterpret_cast<const float*>(L.fy);
     const float* fz = reinterpret_cast<const float*>(L.fz);
     const float* dg = reinterpret_cast<const float*>(L.dg);
-    const bool dot = red.op != RED_NONE;
+    const bool dot = !RES && red.op != RED_NONE;
     Accum<float> acc;
     const int ntx = (nx + kPX - 1) / kPX, nty = (ny + kPY - 1) / kPY, nzs = (nz + kPZ - 1) / kPZ;
     const int items = ntx * nty * nzs;
@@ -222,6 +224,11 @@ __global__ void __launch_bounds__(C * kPPts, C <= 3 ? 2 : 1)
                 a = fmaf(-wzm, xm1[v], a);
                 a = fmaf(-wzp, xp1[v], a);
                 const float res = bv[v] - fmaf(-d[v], x0[v], a);
+                if (RES) {
+                    xo[v] = res;
+                    xm1[v] = x0[v];
+                    continue;
+                }
                 float g = c2[v] * res;
                 if (VAR) g = jdiv(g, diag - d[v]);
                 dv[v] = fmaf(c1[v], dv[v], g);
@@ -258,7 +265,9 @@ size_t cheb3s_smem_bytes(int Kp, bool var) {
 cudaError_t cheb3s_prepare(int Kp, bool var) {
     const int bytes = (int)cheb3s_smem_bytes(Kp, var);
     cudaError_t e = cudaSuccess;
-    BURA_3S_SWITCH(Kp, var, e = cudaFuncSetAttribute(k_cheb_step3s<C, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))
+    BURA_3S_SWITCH(Kp, var, e = cudaFuncSetAttribute(k_cheb_step3s<C, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))
+    if (e != cudaSuccess) return e;
+    BURA_3S_SWITCH(Kp, var, e = cudaFuncSetAttribute(k_cheb_step3s<C, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))
     return e;
 }
 
@@ -269,8 +278,21 @@ cudaError_t launch_cheb_step3s(const Lev& L, int Kp, bool var, int nsm, const fl
     const int per_sm = Kp <= 12 ? 2 : 1;
     const int grid = (int)std::min<long long>(items, (long long)per_sm * nsm);
     const size_t smem = cheb3s_smem_bytes(Kp, var);
-    BURA_3S_SWITCH(Kp, var, launch_pdl(k_cheb_step3s<C, V>, dim3(grid), dim3(C, kPPts), smem, s, L, xin, din, b, xout,
-                                       dout, cs, dsh, red))
+    BURA_3S_SWITCH(Kp, var, launch_pdl(k_cheb_step3s<C, V, false>, dim3(grid), dim3(C, kPPts), smem, s, L, xin, din, b,
+                                       xout, dout, cs, dsh, red))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual3s(const Lev& L, int Kp, bool var, int nsm, const float* x, const float* b, float* r,
+                              const float* dsh, cudaStream_t s) {
+    const long long items = (long long)((L.nx + kPX - 1) / kPX) * ((L.ny + kPY - 1) / kPY) * ((L.nz + kPZ - 1) / kPZ);
+    const int per_sm = Kp <= 12 ? 2 : 1;
+    const int grid = (int)std::min<long long>(items, (long long)per_sm * nsm);
+    const size_t smem = cheb3s_smem_bytes(Kp, var);
+    const ChebStepT<float> none_cs{nullptr, nullptr};
+    const Red none{};
+    BURA_3S_SWITCH(Kp, var, launch_pdl(k_cheb_step3s<C, V, true>, dim3(grid), dim3(C, kPPts), smem, s, L, x,
+                                       (const float*)nullptr, b, r, (float*)nullptr, none_cs, dsh, none))
     return cudaGetLastError();
 }
 
