@@ -12,20 +12,23 @@ Sec. 2.2):
 
     t^{-1} r(t) = sum_{j=0}^k c_j / (t - d_j),   d_0 = 0 > d_1 > ... > d_k.
 
-How (Algorithm 1, Sec. 3.2, taken step by step)
-------------------------------------------------
-* Work in the Chebyshev representation of eq. (eq1bua): s = 2t - 1 and
-  f(s) = ((1+s)/2)^(1-alpha), r(s) = sum pbar_j T_j(s) / (1 + sum_{j>=1} qbar_j T_j(s)).
-* Step 3 (update the rational approximation): on the current points s_i solve
-  f(s_i) - r(s_i) = (-1)^i E (i = 1..l, l = 2k+2) by the inner iteration of
-  Step 3(ii): with E^{(v-1)} fixed the system is linear in (pbar, qbar, E^{(v)});
-  the iteration on E is accelerated with Aitken-Steffensen over three successive
-  values (remark (3) after Algorithm 1).
-* Step 1 (update the equioscillation set): for every point s_i take the nearest
-  zeros of f - r on each side (Step 1(i)), the maximiser of |f - r| between them
-  (Step 1(ii)), then the global maximiser with the sign-preserving insertion
-  rule of Step 1(iii)-(iv).
-* Step 2 (convergence): stop when max_i eta_i - min_i eta_i < delta.
+How (the modified Remez method of Sec. 3.2, Algorithm 1)
+---------------------------------------------------------
+The best approximation is characterised by equioscillation: f - r takes the
+values -E, +E, -E, ... with |E| maximal on 2k+2 ordered points of [0,1].  The
+oracle alternates two sub-problems until the extrema of |f - r| are level:
+* Representation: Chebyshev polynomials in s = 2t - 1 (eq. (eq1bua)),
+  r(s) = sum pbar_j T_j(s) / (1 + sum_{j>=1} qbar_j T_j(s)).
+* Fit on fixed points: the equations f(s_i) - r(s_i) = (-1)^i E (i = 1..l,
+  l = 2k+2) are nonlinear only through E multiplying the denominator.  Freezing
+  that E makes them a linear system in (pbar, qbar, new E); the level is the fixed
+  point of this map, reached with Aitken-Steffensen extrapolation over three
+  successive values (the acceleration Sec. 3.2 recommends), with a secant
+  iteration as fallback.
+* Exchange of points: between consecutive zeros of f - r each new point is the
+  maximiser of |f - r|; then the global maximiser of |f - r| on [0,1] replaces
+  the neighbour of the same error sign, so that the signs keep alternating.
+* Stop when max_i |f - r|(t_i) - min_i |f - r|(t_i) < delta.
 * Output: E = |E_n| and the points; poles are the roots of Q mapped back with
   t = (1+s)/2, and c_0 = P(0)/Q(0), c_j = P(d_j) / (d_j Q'(d_j)) (eq. (simplified);
   c_0 = E by eq. (c0,beta), Sec. 4.1).
@@ -34,24 +37,24 @@ Readings where the paper leaves a choice
 ----------------------------------------
 * Arithmetic: mpmath with max(60, 40 + 4 |log10 eta_2|) decimal digits.  Table
   (tabLastS) shows that quad precision stops converging at k = 7..11; the extreme
-  points cluster at 0 (eta_2 ~ 1e-25 for alpha = 0.9, k = 9) and the Step 3 matrix
+  points cluster at 0 (eta_2 ~ 1e-25 for alpha = 0.9, k = 9) and the fit's matrix
   loses about 4 digits per decade of eta_2, so far more digits are used.
 * Initialisation (the paper uses uniformly sampled points and a least-squares
   r_0, without detail): continuation.  At alpha = 1/2 the k = 1 problem starts
   from the points {0, 0.01, 0.3, 1} and the points for k+1 are those for k with
   two points added below eta_2 by geometric extrapolation of the three smallest
   nonzero points.  Any other alpha starts from the converged points of the same k
-  at alpha -/+ 0.05 (towards 1/2).  r_0 is the exact solution of Step 3 on these
-  points; it must alternate with E > 0 there, as the Initialization step requires,
-  otherwise the run stops with an error.
+  at alpha -/+ 0.05 (towards 1/2).  r_0 is the exact fit on these points; it must
+  alternate with E > 0 there, as the method's initialisation requires, otherwise
+  the run stops with an error.
 * Stopping: delta = 1e-13 E; a run that does not reach it within N = 80
   iterations raises (the extreme points are located to about 1e-15 in log t, so
   the spread floors near 1e-14 E).
-* Step 1 search: the paper refines on shrinking local meshes (remark (2)); here
+* Search for zeros and maxima: the paper refines on shrinking local meshes; here
   zeros are bracketed by bisection in log t and maxima found by golden-section
   search in log t after a coarse scan.  The end points t = 0 and t = 1 are extreme
   points of the BURA error (Lemma BURA_caracter, item 3) and are never displaced by
-  the insertion of Step 1(iv).
+  the insertion of the global maximiser.
 * Sign convention: i = 1 is s = -1 (t = 0), so f(0) - r(0) = -E and r(0) = +E,
   matching Lemma 2.2 ("BURA_caracter") item 3 and eq. (c0,beta).
 * Normalisation of the monomial form: q_k = 1, as in Tables ta:coeff1-3.
@@ -90,8 +93,9 @@ class _Problem:
         return self.f(t) - self.r(pbar, qbar, t)
 
 
-def _step3_linear(P, pts, E_prev):
-    """One linear solve of Step 3(ii) with E^{(v-1)} = E_prev fixed."""
+def _fit_frozen_level(P, pts, E_prev):
+    """The fit on fixed points with the level multiplying the denominator frozen at E_prev: a
+    linear system in (pbar, qbar_1..k, E)."""
     k = P.k
     l = 2 * k + 2
     M = mp.matrix(l, l)
@@ -112,16 +116,16 @@ def _step3_linear(P, pts, E_prev):
     return pbar, qbar, x[l - 1]
 
 
-def _step3(P, pts, E0, V=60):
-    """Step 3: the fixed point E = phi(E) of the inner iteration of Step 3(ii), where phi(E) is
-    the E^{(v)} returned by the linear solve with E^{(v-1)} = E.  Aitken-Steffensen over three
-    successive values (remark (3) after Algorithm 1); when that does not settle the residual
-    g(E) = phi(E) - E within V steps, a secant iteration on g takes over."""
+def _fit(P, pts, E0, V=60):
+    """The equioscillating fit on fixed points: the fixed point E = phi(E), phi(E) being the level
+    the frozen-level linear system returns.  Aitken-Steffensen over three successive values; when
+    that does not settle the residual g(E) = phi(E) - E within V steps, a secant iteration on g
+    takes over."""
     E = E0
     eps = mp.mpf(10) ** (-(mp.mp.dps - 20))
 
     def phi(x):
-        return _step3_linear(P, pts, x)[2]
+        return _fit_frozen_level(P, pts, x)[2]
 
     for _ in range(V):
         E1 = phi(E)
@@ -147,7 +151,7 @@ def _step3(P, pts, E0, V=60):
             if abs(gb) <= eps * abs(b):
                 break
         E = b
-    return _step3_linear(P, pts, E)
+    return _fit_frozen_level(P, pts, E)
 
 
 def _zero_between(P, pbar, qbar, a, b):
@@ -188,7 +192,7 @@ def _golden_max(P, pbar, qbar, a, b):
 
 
 def _argmax_between(P, pbar, qbar, a, b, nscan=12):
-    """Step 1(ii): argmax of |f - r| on [a, b] (a may be 0, b may be 1).
+    """argmax of |f - r| on [a, b], an interval between consecutive zeros (a may be 0, b may be 1).
 
     t = 0 and t = 1 are extreme points of the BURA error (Lemma BURA_caracter, item 3), so on the
     first and the last interval the point is the end point itself: a scan would otherwise pick a
@@ -208,7 +212,7 @@ def _argmax_between(P, pbar, qbar, a, b, nscan=12):
 
 
 def _global_argmax(P, pbar, qbar, pts, nscan=400):
-    """Step 1(iii): global maximiser of |f - r| on [0,1] (scan + refine)."""
+    """Global maximiser of |f - r| on [0,1] (scan + refine)."""
     lo_exp = mp.mp.dps - 15
     grid = sorted(set([mp.mpf(0), mp.mpf(1)] + list(pts)
                       + [mp.mpf(10) ** (-lo_exp + lo_exp * mp.mpf(i) / nscan) for i in range(nscan)]
@@ -225,7 +229,7 @@ def _global_argmax(P, pbar, qbar, pts, nscan=400):
 
 
 def remez_bura(alpha, k, pts0, dps=60, N=80, delta_rel=mp.mpf(10) ** -13):
-    """Algorithm 1 for beta = 1, m = k, from the initial points ``pts0`` (in t).
+    """The modified Remez method (Sec. 3.2) for beta = 1, m = k, from the initial points ``pts0`` (in t).
 
     Returns (pbar, qbar, E, pts): Chebyshev coefficients of P and Q in s = 2t-1
     (qbar_0 = 1), the signed level E (> 0 at convergence) and the 2k+2 points in t.
@@ -236,17 +240,17 @@ def remez_bura(alpha, k, pts0, dps=60, N=80, delta_rel=mp.mpf(10) ** -13):
         pts = [mp.mpf(t) for t in pts0]
         if len(pts) != l:
             raise ValueError("need 2k+2 initial points")
-        # Initialization: r_0 solves Step 3 on s^(0); it must alternate there with E > 0.
-        pbar, qbar, E = _step3(P, pts, mp.mpf(0))
+        # r_0: the fit on the initial points; it must alternate there with E > 0.
+        pbar, qbar, E = _fit(P, pts, mp.mpf(0))
         if not E > 0:
             raise RuntimeError("inadmissible initial points for alpha=%s k=%d" % (alpha, k))
         converged = False
         for _n in range(1, N + 1):
-            # Step 1 (i)-(ii): zeros around each point, then the maximiser between them.
+            # zeros of the error between neighbouring points, then the maximiser between zeros
             zeros = [_zero_between(P, pbar, qbar, pts[i], pts[i + 1]) for i in range(l - 1)]
             bnd = [mp.mpf(0)] + zeros + [mp.mpf(1)]
             new = [_argmax_between(P, pbar, qbar, bnd[i], bnd[i + 1]) for i in range(l)]
-            # Step 1 (iii)-(iv): global maximiser, inserted keeping the sign pattern.
+            # the global maximiser replaces the neighbour of the same sign (signs keep alternating)
             ts = _global_argmax(P, pbar, qbar, new)
             # t = 0 and t = 1 are extreme points of the BURA error (Lemma BURA_caracter, item 3):
             # they stay in the set, so a maximiser that would displace them is not inserted
@@ -258,12 +262,12 @@ def remez_bura(alpha, k, pts0, dps=60, N=80, delta_rel=mp.mpf(10) ** -13):
                     new[j] = ts
             eta = [abs(P.e(pbar, qbar, t)) for t in new]
             pts = new
-            # Step 2: convergence check.
+            # level extrema: done
             if max(eta) - min(eta) < delta_rel * abs(E):
                 converged = True
                 break
-            # Step 3: new rational approximation on the updated points.
-            pbar, qbar, E = _step3(P, pts, E)
+            # refit on the exchanged points
+            pbar, qbar, E = _fit(P, pts, E)
             if not E > 0:
                 raise RuntimeError("Remez lost the alternation for alpha=%s k=%d" % (alpha, k))
         if not converged:
@@ -377,7 +381,7 @@ def bura(alpha, k, dps=60):
                         raise
                     work += 40
         # r(0) = E holds exactly for the BURA (t = 0 is an extreme point, where the error is -r(0)); the
-        # Step 3 system meets it only to its working precision divided by |Q(s = -1)|, which can be as
+        # fit on the points meets it only to its working precision divided by |Q(s = -1)|, which can be as
         # small as 1e-89 of Q's coefficients.  When the computed r(0) misses E by more than 1e-25
         # relative, Algorithm 1 is rerun from the converged points with 40 more digits.
         for _ in range(4):
@@ -400,7 +404,7 @@ def _r_at_zero(pbar, qbar):
 
 
 def _work_dps(pts, dps):
-    """The Step 3 matrix loses about 4 digits per decade that eta_2 sits below 1 (its rows at the
+    """The fit's matrix loses about 4 digits per decade that eta_2 sits below 1 (its rows at the
     clustered points near s = -1 become nearly equal), so the working precision grows with
     -log10(eta_2) of the starting points."""
     return max(dps, int(mp.ceil(40 + 4 * (-mp.log10(pts[1])))))
