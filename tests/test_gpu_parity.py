@@ -427,6 +427,41 @@ def test_full_size_3d_variable_coefficients(lib):
     assert _rel(u, usum) <= 1e-12
 
 
+@pytest.mark.parametrize("var", [False, True])
+@pytest.mark.parametrize("k", [3, 7, 9, 12])
+def test_staged_3d_sweeps_every_chunk_count(lib, k, var):
+    """The 3-D FP32 sweeps staged in shared memory (the levels at least 127 points wide) for 1, 2, 3 and
+    4 chunks of four systems a point (k = 3, 7, 9, 12), constant and variable coefficients, on 127^3: a
+    16 x 8 x 128 work item leaves ragged tiles on every axis (127 = 7 * 16 + 15 = 15 * 8 + 7 < 128).
+    Constant coefficients: within tol of the exact BURA value (eq. (exacalg)).  Variable coefficients
+    (log-uniform in [1e-2, 1] on 8^3 blocks): the rigorous bound of every system's residual, computed with
+    the oracle's sparse operator as in the 255^3 test, within tol ||f||."""
+    shape, alpha, tol = (127, 127, 127), 0.5, 1e-6
+    nps = _np_shape(shape)
+    f = W.rhs_normal(nps, 11)
+    ref = tables.entry(alpha, k)
+    if not var:
+        u, st, rc, _ = _solve(lib, shape, alpha, k, f, tol, lib.BURA_PREC_MIXED)
+        assert rc == lib.BURA_OK
+        assert _rel(u, exact.bura_value(nps, f, ref["c"], ref["d"])) <= tol, st
+        return
+    faces = W.block_lognormal_faces(nps, 8, 1e-2, 1.0, 2)
+    plan = lib.bura_setup(shape, alpha, k, faces=faces, options=_opts(lib, lib.BURA_PREC_MIXED))
+    try:
+        fd = torch.from_numpy(f).cuda()
+        V = torch.zeros((k + 1, f.size), dtype=torch.float64, device="cuda")
+        assert lib.bura_solve_systems(plan, fd, V, tol) == lib.BURA_OK
+        torch.cuda.synchronize()
+        c, d, _ = lib.bura_get_rational(plan, k)
+        V = V.cpu().numpy()
+    finally:
+        lib.bura_destroy(plan)
+    A, _ = operators.scaled_matrix(nps, faces)
+    lam_lo = min(float(a.min()) for a in faces) * float(exact.eigenvalues(nps).min())
+    bound = sum(c[j] * np.linalg.norm(f - (A @ V[j] - d[j] * V[j])) / (lam_lo - d[j]) for j in range(k + 1))
+    assert bound <= tol * np.linalg.norm(f), bound / np.linalg.norm(f)
+
+
 @pytest.mark.parametrize("kind", ["CTA", "FDIAG"])
 @pytest.mark.parametrize("precision,tol", [("MIXED", 1e-6), ("FP64", 1e-10)])
 def test_plan_set_up_after_a_larger_coarse_cta_solves_both(lib, precision, tol, kind):
