@@ -427,16 +427,17 @@ def test_full_size_3d_variable_coefficients(lib):
     assert _rel(u, usum) <= 1e-12
 
 
-@pytest.mark.parametrize("var", [False, True])
-@pytest.mark.parametrize("k", [3, 7, 9, 12])
-def test_staged_3d_sweeps_every_chunk_count(lib, k, var):
+@pytest.mark.parametrize("n,k,var", [(127, k, v) for v in (False, True) for k in (3, 7, 9, 12)]
+                         + [(255, 7, False), (255, 12, False), (255, 3, True)])
+def test_staged_3d_sweeps_every_chunk_count(lib, n, k, var):
     """The 3-D FP32 sweeps staged in shared memory (the levels at least 127 points wide) for 1, 2, 3 and
     4 chunks of four systems a point (k = 3, 7, 9, 12), constant and variable coefficients, on 127^3: a
-    16 x 8 x 128 work item leaves ragged tiles on every axis (127 = 7 * 16 + 15 = 15 * 8 + 7 < 128).
-    Constant coefficients: within tol of the exact BURA value (eq. (exacalg)).  Variable coefficients
-    (log-uniform in [1e-2, 1] on 8^3 blocks): the rigorous bound of every system's residual, computed with
-    the oracle's sparse operator as in the 255^3 test, within tol ||f||."""
-    shape, alpha, tol = (127, 127, 127), 0.5, 1e-6
+    16 x 8 x 128 work item leaves ragged tiles on every axis (127 = 7 * 16 + 15 = 15 * 8 + 7 < 128); on
+    255^3 every column of tiles is two work items along z (128 + 127 planes), so the second item starts
+    from the plane below it.  Constant coefficients: within tol of the exact BURA value (eq. (exacalg)).
+    Variable coefficients (log-uniform in [1e-2, 1] on 8^3 blocks): the rigorous bound of every system's
+    residual, computed with the oracle's sparse operator as in the 255^3 test, within tol ||f||."""
+    shape, alpha, tol = (n, n, n), 0.5, 1e-6
     nps = _np_shape(shape)
     f = W.rhs_normal(nps, 11)
     ref = tables.entry(alpha, k)
