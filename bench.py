@@ -148,15 +148,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_SOURCES = ("kernels_f32.cu", "kernels_f64.cu", "kernels_tma.cu", "kernels_df.cu", "outer.cu", "fdiag.cu", "strips.cu", "sweep3d.cu", "noalloc.cu",
-                  "kernels.cuh", "kernels_impl.cuh", "tma.cuh")
+# Per workload of profiles/ncu_traffic.json: the sources of the kernels whose DRAM traffic it records
+# (device code and the headers it includes).  Host-only files and the sources of other kernels do not
+# change the recorded traffic, so they are not hashed.
+TRAFFIC_SOURCES = {"2d_1023_k7": ("kernels_f32.cu", "kernels_tma.cu", "kernels.cuh", "kernels_impl.cuh", "tma.cuh")}
 
 
-def sources_sha():
-    """Hash of the kernel sources (device code and the headers it includes), whose per-launch DRAM
-    traffic profiles/ncu_traffic.json records; host-only files do not change it."""
+def sources_sha(workload="2d_1023_k7"):
+    """Hash of the kernel sources whose per-launch DRAM traffic profiles/ncu_traffic.json records for
+    `workload`."""
     h = hashlib.sha256()
-    for fn in KERNEL_SOURCES:
+    for fn in TRAFFIC_SOURCES[workload]:
         with open(os.path.join(CSRC, fn), "rb") as fh:
             h.update(fn.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -178,9 +180,10 @@ def ncu_traffic(kernel, workload="2d_1023_k7"):
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("sources_sha") != sources_sha():
+    w = d.get("workloads", {}).get(workload)
+    if not w or workload not in TRAFFIC_SOURCES or w.get("sources_sha") != sources_sha(workload):
         return None
-    ent = d.get("workloads", {}).get(workload, {}).get(kernel)
+    ent = w.get("kernels", {}).get(kernel)
     return None if ent is None else float(ent["dram_bytes_per_launch_full_size"])
 
 

@@ -1,7 +1,8 @@
 // The 3-D Chebyshev step and the 3-D residual r = b - (A - d_j I) x (FP32) with their inputs staged in
 // shared memory.
 //
-// A work item is a tile of kPX x kPY points of the (x, y) plane over kPZ consecutive planes.  A CTA of
+// A work item is a tile of kPX x kPY points of the (x, y) plane over pz consecutive planes (kPZ where the
+// items of a level fill the grid's CTA slots, kPZ / 2 on levels where they do not).  A CTA of
 // Kp/4 x kPX x kPY threads (one 16-byte chunk of one point each) marches the item along z: a ring of
 // kPRing plane slots in shared memory holds, per plane, x on the tile with a one-point halo, b, the
 // previous direction d, and for variable coefficients the face weights and the diagonal of the tile's
@@ -21,7 +22,7 @@ constexpr int kPX = 16, kPY = 8;      // tile points along x and y
 #ifndef BURA_3S_PZ
 #define BURA_3S_PZ 128
 #endif
-constexpr int kPZ = BURA_3S_PZ;       // planes per work item
+constexpr int kPZ = BURA_3S_PZ;       // planes per work item on levels whose items fill the grid
 constexpr int kPRing = 4;             // plane slots of the ring
 constexpr int kPHx = kPX + 2, kPHy = kPY + 2;  // the tile with its one-point halo
 constexpr int kPPts = kPX * kPY;
@@ -56,7 +57,7 @@ template <int C, bool VAR, bool RES>
 __global__ void __launch_bounds__(C * kPPts, C <= 3 ? 2 : 1)
     k_cheb_step3s(Lev L, const float* __restrict__ xin, const float* __restrict__ din, const float* __restrict__ b,
                   float* __restrict__ xout, float* __restrict__ dout, ChebStepT<float> cs,
-                  const float* __restrict__ dsh, Red red) {
+                  const float* __restrict__ dsh, Red red, int pz) {
     pdl_wait();
     constexpr int Kp = 4 * C;
     constexpr int SF = slot_floats<VAR>(Kp);
@@ -78,13 +79,13 @@ __global__ void __launch_bounds__(C * kPPts, C <= 3 ? 2 : 1)
     const float* dg = reinterpret_cast<const float*>(L.dg);
     const bool dot = !RES && red.op != RED_NONE;
     Accum<float> acc;
-    const int ntx = (nx + kPX - 1) / kPX, nty = (ny + kPY - 1) / kPY, nzs = (nz + kPZ - 1) / kPZ;
+    const int ntx = (nx + kPX - 1) / kPX, nty = (ny + kPY - 1) / kPY, nzs = (nz + pz - 1) / pz;
     const int items = ntx * nty * nzs;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int tz = item / (ntx * nty);
         const int rem = item - tz * ntx * nty;
         const int ty = rem / ntx, tx = rem - ty * ntx;
-        const int X0 = tx * kPX, Y0 = ty * kPY, l0 = tz * kPZ, l1 = min(nz, l0 + kPZ);
+        const int X0 = tx * kPX, Y0 = ty * kPY, l0 = tz * pz, l1 = min(nz, l0 + pz);
         // this thread's copies of a plane, fixed per item (slot offset, offset within the plane, in range):
         // halo chunks tid and tid + nthr of the (kPX + 2) x (kPY + 2) x C, the b (and d) chunk tid, and face
         // weights tid + u nthr (u < kFc)
@@ -247,6 +248,14 @@ __global__ void __launch_bounds__(C * kPPts, C <= 3 ? 2 : 1)
     if (dot) reduce_finish<float>(acc, red, Kp);
 }
 
+// Planes per work item for a level and the grid: kPZ planes where the level's items fill the CTA slots,
+// else kPZ / 2 (a 127^3 level has 128 items of 128 planes for 304 slots of 152 SMs).
+int item_grid(const Lev& L, long long slots, int& pz) {
+    const long long cols = (long long)((L.nx + kPX - 1) / kPX) * ((L.ny + kPY - 1) / kPY);
+    pz = cols * ((L.nz + kPZ - 1) / kPZ) >= slots ? kPZ : kPZ / 2;
+    return (int)std::min<long long>(cols * ((L.nz + pz - 1) / pz), slots);
+}
+
 }  // namespace
 
 size_t cheb3s_smem_bytes(int Kp, bool var) {
@@ -274,25 +283,25 @@ cudaError_t cheb3s_prepare(int Kp, bool var) {
 cudaError_t launch_cheb_step3s(const Lev& L, int Kp, bool var, int nsm, const float* xin, const float* din,
                                const float* b, float* xout, float* dout, ChebStepT<float> cs, const float* dsh,
                                const Red& red, cudaStream_t s) {
-    const long long items = (long long)((L.nx + kPX - 1) / kPX) * ((L.ny + kPY - 1) / kPY) * ((L.nz + kPZ - 1) / kPZ);
     const int per_sm = Kp <= 12 ? 2 : 1;
-    const int grid = (int)std::min<long long>(items, (long long)per_sm * nsm);
+    int pz = 0;
+    const int grid = item_grid(L, (long long)per_sm * nsm, pz);
     const size_t smem = cheb3s_smem_bytes(Kp, var);
     BURA_3S_SWITCH(Kp, var, launch_pdl(k_cheb_step3s<C, V, false>, dim3(grid), dim3(C, kPPts), smem, s, L, xin, din, b,
-                                       xout, dout, cs, dsh, red))
+                                       xout, dout, cs, dsh, red, pz))
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual3s(const Lev& L, int Kp, bool var, int nsm, const float* x, const float* b, float* r,
                               const float* dsh, cudaStream_t s) {
-    const long long items = (long long)((L.nx + kPX - 1) / kPX) * ((L.ny + kPY - 1) / kPY) * ((L.nz + kPZ - 1) / kPZ);
     const int per_sm = Kp <= 12 ? 2 : 1;
-    const int grid = (int)std::min<long long>(items, (long long)per_sm * nsm);
+    int pz = 0;
+    const int grid = item_grid(L, (long long)per_sm * nsm, pz);
     const size_t smem = cheb3s_smem_bytes(Kp, var);
     const ChebStepT<float> none_cs{nullptr, nullptr};
     const Red none{};
     BURA_3S_SWITCH(Kp, var, launch_pdl(k_cheb_step3s<C, V, true>, dim3(grid), dim3(C, kPPts), smem, s, L, x,
-                                       (const float*)nullptr, b, r, (float*)nullptr, none_cs, dsh, none))
+                                       (const float*)nullptr, b, r, (float*)nullptr, none_cs, dsh, none, pz))
     return cudaGetLastError();
 }
 
