@@ -753,7 +753,13 @@ def main(argv=None):
         o.precision = precision
         return bura.bura_setup(SHAPE, alpha, K_DEG, options=o)
 
-    plans = {a: make_plan(a, bura.BURA_PREC_MIXED) for a in ALPHAS}
+    # setup_s: wall time of bura_setup (host Remez, hierarchy, device buffers; the first one also pays
+    # the library's module load on the device)
+    plans, setup_s = {}, {}
+    for a in ALPHAS:
+        t0 = time.perf_counter()
+        plans[a] = make_plan(a, bura.BURA_PREC_MIXED)
+        setup_s[a] = time.perf_counter() - t0
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     def step(i, plan_set, tol=TOL, out=u):
@@ -798,7 +804,7 @@ def main(argv=None):
         per_alpha["%.2f" % a] = {"ms_mean": sum(sel) / len(sel), "p50_ms": ss[len(ss) // 2],
                                  "p99_ms": ss[min(len(ss) - 1, int(round(0.99 * (len(ss) - 1))))],
                                  "solves": len(sel), "inner_iters": st["iters"], "outer": st["outer"],
-                                 "err_bound": st["err_bound"]}
+                                 "err_bound": st["err_bound"], "setup_s": setup_s[a]}
 
     # ---- kernel-level timing of the same solves (events around every fine-level launch)
     prof_plan = plans[0.5]
